@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the fiber-diffraction hot path on one B300 (or N replicas).
+
+One step = the whole forward path for the 2,000-atom helical fiber model
+(hexagonal 20x20x28 A cell, d >= 2.0 A: 5,062 reflections; Voigt orientation
+3 deg / 2 deg; Hosemann g = 2 % along a and b; 64x64 shell nodes; 1024^2
+detector): structure factors (fdx_structure_factors) then the
+Lorentz-corrected pattern (fdx_pattern, which includes the per-call pixel
+geometry, node-table and reflection set-up kernels).
+
+Metric: pixel-reflection-node evaluations per second, where the evaluation
+count E is the number of (pixel, reflection, node) terms inside the lineshape
+support (computed once with fdx_pattern_evals).  Inputs are resident in HBM
+when the timed region starts; between timed steps a 512 MiB buffer is written
+to flush L2 (outside the per-step CUDA events).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
+no collective on the data path); value = all ranks' evaluations / max time.
+`--impl reference` times the FP64 CPU oracle on a bounded pixel sample of the
+same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pixel·reflection-node evals/s"
+UNIT = "evals/s"
+WORKLOAD = "helix_2000atoms_hex20x20x28_dmin2.0_voigt3-2deg_g2pct_nodes64_det1024"
+# Algorithmic FP32 operations per in-support evaluation (Hosemann lineshape),
+# counting an FMA as two: t_i = tau_i - sigma_i (3); sin^2(pi t) by a degree-6
+# polynomial in t^2 (3 x 14); Hosemann denominators (3 x 2); their product (2);
+# reciprocal (1); weight (1); accumulation (1).
+FLOPS_PER_EVAL = 55
+SF_FLOPS_PER_TERM = 30
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """148 SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or "0"
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", dev, "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [r[0] for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[2][k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+def dist_init(n_gpus):
+    import torch
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(problem, budget_s=12.0, n_pix=None, seed=5):
+    """Time the FP64 oracle (as it stands) on a bounded pixel sample."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    oracle.build()
+    hkl = oracle.reflections(problem.cell, problem.d_min, problem.d_max)
+    M = oracle.intensities_M(problem, hkl)
+    rng = np.random.default_rng(seed)
+    n = problem.geom.n_x
+    # pixels from the central half of the detector, where reflections are dense
+    probe = np.stack([rng.integers(n // 4, 3 * n // 4, 2), rng.integers(n // 4, 3 * n // 4, 2)], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    oracle.pattern(problem, hkl, M, probe)
+    per_px = max((time.perf_counter() - t0) / len(probe), 1e-4)
+    k = n_pix or int(max(4, min(512, budget_s / per_px)))
+    pix = np.stack([rng.integers(n // 4, 3 * n // 4, k), rng.integers(n // 4, 3 * n // 4, k)], 1).astype(np.int32)
+    t0 = time.perf_counter()
+    _, E = oracle.pattern(problem, hkl, M, pix)
+    dt = time.perf_counter() - t0
+    evals = int(E[:, 0].sum())
+    return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d seeded pixels of the central half of the 1024^2 detector, full reflection list "
+                      "(%d in-support evals in %.1f s)" % (k, evals, dt)}, dt
+
+
+def run_reference(args):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from paper_2608_23245_b300 import workloads as W
+    p = W.config1()
+    per_step_budget = max(2.0, 100.0 / max(1, args.steps + args.warmup))
+    times, evals = [], 0
+    cb = None
+    for s in range(args.warmup + args.steps):
+        cb, dt = cpu_baseline(p, budget_s=per_step_budget, seed=100 + s)
+        if s >= args.warmup:
+            times.append(dt)
+            evals += int(cb["sample"].split("(")[1].split(" ")[0])
+    total = sum(times)
+    value = evals / total
+    cb["value"] = value
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "pixel subset per step", "l2_flush": "n/a (CPU)"},
+            "impl": "reference", "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fdx", choices=["fdx", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2608_23245_b300 import _build, fdx, workloads as W
+    rank, world = dist_init(args.gpus)
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    dev = "cuda"
+    p = W.config1()
+    sim = fdx.Simulation(p, dev)
+    stream = torch.cuda.current_stream()
+    # evaluation count E (once, outside the timed region)
+    sim.forward()
+    E = int(sim.evals().to(torch.int64).sum().item())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        sim.structure_factors()
+        sim.pattern()
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # dominant kernel (the pattern launch) timed on its own stream position
+    pstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    os.makedirs(os.path.dirname(clocks_path), exist_ok=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(clocks_path) as cs:
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            starts[s].record(stream)
+            sim.structure_factors()
+            pstarts[s].record(stream)
+            sim.pattern()
+            ends[s].record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        wall = time.perf_counter() - t_wall
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    pat_ms = [pstarts[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = E * args.steps * world / total_s
+
+    # end to end through the C-ABI with host buffers: pinned host inputs copied
+    # in, image copied out, every step
+    host = {k: getattr(sim.atoms, k).cpu().pin_memory() for k in ("frac", "B", "occ", "elem", "ff")}
+    hkl_host = sim.hkl.cpu().pin_memory()
+    img_host = torch.empty_like(sim.image, device="cpu").pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in host.values()) + hkl_host.numel() * 4
+    d2h = img_host.numel() * 4
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        for k, t in host.items():
+            getattr(sim.atoms, k).copy_(t, non_blocking=True)
+        sim.hkl.copy_(hkl_host, non_blocking=True)
+        step()
+        img_host.copy_(sim.image, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
+    e2e_value = E * args.steps * world / e2e_s
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+    clocks = cs.summary()
+    peaks = _peaks()
+    pat_s = sum(pat_ms) / len(pat_ms) / 1e3
+    achieved = FLOPS_PER_EVAL * E / pat_s / 1e12
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "evals_per_step": E, "n_refl": int(sim.hkl.shape[0]), "n_atoms": p.atoms.n,
+                   "l2_flush": "512 MiB write between steps, outside the per-step events",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "basis": "%d algorithmic FP32 flops per in-support eval; peak = 148 SMs x 128 lanes x 2 x "
+                              "%.0f MHz (FP32 FMA pipe)" % (FLOPS_PER_EVAL, peaks.get("sm_max_mhz", 2032.0)),
+                     "pattern_ms": 1e3 * pat_s},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(p)
+        line["cpu_baseline"] = cb
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

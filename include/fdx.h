@@ -1,0 +1,185 @@
+/*
+ * fdx.h -- C-ABI of libfdx, the B300 (sm_103a) fiber-diffraction hot path.
+ *
+ * The library computes, on one GPU:
+ *   1. the reflection list of a cell (Sect. "Structure factors and reflection
+ *      list": every (h,k,l) != 0 with d_min <= d <= d_max);
+ *   2. structure factors by direct summation over atoms (Eq. structure_factor,
+ *      with the atomic form factor f(s) = sum_i a_i exp(-b_i s^2/4) + c and the
+ *      isotropic Debye-Waller factor exp(-B s^2/4), B = 8 pi^2 <u^2>, Sect.
+ *      "Paracrystalline disorder"), and per reflection M = |F|^2 P DW_axis with
+ *      the Hosemann intensity factor P of Eq. Ipara and the axis damping
+ *      D(S) = exp(-1/4 sum_i B_i (S . a^_i)^2);
+ *   3. the detector image: per pixel, the shell-quadrature sum of Eq.
+ *      direct_sum over the gnomonic nodes of Eq. gnomonic with the weights of
+ *      Eq. node_weight (Gaussian, Lorentzian or Voigt angular shape, Sect.
+ *      "Angular peak shapes"), the lattice factor of Eq. I_shape (sinc^2 with
+ *      N_eff of Eq. Neff) or of Eq. Z (Hosemann), evaluated at the pixel's
+ *      query point on the Ewald sphere, times the Lorentz factor of Eq.
+ *      lorentz.
+ *
+ * Conventions
+ *   - Units: lengths in Angstrom, reciprocal lengths in 1/Angstrom, angles in
+ *     radians; detector distance and pixel size in one common unit (mm).
+ *   - Cell frame (Sect. "Unit cell and reciprocal-space frame"): c along z,
+ *     b in the yz-plane; fiber and beam axes are given in that frame.
+ *   - Detector: pixel (i, j) has centre u = (i + 1/2 - n_x/2) p along
+ *     u^ = normalize(n x b), v = (j + 1/2 - n_y/2) p along v^ = b x u^;
+ *     image[j][i], row j along +v.  Tilt 0, beam centre at the detector centre.
+ *   - Ownership: every array is owned by the caller.  Device arrays must stay
+ *     valid until the work queued on `stream` has finished.  The library never
+ *     allocates device memory: scratch comes from the caller's `workspace`.
+ *     Host structs are read during the call only.
+ *   - Errors: every entry point validates its arguments on the host before it
+ *     queues any work and returns one of the FDX_* codes below; no C++
+ *     exception crosses the ABI.  After validation the calls are asynchronous
+ *     on `stream` (a cudaStream_t passed as void*; NULL = legacy default
+ *     stream), except fdx_reflections, which is synchronous.
+ *   - Determinism: no result is accumulated with atomics; two calls with the
+ *     same inputs produce bitwise identical outputs.
+ */
+#ifndef FDX_H
+#define FDX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define FDX_OK 0
+#define FDX_ERR_ARG (-1)       /* null pointer, non-positive size, NaN, bad enum */
+#define FDX_ERR_GEOMETRY (-2)  /* |beam . fiber| > 1e-3 (Sect. Experimental geometry), d_min <= 0, bad cell */
+#define FDX_ERR_WORKSPACE (-3) /* workspace too small or misaligned (256-byte alignment) */
+#define FDX_ERR_CUDA (-4)      /* a CUDA runtime call or kernel launch failed */
+#define FDX_ERR_CAPACITY (-5)  /* output capacity too small */
+#define FDX_ERR_TIMEOUT (-6)   /* reserved: bounded device wait expired */
+
+#define FDX_LINESHAPE_SINC 0     /* K = N sinc^2(N t), N = 1/beta, |t| <= min(K_z/N, 1/2) (Eq. I_shape) */
+#define FDX_LINESHAPE_HOSEMANN 1 /* K = beta/(beta^2 + (1-beta^2) sin^2(pi t)), |t| <= 1/2 (Eq. Z) */
+#define FDX_INTENSITY_NONE 0     /* P = 1 */
+#define FDX_INTENSITY_HOSEMANN 1 /* P = prod_i 2A_i/(1 + A_i^2), A_i = exp(-2 pi^2 g_i^2 h_i^2) (Eq. Ipara) */
+
+/* Unit cell: a, b, c in Angstrom; alpha, beta, gamma in radians. */
+typedef struct fdx_cell {
+    double a, b, c;
+    double alpha, beta, gamma;
+} fdx_cell;
+
+/* Atoms of one model.  All pointers are device pointers. */
+typedef struct fdx_atoms {
+    int32_t n_atoms;      /* >= 1 */
+    int32_t n_elem;       /* 1..64 element types */
+    const double *frac;   /* [n_atoms][3] fractional coordinates (any real value) */
+    const float *B;       /* [n_atoms] isotropic B (A^2) */
+    const float *occ;     /* [n_atoms] occupancy, or NULL for 1 (the paper sets 1) */
+    const uint8_t *elem;  /* [n_atoms] element index < n_elem (an index >= n_elem makes F NaN) */
+    const float *ff;      /* [n_elem][9] form factor a1..a4, b1..b4, c: f(s) = sum a_i exp(-b_i s^2/4) + c */
+} fdx_atoms;
+
+/* Disorder and quadrature parameters (ParacrystalSpec and simulate(), Sect.
+ * "Paracrystalline disorder and the simulation loop"). */
+typedef struct fdx_broadening {
+    double L[3];            /* crystallite size along a, b, c (A); N_base,i = L_i/|a_i| */
+    double g[3];            /* Hosemann g along a, b, c (>= 0) */
+    double B_axis[3];       /* axis damping B_a, B_b, B_c (A^2) */
+    int32_t lineshape;      /* FDX_LINESHAPE_* */
+    int32_t intensity_model;/* FDX_INTENSITY_* */
+    double sigma;           /* Gaussian orientation width (rad); gamma == 0 selects the Gaussian */
+    double gamma;           /* Lorentzian HWHM (rad); sigma < 1e-12 selects the Lorentzian */
+    double sigma_r;         /* radial shell width (1/A); enters as sigma_r sqrt(2 pi) */
+    double T;               /* patch half-extent in tangent units, > 0 */
+    int32_t n_nodes;        /* nodes per axis of the midpoint grid, 1..512 */
+    int32_t reserved;
+    double K_z;             /* sinc support in zeros (> 0) */
+} fdx_broadening;
+
+/* Experiment geometry (params_experiment, Sect. "Experimental geometry"). */
+typedef struct fdx_geometry {
+    double wavelength;      /* A */
+    double distance;        /* sample-detector distance */
+    double pixel;           /* pixel size, same unit as distance */
+    int32_t n_x, n_y;       /* detector size in pixels, 1..16384 each */
+    double fiber_axis[3];   /* fiber (rotation) axis, need not be unit */
+    double beam_axis[3];    /* incident beam direction, need not be unit */
+    double delta_L;         /* Lorentz regulariser delta of Eq. lorentz (1/A), > 0 */
+} fdx_geometry;
+
+/* One pattern problem. */
+typedef struct fdx_problem {
+    fdx_cell cell;
+    fdx_broadening br;
+    fdx_geometry geom;
+    int32_t n_refl;         /* >= 0 */
+    int32_t reserved;
+    const int32_t *hkl;     /* [n_refl][3] device */
+    const float *M;         /* [n_refl] device: M = |F|^2 P DW_axis */
+} fdx_problem;
+
+/*
+ * fdx_reflections -- reflection list (Sect. "Structure factors and reflection
+ * list").  Every (h,k,l) != (0,0,0) with d_min <= d <= d_max (d = 1/|D|,
+ * D = h a* + k b* + l c*, Eq. recip_basis), Friedel mates included, in
+ * lexicographic (h, k, l) order.  A reflection on the boundary within a
+ * relative 1e-12 of 1/d^2 is kept.  d_max <= 0 means no upper cut.
+ * Count/fill protocol: with capacity == 0 (hkl_out may be NULL) only *n_out
+ * is written.  hkl_out ([capacity][3]) may be host or device memory.
+ * Returns FDX_ERR_CAPACITY (and the needed count in *n_out) when capacity is
+ * too small.  Synchronous.
+ */
+int fdx_reflections(const fdx_cell *cell, double d_min, double d_max, int32_t capacity, int32_t *hkl_out,
+                    int32_t *n_out);
+
+/* Bytes of workspace fdx_structure_factors needs for this size. */
+size_t fdx_sf_workspace_size(int32_t n_atoms, int32_t n_refl);
+
+/*
+ * fdx_structure_factors -- Eq. structure_factor by direct summation:
+ *   F_hkl = sum_j occ_j f_{e_j}(s) exp(-B_j s^2/4) exp(2 pi i (h x_j + k y_j + l z_j)),
+ *   s = |D_hkl| = 1/d.
+ * F_out ([n_refl][2] device, re/im) and, when M_out is not NULL,
+ * M_out[r] = |F_r|^2 P_r DW_r (P and DW from `br`, which may be NULL for
+ * P = DW = 1).  FP32 arithmetic with exact 32-bit fixed-point phase
+ * reduction and compensated sums.  Asynchronous on `stream`.
+ */
+int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fdx_broadening *br, int32_t n_refl,
+                          const int32_t *hkl, float *F_out, float *M_out, void *workspace, size_t ws_bytes,
+                          void *stream);
+
+/* Bytes of workspace fdx_pattern / fdx_pattern_evals need for these problems. */
+size_t fdx_workspace_size(int32_t n_models, const fdx_problem *const *probs);
+
+/*
+ * fdx_pattern -- detector images.  For every pixel (R, Z from the Ewald
+ * construction, Eq. laue) and every reflection, the query point is the
+ * pixel's ring point in the reflection's meridional half-plane,
+ * p = Z n + R e_R(D), and
+ *   I_pix = L(R) sum_hkl M_hkl r0^2 sum_{k: |t_i| <= t_max,i} w_k prod_i K_i(t_i),
+ *   t_i = a_i . (p - s_k),  L(R) = delta_L / (R + delta_L),
+ * with s_k the gnomonic shell nodes (Eq. gnomonic) and w_k their weights
+ * (Eq. node_weight).  images[m] is [n_y][n_x] float (device).  Models are
+ * processed one after another on `stream`.  Asynchronous.
+ */
+int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const *images, void *workspace,
+                size_t ws_bytes, void *stream);
+
+/*
+ * fdx_pattern_evals -- the number of (reflection, node) terms inside the
+ * support for each pixel of one problem (the unit of the throughput metric),
+ * written to counts ([n_y][n_x] int32, device).  Asynchronous.
+ */
+int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream);
+
+/* Human-readable text for a return code (static storage). */
+const char *fdx_error_string(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fdx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDX_H */

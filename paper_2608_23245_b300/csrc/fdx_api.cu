@@ -1,0 +1,330 @@
+// C-ABI entry points of libfdx: argument validation on the host, workspace
+// carving, and kernel launches on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
+#include "fdx_internal.cuh"
+
+using namespace fdx;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
+
+int validate_cell(const fdx_cell *c) {
+    if (!c) return FDX_ERR_ARG;
+    const double v[6] = {c->a, c->b, c->c, c->alpha, c->beta, c->gamma};
+    for (double x : v)
+        if (!isfinite(x)) return FDX_ERR_ARG;
+    if (c->a <= 0 || c->b <= 0 || c->c <= 0) return FDX_ERR_GEOMETRY;
+    for (int k = 3; k < 6; ++k)
+        if (v[k] <= 0 || v[k] >= FDX_PI) return FDX_ERR_GEOMETRY;
+    // positive cell volume: 1 - cos^2 a - cos^2 b - cos^2 g + 2 cos a cos b cos g > 0
+    const double ca = cos(c->alpha), cb = cos(c->beta), cg = cos(c->gamma);
+    if (1 - ca * ca - cb * cb - cg * cg + 2 * ca * cb * cg <= 1e-12) return FDX_ERR_GEOMETRY;
+    return FDX_OK;
+}
+
+int validate_broadening(const fdx_broadening *b) {
+    if (!b) return FDX_ERR_ARG;
+    for (int i = 0; i < 3; ++i) {
+        if (!(b->L[i] > 0) || !isfinite(b->L[i])) return FDX_ERR_ARG;
+        if (!(b->g[i] >= 0) || !isfinite(b->g[i])) return FDX_ERR_ARG;
+        if (!isfinite(b->B_axis[i])) return FDX_ERR_ARG;
+    }
+    if (b->lineshape != FDX_LINESHAPE_SINC && b->lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
+    if (b->intensity_model != FDX_INTENSITY_NONE && b->intensity_model != FDX_INTENSITY_HOSEMANN) return FDX_ERR_ARG;
+    if (!(b->sigma >= 0) || !(b->gamma >= 0) || !isfinite(b->sigma) || !isfinite(b->gamma)) return FDX_ERR_ARG;
+    if (b->gamma == 0 && !(b->sigma > 0)) return FDX_ERR_ARG;  // no angular shape
+    if (!(b->sigma_r > 0) || !isfinite(b->sigma_r)) return FDX_ERR_ARG;
+    if (!(b->T > 0) || !isfinite(b->T)) return FDX_ERR_ARG;
+    if (b->n_nodes < 1 || b->n_nodes > 512) return FDX_ERR_ARG;
+    if (!(b->K_z > 0) || !isfinite(b->K_z)) return FDX_ERR_ARG;
+    return FDX_OK;
+}
+
+int validate_geometry(const fdx_geometry *g) {
+    if (!g) return FDX_ERR_ARG;
+    if (!(g->wavelength > 0) || !(g->distance > 0) || !(g->pixel > 0) || !(g->delta_L > 0)) return FDX_ERR_ARG;
+    if (!isfinite(g->wavelength) || !isfinite(g->distance) || !isfinite(g->pixel) || !isfinite(g->delta_L))
+        return FDX_ERR_ARG;
+    if (g->n_x < 1 || g->n_y < 1 || g->n_x > 16384 || g->n_y > 16384) return FDX_ERR_ARG;
+    if (!finite3(g->fiber_axis) || !finite3(g->beam_axis)) return FDX_ERR_ARG;
+    const double nf = sqrt(g->fiber_axis[0] * g->fiber_axis[0] + g->fiber_axis[1] * g->fiber_axis[1] +
+                           g->fiber_axis[2] * g->fiber_axis[2]);
+    const double nb = sqrt(g->beam_axis[0] * g->beam_axis[0] + g->beam_axis[1] * g->beam_axis[1] +
+                           g->beam_axis[2] * g->beam_axis[2]);
+    if (!(nf > 0) || !(nb > 0)) return FDX_ERR_ARG;
+    const double c = (g->fiber_axis[0] * g->beam_axis[0] + g->fiber_axis[1] * g->beam_axis[1] +
+                      g->fiber_axis[2] * g->beam_axis[2]) / (nf * nb);
+    if (fabs(c) > 1e-3) return FDX_ERR_GEOMETRY;  // Sect. Experimental geometry
+    return FDX_OK;
+}
+
+int validate_problem(const fdx_problem *p) {
+    if (!p) return FDX_ERR_ARG;
+    int rc = validate_cell(&p->cell);
+    if (rc) return rc;
+    if ((rc = validate_broadening(&p->br))) return rc;
+    if ((rc = validate_geometry(&p->geom))) return rc;
+    if (p->n_refl < 0) return FDX_ERR_ARG;
+    if (p->n_refl > 0 && (!p->hkl || !p->M)) return FDX_ERR_ARG;
+    return FDX_OK;
+}
+
+struct Layout {
+    size_t pixgeo, nodes, recs, reach, total;
+};
+
+Layout layout_for(const fdx_problem *p) {
+    Layout L;
+    size_t off = 0;
+    L.pixgeo = off;
+    off += align_up(sizeof(float4) * (size_t)p->geom.n_x * p->geom.n_y);
+    L.nodes = off;
+    off += align_up(2 * sizeof(float4) * (size_t)p->br.n_nodes * p->br.n_nodes);
+    L.recs = off;
+    off += align_up(sizeof(float) * REC_SIZE * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    L.reach = off;
+    off += align_up(sizeof(float4) * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    L.total = off;
+    return L;
+}
+
+void unit3(const double *v, double *o) {
+    const double n = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int q = 0; q < 3; ++q) o[q] = v[q] / n;
+}
+
+void cross3(const double *x, const double *y, double *z) {
+    z[0] = x[1] * y[2] - x[2] * y[1];
+    z[1] = x[2] * y[0] - x[0] * y[2];
+    z[2] = x[0] * y[1] - x[1] * y[0];
+}
+
+// Queue set-up kernels and the pattern kernel for one problem.
+int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, cudaStream_t st) {
+    const Layout L = layout_for(p);
+    double A[9], As[9];
+    cell_basis(p->cell, A, As);
+    double nh[3], bh[3], uh[3], vh[3];
+    unit3(p->geom.fiber_axis, nh);
+    unit3(p->geom.beam_axis, bh);
+    cross3(nh, bh, uh);
+    unit3(uh, uh);
+    cross3(bh, uh, vh);
+
+    PixelParams pp;
+    pp.nx = p->geom.n_x, pp.ny = p->geom.n_y;
+    pp.lambda = p->geom.wavelength, pp.dist = p->geom.distance, pp.pix = p->geom.pixel;
+    for (int q = 0; q < 3; ++q) pp.bh[q] = bh[q], pp.uh[q] = uh[q], pp.vh[q] = vh[q], pp.nh[q] = nh[q];
+    pp.pixgeo = reinterpret_cast<float4 *>(ws + L.pixgeo);
+    if (launch_pixel_geometry(pp, st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    NodeParams np;
+    np.n = p->br.n_nodes, np.T = p->br.T, np.h = 2.0 * p->br.T / p->br.n_nodes;
+    np.sigma = p->br.sigma, np.gamma = p->br.gamma, np.sigma_r = p->br.sigma_r;
+    np.nodes = reinterpret_cast<float4 *>(ws + L.nodes);
+    if (launch_nodes(np, weideman_coeffs(), st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    ReflSetupParams rp;
+    memcpy(rp.A, A, sizeof A);
+    memcpy(rp.As, As, sizeof As);
+    for (int q = 0; q < 3; ++q) {
+        rp.nh[q] = nh[q], rp.bh[q] = bh[q];
+        rp.alen[q] = sqrt(A[3 * q] * A[3 * q] + A[3 * q + 1] * A[3 * q + 1] + A[3 * q + 2] * A[3 * q + 2]);
+        rp.L[q] = p->br.L[q], rp.g[q] = p->br.g[q], rp.Bax[q] = p->br.B_axis[q];
+    }
+    rp.T = p->br.T, rp.K_z = p->br.K_z;
+    rp.lineshape = p->br.lineshape, rp.intensity_model = p->br.intensity_model, rp.n_refl = p->n_refl, rp.pad = 0;
+    rp.hkl = p->hkl, rp.M = p->M;
+    rp.recs = reinterpret_cast<float *>(ws + L.recs);
+    rp.reach = reinterpret_cast<float4 *>(ws + L.reach);
+    if (launch_refl_setup(rp, st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    PatternParams P;
+    P.nx = p->geom.n_x, P.ny = p->geom.n_y, P.n_refl = p->n_refl, P.n_nodes = p->br.n_nodes;
+    P.T = (float)p->br.T;
+    P.inv_h = (float)(p->br.n_nodes / (2.0 * p->br.T));
+    for (int i = 0; i < 3; ++i) P.AZ[i] = (float)(A[3 * i] * nh[0] + A[3 * i + 1] * nh[1] + A[3 * i + 2] * nh[2]);
+    P.delta_L = p->geom.delta_L;
+    P.pixgeo = pp.pixgeo;
+    P.reach = rp.reach;
+    P.recs = rp.recs;
+    P.nodes = np.nodes;
+    P.image = image;
+    P.counts = counts;
+    if (launch_pattern(P, p->br.lineshape, counts != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
+    return FDX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fdx_version(void) { return 100; }
+
+const char *fdx_error_string(int code) {
+    switch (code) {
+        case FDX_OK: return "ok";
+        case FDX_ERR_ARG: return "invalid argument";
+        case FDX_ERR_GEOMETRY: return "invalid geometry (cell, resolution, or beam not orthogonal to fiber)";
+        case FDX_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+        case FDX_ERR_CUDA: return "CUDA runtime error";
+        case FDX_ERR_CAPACITY: return "output capacity too small";
+        case FDX_ERR_TIMEOUT: return "bounded device wait expired";
+        default: return "unknown error";
+    }
+}
+
+int fdx_reflections(const fdx_cell *cell, double d_min, double d_max, int32_t capacity, int32_t *hkl_out,
+                    int32_t *n_out) {
+    int rc = validate_cell(cell);
+    if (rc) return rc;
+    if (!n_out || capacity < 0 || (capacity > 0 && !hkl_out)) return FDX_ERR_ARG;
+    if (!(d_min > 0) || !isfinite(d_min) || !isfinite(d_max)) return FDX_ERR_GEOMETRY;
+    double A[9], As[9];
+    cell_basis(*cell, A, As);
+    // |h| <= |D| |a| <= |a| / d_min
+    const int H = (int)ceil(cell->a / d_min), K = (int)ceil(cell->b / d_min), Lm = (int)ceil(cell->c / d_min);
+    const double s2max = (1.0 + 1e-12) / (d_min * d_min);
+    const double s2min = d_max > 0 ? (1.0 - 1e-12) / (d_max * d_max) : 0.0;
+    std::vector<int32_t> out;
+    for (int h = -H; h <= H; ++h)
+        for (int k = -K; k <= K; ++k)
+            for (int l = -Lm; l <= Lm; ++l) {
+                if (!h && !k && !l) continue;
+                double D[3];
+                for (int q = 0; q < 3; ++q) D[q] = h * As[q] + k * As[3 + q] + l * As[6 + q];
+                const double s2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+                if (s2 > s2max || s2 < s2min) continue;
+                out.push_back(h), out.push_back(k), out.push_back(l);
+            }
+    const int32_t n = (int32_t)(out.size() / 3);
+    *n_out = n;
+    if (capacity == 0) return FDX_OK;
+    if (capacity < n) return FDX_ERR_CAPACITY;
+    if (n == 0) return FDX_OK;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, hkl_out);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        attr.type = cudaMemoryTypeUnregistered;
+    }
+    if (attr.type == cudaMemoryTypeDevice) {
+        if (cudaMemcpy(hkl_out, out.data(), out.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            return FDX_ERR_CUDA;
+    } else {
+        memcpy(hkl_out, out.data(), out.size() * sizeof(int32_t));
+    }
+    return FDX_OK;
+}
+
+size_t fdx_sf_workspace_size(int32_t n_atoms, int32_t n_refl) {
+    if (n_atoms < 1 || n_refl < 0) return 0;
+    size_t off = 0;
+    off += align_up(sizeof(uint4) * (size_t)n_atoms);
+    off += align_up(sizeof(float2) * (size_t)n_atoms);
+    // at most 64 splits of the atom list
+    off += align_up(sizeof(float4) * (size_t)64 * (size_t)(n_refl > 0 ? n_refl : 1));
+    return off;
+}
+
+int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fdx_broadening *br, int32_t n_refl,
+                          const int32_t *hkl, float *F_out, float *M_out, void *workspace, size_t ws_bytes,
+                          void *stream) {
+    int rc = validate_cell(cell);
+    if (rc) return rc;
+    if (!atoms || atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
+    if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
+    if (n_refl < 0) return FDX_ERR_ARG;
+    if (n_refl > 0 && (!hkl || !F_out)) return FDX_ERR_ARG;
+    if (br && (rc = validate_broadening(br))) return rc;
+    if (n_refl == 0) return FDX_OK;
+    const size_t need = fdx_sf_workspace_size(atoms->n_atoms, n_refl);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+
+    SFParams p;
+    memset(&p, 0, sizeof p);
+    double A[9], As[9];
+    cell_basis(*cell, A, As);
+    memcpy(p.As, As, sizeof As);
+    p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
+    // Split the atom list so that the grid has >= ~4 CTAs per SM, keeping >= 512 atoms per split.
+    const int refl_blocks = (n_refl + 127) / 128;
+    int n_split = (600 + refl_blocks - 1) / refl_blocks;
+    n_split = n_split < 1 ? 1 : (n_split > 64 ? 64 : n_split);
+    const int max_by_atoms = (atoms->n_atoms + 511) / 512;
+    if (n_split > max_by_atoms) n_split = max_by_atoms;
+    if (n_split < 1) n_split = 1;
+    int per = (atoms->n_atoms + n_split - 1) / n_split;
+    per = (per + 255) / 256 * 256;
+    n_split = (atoms->n_atoms + per - 1) / per;
+    p.n_split = n_split, p.atoms_per_split = per;
+    p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
+    char *ws = static_cast<char *>(workspace);
+    size_t off = 0;
+    p.atoms_q = reinterpret_cast<uint4 *>(ws + off);
+    off += align_up(sizeof(uint4) * (size_t)atoms->n_atoms);
+    p.atoms_w = reinterpret_cast<float2 *>(ws + off);
+    off += align_up(sizeof(float2) * (size_t)atoms->n_atoms);
+    p.partial = reinterpret_cast<float4 *>(ws + off);
+    p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;
+    p.has_br = br ? 1 : 0;
+    if (br) {
+        p.intensity_model = br->intensity_model;
+        for (int i = 0; i < 3; ++i) {
+            p.g[i] = br->g[i], p.Bax[i] = br->B_axis[i];
+            p.alen[i] = sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]);
+        }
+    }
+    if (launch_structure_factors(p, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FDX_ERR_CUDA;
+    return FDX_OK;
+}
+
+size_t fdx_workspace_size(int32_t n_models, const fdx_problem *const *probs) {
+    if (n_models < 1 || !probs) return 0;
+    size_t best = 0;
+    for (int m = 0; m < n_models; ++m) {
+        if (!probs[m]) return 0;
+        const size_t t = layout_for(probs[m]).total;
+        best = t > best ? t : best;
+    }
+    return best;
+}
+
+int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const *images, void *workspace,
+                size_t ws_bytes, void *stream) {
+    if (n_models < 1 || !probs || !images) return FDX_ERR_ARG;
+    for (int m = 0; m < n_models; ++m) {
+        int rc = validate_problem(probs[m]);
+        if (rc) return rc;
+        if (!images[m]) return FDX_ERR_ARG;
+    }
+    const size_t need = fdx_workspace_size(n_models, probs);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (int m = 0; m < n_models; ++m) {
+        int rc = run_pattern(probs[m], images[m], nullptr, static_cast<char *>(workspace), st);
+        if (rc) return rc;
+    }
+    return FDX_OK;
+}
+
+int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream) {
+    int rc = validate_problem(prob);
+    if (rc) return rc;
+    if (!counts) return FDX_ERR_ARG;
+    const fdx_problem *pp[1] = {prob};
+    const size_t need = fdx_workspace_size(1, pp);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    return run_pattern(prob, nullptr, counts, static_cast<char *>(workspace), static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

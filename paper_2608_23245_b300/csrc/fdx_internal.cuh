@@ -1,0 +1,186 @@
+// Internal declarations shared by the libfdx CUDA sources (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fdx.h"
+#include "poly_coeffs.cuh"
+
+#define FDX_FULL_MASK 0xffffffffu
+#define FDX_PI 3.14159265358979323846
+
+namespace fdx {
+
+// ---------------------------------------------------------------------------
+// Float-float ("double-float") arithmetic: a value is hi + lo with |lo| <=
+// ulp(hi)/2.  Error-free transformations after Knuth (TwoSum), Dekker
+// (FastTwoSum) and the FMA form of TwoProduct (Ogita, Rump, Oishi 2005).
+// B300 runs FP64 at a small fraction of its FP32 rate, so the places that need
+// more than 24 bits use these pairs instead.
+// ---------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b) {  // requires |a| >= |b| or a == 0
+    float s = a + b;
+    float e = b - (s - a);
+    return {s, e};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+    ff s = two_sum(a.hi, b.hi);
+    float e = s.lo + (a.lo + b.lo);
+    return fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+    ff s = two_sum(a.hi, b);
+    return fast_two_sum(s.hi, s.lo + a.lo);
+}
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+    float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff{-b.hi, -b.lo}); }
+
+__host__ __device__ __forceinline__ void split_double(double x, float &hi, float &lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+// Horner evaluation with coefficients in increasing order.
+template <int N>
+__device__ __forceinline__ float horner(const float (&c)[N], float x) {
+    float acc = c[N - 1];
+#pragma unroll
+    for (int k = N - 2; k >= 0; --k) acc = fmaf(acc, x, c[k]);
+    return acc;
+}
+
+// sin^2(pi t) for |t| <= 1/2: t^2 Q(t^2), Q fitted by fit_poly.py.
+__device__ __forceinline__ float sinpi_sq(float t) {
+    const float Q[7] = FDX_SINPI2_C;
+    float x = t * t;
+    return x * horner(Q, x);
+}
+
+// ---------------------------------------------------------------------------
+// Per-reflection record of the pattern kernel (64 floats, 256 B), written by
+// the reflection set-up kernel in FP64 and rounded once.
+// Local frame: (S^, e1, e2) with e1 = normalize(n x S^) (or b x S^ on the
+// axis), e2 = S^ x e1; e_R is the unit radial direction of D (e1 on the
+// axis).  All "/r0" quantities are in units of r0 = |D|.
+// ---------------------------------------------------------------------------
+enum RecField {
+    REC_RD = 0,    // R_D hi, lo
+    REC_ZD = 2,    // Z_D hi, lo
+    REC_NFR = 4,   // n . (S^, e1, e2) / r0, hi[3] then lo[3]
+    REC_EFR = 10,  // e_R . (S^, e1, e2) / r0, hi[3] then lo[3]
+    REC_AR = 16,   // a_i . e_R  (i = a, b, c)
+    REC_H = 19,    // h_i as float (exact)
+    REC_E1 = 22,   // r0 a_i . e1
+    REC_E2 = 25,   // r0 a_i . e2
+    REC_CR = 28,   // 4 box corners sum_i (+-) tmax_i a*_i in the local frame, / r0 (4 x 3)
+    REC_LA = 40,   // Hosemann: beta_i^2;  sinc: N_i
+    REC_LB = 43,   // Hosemann: 1 - beta_i^2
+    REC_TM = 46,   // support half-widths tmax_i
+    REC_FR = 49,   // pair factor: Hosemann M r0^2 prod beta_i; sinc M r0^2 prod N_i / pi^6
+    REC_SIZE = 64
+};
+
+struct PatternParams {
+    int nx, ny, n_refl, n_nodes;
+    float T, inv_h;       // grid half-extent, 1 / node spacing
+    float AZ[3];          // a_i . n (cell constants)
+    double delta_L;
+    const float4 *pixgeo; // [ny*nx] (R hi, R lo, Z hi, Z lo)
+    const float4 *reach;  // [n_refl] (r0, rho_B, psi_D, dpsi)
+    const float *recs;    // [n_refl][REC_SIZE]
+    const float4 *nodes;  // [n*n][2]: (cm1 hi, cm1 lo, cd1 hi, cd1 lo), (cd2 hi, cd2 lo, w, 0)
+    float *image;         // [ny][nx]
+    int32_t *counts;      // [ny][nx] (count mode)
+};
+
+struct ReflSetupParams {
+    double A[9], As[9];   // real basis rows a, b, c and reciprocal rows a*, b*, c*
+    double nh[3], bh[3];  // unit fiber and beam axes
+    double alen[3];       // |a_i|
+    double L[3], g[3], Bax[3];
+    double T, K_z;
+    int lineshape, intensity_model, n_refl, pad;
+    const int32_t *hkl;
+    const float *M;       // may be null (then M = 1)
+    float *recs;
+    float4 *reach;
+};
+
+struct NodeParams {
+    int n;
+    double T, h, sigma, gamma, sigma_r;
+    float4 *nodes;
+};
+
+struct PixelParams {
+    int nx, ny;
+    double lambda, dist, pix;
+    double bh[3], uh[3], vh[3], nh[3];
+    float4 *pixgeo;
+};
+
+// Weideman (1994) rational approximation of the Faddeeva function,
+// w(z) ~ 2 p(Z) / (L - i z)^2 + 1 / (sqrt(pi) (L - i z)), Z = (L + i z)/(L - i z),
+// for Im z >= 0; coefficients computed once on the host (fdx_setup.cu).
+#define FDX_WEIDEMAN_N 40
+struct WeidemanCoeffs {
+    double a[FDX_WEIDEMAN_N];  // a_1 .. a_N
+    double L;
+};
+
+// Host helpers (fdx_setup.cu)
+void cell_basis(const fdx_cell &c, double A[9], double As[9]);
+const WeidemanCoeffs &weideman_coeffs();
+
+// Launchers
+cudaError_t launch_pixel_geometry(const PixelParams &p, cudaStream_t s);
+cudaError_t launch_nodes(const NodeParams &p, const WeidemanCoeffs &wc, cudaStream_t s);
+cudaError_t launch_refl_setup(const ReflSetupParams &p, cudaStream_t s);
+cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s);
+
+struct SFParams {
+    int n_atoms, n_elem, n_refl, n_split, atoms_per_split;
+    double As[9];
+    const double *frac;
+    const float *B, *occ, *ff;
+    const uint8_t *elem;
+    uint4 *atoms_q;        // packed: X, Y, Z (fixed point), elem
+    float2 *atoms_w;       // packed: Bq = -B log2(e)/4, log2(occ)
+    const int32_t *hkl;
+    float4 *partial;       // [n_split][n_refl] (re hi, re lo, im hi, im lo)
+    float *F_out, *M_out;
+    int has_br, intensity_model;
+    double g[3], Bax[3], alen[3];
+};
+
+cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);
+
+}  // namespace fdx

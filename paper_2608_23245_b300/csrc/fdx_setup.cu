@@ -1,0 +1,264 @@
+// Set-up kernels of the pattern path: detector pixel geometry, shell-node
+// table with angular weights, and per-reflection records.  All three run in
+// FP64 once per problem and round their results to float or float-float
+// pairs, so the hot loop can stay in FP32.
+#include <math.h>
+#include <mutex>
+
+#include "fdx_internal.cuh"
+
+namespace fdx {
+
+// ---------------------------------------------------------------------------
+// Cell -> real and reciprocal basis (Eq. recip_basis), in the frame of Sect.
+// "Unit cell and reciprocal-space frame": c along z, b in the yz-plane.
+// ---------------------------------------------------------------------------
+void cell_basis(const fdx_cell &c, double A[9], double As[9]) {
+    const double ca = cos(c.alpha), cb = cos(c.beta), cg = cos(c.gamma), sa = sin(c.alpha);
+    double a[3], b[3], cc[3];
+    cc[0] = 0.0, cc[1] = 0.0, cc[2] = c.c;
+    b[0] = 0.0, b[1] = c.b * sa, b[2] = c.b * ca;
+    a[2] = c.a * cb;
+    a[1] = c.a * (cg - ca * cb) / sa;
+    a[0] = sqrt(fmax(0.0, c.a * c.a - a[1] * a[1] - a[2] * a[2]));
+    auto cross = [](const double *x, const double *y, double *z) {
+        z[0] = x[1] * y[2] - x[2] * y[1];
+        z[1] = x[2] * y[0] - x[0] * y[2];
+        z[2] = x[0] * y[1] - x[1] * y[0];
+    };
+    double bc[3], ca_[3], ab[3];
+    cross(b, cc, bc);
+    cross(cc, a, ca_);
+    cross(a, b, ab);
+    const double V = a[0] * bc[0] + a[1] * bc[1] + a[2] * bc[2];
+    for (int k = 0; k < 3; ++k) {
+        A[k] = a[k], A[3 + k] = b[k], A[6 + k] = cc[k];
+        As[k] = bc[k] / V, As[3 + k] = ca_[k] / V, As[6 + k] = ab[k] / V;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weideman (1994, SIAM J. Numer. Anal. 31, 1497) coefficients:
+//   a_n = (1/2M) sum_{k=-M}^{M-1} f(theta_k) cos(n theta_k),
+//   theta_k = k pi / M, f(theta) = exp(-t^2) (L^2 + t^2), t = L tan(theta/2),
+//   M = 2N, L = sqrt(N / sqrt 2).   (f(-pi) = 0.)
+// ---------------------------------------------------------------------------
+const WeidemanCoeffs &weideman_coeffs() {
+    static WeidemanCoeffs wc;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const int N = FDX_WEIDEMAN_N, M = 2 * N;
+        const double L = sqrt(N / sqrt(2.0));
+        wc.L = L;
+        for (int n = 1; n <= N; ++n) {
+            double s = 0.0;
+            for (int k = -M + 1; k <= M - 1; ++k) {
+                const double th = k * FDX_PI / M;
+                const double t = L * tan(0.5 * th);
+                s += exp(-t * t) * (L * L + t * t) * cos(n * th);
+            }
+            wc.a[n - 1] = s / (2.0 * M);
+        }
+    });
+    return wc;
+}
+
+__device__ double faddeeva_re(double x, double y, const WeidemanCoeffs &wc) {
+    // w(z) for z = x + i y, y >= 0.  L - i z = (L + y) - i x ; L + i z = (L - y) + i x.
+    const double L = wc.L;
+    const double dr = L + y, di = -x;          // den = L - i z
+    const double nr = L - y, ni = x;           // num = L + i z
+    const double dd = dr * dr + di * di;
+    const double Zr = (nr * dr + ni * di) / dd, Zi = (ni * dr - nr * di) / dd;
+    double pr = wc.a[FDX_WEIDEMAN_N - 1], pi = 0.0;
+    for (int k = FDX_WEIDEMAN_N - 2; k >= 0; --k) {
+        const double tr = pr * Zr - pi * Zi + wc.a[k];
+        pi = pr * Zi + pi * Zr;
+        pr = tr;
+    }
+    // 2 p / den^2 + 1 / (sqrt(pi) den)
+    const double d2r = dr * dr - di * di, d2i = 2.0 * dr * di;
+    const double d2d = d2r * d2r + d2i * d2i;
+    const double t1r = 2.0 * (pr * d2r + pi * d2i) / d2d;
+    const double t2r = dr / (dd * sqrt(FDX_PI));
+    return t1r + t2r;
+}
+
+// Angular shape g(Delta; sigma, gamma), g(0) = 1 (Sect. "Angular peak shapes").
+__device__ double angular_shape(double D, double sigma, double gamma, const WeidemanCoeffs &wc) {
+    if (gamma == 0.0) return exp(-D * D / (2.0 * sigma * sigma));
+    if (sigma < 1e-12) return gamma * gamma / (D * D + gamma * gamma);
+    const double s = 1.0 / (sigma * sqrt(2.0));
+    return faddeeva_re(D * s, gamma * s, wc) / faddeeva_re(0.0, gamma * s, wc);
+}
+
+// ---------------------------------------------------------------------------
+// Pixel geometry: pixel -> S on the Ewald sphere (Eq. laue) -> (R, Z).
+// S = r/(lambda |r|) - b/lambda with r = SF b + u u^ + v v^.  SF/|r| - 1 is
+// written as -(u^2+v^2)/(|r|(|r|+SF)) to avoid cancellation near the beam.
+// ---------------------------------------------------------------------------
+__global__ void pixel_geometry_kernel(PixelParams p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= p.nx) return;
+    const double u = (i + 0.5 - 0.5 * p.nx) * p.pix;
+    const double v = (j + 0.5 - 0.5 * p.ny) * p.pix;
+    const double rho2 = u * u + v * v;
+    const double rn = sqrt(p.dist * p.dist + rho2);
+    const double fb = -rho2 / (rn * (rn + p.dist));
+    double S[3];
+    for (int q = 0; q < 3; ++q) S[q] = (fb * p.bh[q] + (u * p.uh[q] + v * p.vh[q]) / rn) / p.lambda;
+    const double Z = S[0] * p.nh[0] + S[1] * p.nh[1] + S[2] * p.nh[2];
+    double pr[3];
+    for (int q = 0; q < 3; ++q) pr[q] = S[q] - Z * p.nh[q];
+    const double R = sqrt(pr[0] * pr[0] + pr[1] * pr[1] + pr[2] * pr[2]);
+    float4 o;
+    split_double(R, o.x, o.y);
+    split_double(Z, o.z, o.w);
+    p.pixgeo[(size_t)j * p.nx + i] = o;
+}
+
+// ---------------------------------------------------------------------------
+// Shell nodes (Eq. gnomonic) on the n x n midpoint grid d = -T + (j + 1/2) h
+// and weights (Eq. node_weight):
+//   w = sigma_r sqrt(2 pi) g(Delta) (1 + d1^2 + d2^2)^(-3/2) h^2,
+//   Delta = arccos((1 + d^2)^(-1/2)) = atan |d|.
+// Stored: c - 1, c d1, c d2 as float-float (c = (1 + d^2)^(-1/2)) and w.
+// c - 1 = -rho^2 / (q (1 + q)), q = sqrt(1 + rho^2), without cancellation.
+// ---------------------------------------------------------------------------
+__global__ void nodes_kernel(NodeParams p, WeidemanCoeffs wc) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (m >= p.n) return;
+    const double d1 = -p.T + (j + 0.5) * p.h, d2 = -p.T + (m + 0.5) * p.h;
+    const double rho2 = d1 * d1 + d2 * d2;
+    const double q = sqrt(1.0 + rho2), c = 1.0 / q;
+    const double cm1 = -rho2 / (q * (1.0 + q));
+    const double Delta = atan(sqrt(rho2));
+    const double g = angular_shape(Delta, p.sigma, p.gamma, wc);
+    const double w = p.sigma_r * sqrt(2.0 * FDX_PI) * g * c * c * c * p.h * p.h;
+    float4 a, b;
+    split_double(cm1, a.x, a.y);
+    split_double(d1 * c, a.z, a.w);
+    split_double(d2 * c, b.x, b.y);
+    b.z = (float)w;
+    b.w = 0.0f;
+    const size_t k = (size_t)j * p.n + m;
+    p.nodes[2 * k] = a;
+    p.nodes[2 * k + 1] = b;
+}
+
+// ---------------------------------------------------------------------------
+// Per-reflection record (FP64 -> rounded once), see RecField.
+// Disorder scalars (Eqs. Ah, breadth, Neff):  x_i = pi^2 g_i^2 h_i^2,
+//   (1 - A)/(1 + A) = tanh x_i,  beta_i = min(1, |a_i|/L_i + tanh x_i).
+// Reach (for the candidate test): a pixel can see reflection D only if
+// | |p| - r0 | <= rho_B and its polar angle is within
+//   dpsi = atan(T sqrt 2) + asin(rho_B / r0)
+// of D's, rho_B being the circumradius of the support box.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dot3(const double *x, const double *y) {
+    return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+}
+
+__global__ void refl_setup_kernel(ReflSetupParams p) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.n_refl) return;
+    const int hk[3] = {p.hkl[3 * r], p.hkl[3 * r + 1], p.hkl[3 * r + 2]};
+    double D[3];
+    for (int q = 0; q < 3; ++q) D[q] = hk[0] * p.As[q] + hk[1] * p.As[3 + q] + hk[2] * p.As[6 + q];
+    const double r0 = sqrt(dot3(D, D));
+    double Sh[3] = {D[0] / r0, D[1] / r0, D[2] / r0};
+    double t[3] = {p.nh[1] * Sh[2] - p.nh[2] * Sh[1], p.nh[2] * Sh[0] - p.nh[0] * Sh[2],
+                   p.nh[0] * Sh[1] - p.nh[1] * Sh[0]};
+    double tn = sqrt(dot3(t, t));
+    if (tn < 1e-12) {
+        t[0] = p.bh[1] * Sh[2] - p.bh[2] * Sh[1];
+        t[1] = p.bh[2] * Sh[0] - p.bh[0] * Sh[2];
+        t[2] = p.bh[0] * Sh[1] - p.bh[1] * Sh[0];
+        tn = sqrt(dot3(t, t));
+    }
+    const double e1[3] = {t[0] / tn, t[1] / tn, t[2] / tn};
+    const double e2[3] = {Sh[1] * e1[2] - Sh[2] * e1[1], Sh[2] * e1[0] - Sh[0] * e1[2],
+                          Sh[0] * e1[1] - Sh[1] * e1[0]};
+    const double ZD = dot3(D, p.nh);
+    double perp[3] = {D[0] - ZD * p.nh[0], D[1] - ZD * p.nh[1], D[2] - ZD * p.nh[2]};
+    const double RD = sqrt(dot3(perp, perp));
+    double eR[3];
+    if (RD < 1e-12 * r0) {
+        for (int q = 0; q < 3; ++q) eR[q] = e1[q];
+    } else {
+        for (int q = 0; q < 3; ++q) eR[q] = perp[q] / RD;
+    }
+    float *o = p.recs + (size_t)r * REC_SIZE;
+    split_double(RD, o[REC_RD], o[REC_RD + 1]);
+    split_double(ZD, o[REC_ZD], o[REC_ZD + 1]);
+    const double *frame[3] = {Sh, e1, e2};
+    for (int q = 0; q < 3; ++q) {
+        split_double(dot3(p.nh, frame[q]) / r0, o[REC_NFR + q], o[REC_NFR + 3 + q]);
+        split_double(dot3(eR, frame[q]) / r0, o[REC_EFR + q], o[REC_EFR + 3 + q]);
+    }
+    double beta[3], tm[3];
+    for (int i = 0; i < 3; ++i) {
+        const double *ai = p.A + 3 * i;
+        o[REC_AR + i] = (float)dot3(ai, eR);
+        o[REC_H + i] = (float)hk[i];
+        o[REC_E1 + i] = (float)(r0 * dot3(ai, e1));
+        o[REC_E2 + i] = (float)(r0 * dot3(ai, e2));
+        const double x = FDX_PI * FDX_PI * p.g[i] * p.g[i] * (double)hk[i] * hk[i];
+        const double b = p.alen[i] / p.L[i] + tanh(x);
+        beta[i] = b < 1.0 ? b : 1.0;
+        if (p.lineshape == FDX_LINESHAPE_HOSEMANN) {
+            tm[i] = 0.5;
+            o[REC_LA + i] = (float)(beta[i] * beta[i]);
+            o[REC_LB + i] = (float)(1.0 - beta[i] * beta[i]);
+        } else {
+            tm[i] = fmin(p.K_z * beta[i], 0.5);
+            o[REC_LA + i] = (float)(1.0 / beta[i]);
+            o[REC_LB + i] = 0.0f;
+        }
+        o[REC_TM + i] = (float)tm[i];
+    }
+    double rhoB = 0.0;
+    for (int v = 0; v < 4; ++v) {
+        const double sb = (v & 1) ? -1.0 : 1.0, sc = (v & 2) ? -1.0 : 1.0;
+        double C[3];
+        for (int q = 0; q < 3; ++q) C[q] = tm[0] * p.As[q] + sb * tm[1] * p.As[3 + q] + sc * tm[2] * p.As[6 + q];
+        rhoB = fmax(rhoB, sqrt(dot3(C, C)));
+        for (int q = 0; q < 3; ++q) o[REC_CR + 3 * v + q] = (float)(dot3(C, frame[q]) / r0);
+    }
+    const double M = p.M ? (double)p.M[r] : 1.0;
+    double fr = M * r0 * r0;
+    if (p.lineshape == FDX_LINESHAPE_HOSEMANN) {
+        fr *= beta[0] * beta[1] * beta[2];
+    } else {
+        const double pi2 = FDX_PI * FDX_PI;
+        fr *= (1.0 / beta[0]) * (1.0 / beta[1]) * (1.0 / beta[2]) / (pi2 * pi2 * pi2);
+    }
+    o[REC_FR] = (float)fr;
+    for (int k = REC_FR + 1; k < REC_SIZE; ++k) o[k] = 0.0f;
+    const double psiD = atan2(RD, ZD);
+    const double dpsi = atan(p.T * sqrt(2.0)) + (rhoB < r0 ? asin(rhoB / r0) : FDX_PI);
+    p.reach[r] = make_float4((float)r0, (float)(rhoB * (1.0 + 1e-4) + 1e-6), (float)psiD,
+                             (float)(dpsi * (1.0 + 1e-4) + 1e-6));
+}
+
+cudaError_t launch_pixel_geometry(const PixelParams &p, cudaStream_t s) {
+    dim3 grid((p.nx + 127) / 128, p.ny);
+    pixel_geometry_kernel<<<grid, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nodes(const NodeParams &p, const WeidemanCoeffs &wc, cudaStream_t s) {
+    dim3 grid((p.n + 63) / 64, p.n);
+    nodes_kernel<<<grid, 64, 0, s>>>(p, wc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_refl_setup(const ReflSetupParams &p, cudaStream_t s) {
+    if (p.n_refl <= 0) return cudaSuccess;
+    refl_setup_kernel<<<(p.n_refl + 127) / 128, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace fdx

@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libfdx (include/fdx.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+PyTorch supplies device memory (tensors) and the stream; the structs below
+mirror the C structs field by field.  The functions carry the C entry points'
+names.  There is no CPU fallback: if libfdx.so is missing or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfdx.so")
+_lock = threading.Lock()
+_lib = None
+
+FDX_OK = 0
+LINESHAPE_SINC, LINESHAPE_HOSEMANN = 0, 1
+INTENSITY_NONE, INTENSITY_HOSEMANN = 0, 1
+
+
+class FdxError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__("%s failed: %s (%d)" % (where, error_string(code), code))
+        self.code = code
+
+
+class Cell(C.Structure):
+    _fields_ = [("a", C.c_double), ("b", C.c_double), ("c", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double)]
+
+
+class Atoms(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("n_elem", C.c_int32), ("frac", C.c_void_p), ("B", C.c_void_p),
+                ("occ", C.c_void_p), ("elem", C.c_void_p), ("ff", C.c_void_p)]
+
+
+class Broadening(C.Structure):
+    _fields_ = [("L", C.c_double * 3), ("g", C.c_double * 3), ("B_axis", C.c_double * 3),
+                ("lineshape", C.c_int32), ("intensity_model", C.c_int32),
+                ("sigma", C.c_double), ("gamma", C.c_double), ("sigma_r", C.c_double), ("T", C.c_double),
+                ("n_nodes", C.c_int32), ("reserved", C.c_int32), ("K_z", C.c_double)]
+
+
+class Geometry(C.Structure):
+    _fields_ = [("wavelength", C.c_double), ("distance", C.c_double), ("pixel", C.c_double),
+                ("n_x", C.c_int32), ("n_y", C.c_int32), ("fiber_axis", C.c_double * 3),
+                ("beam_axis", C.c_double * 3), ("delta_L", C.c_double)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("cell", Cell), ("br", Broadening), ("geom", Geometry), ("n_refl", C.c_int32),
+                ("reserved", C.c_int32), ("hkl", C.c_void_p), ("M", C.c_void_p)]
+
+
+def lib():
+    """Load libfdx.so (built in-tree by _build.py); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libfdx.so is not built (run `python -m paper_2608_23245_b300._build`)")
+            L = C.CDLL(LIB_PATH)
+            L.fdx_version.restype = C.c_int
+            L.fdx_error_string.restype = C.c_char_p
+            L.fdx_error_string.argtypes = [C.c_int]
+            L.fdx_reflections.argtypes = [C.POINTER(Cell), C.c_double, C.c_double, C.c_int32, C.c_void_p,
+                                          C.POINTER(C.c_int32)]
+            L.fdx_sf_workspace_size.restype = C.c_size_t
+            L.fdx_sf_workspace_size.argtypes = [C.c_int32, C.c_int32]
+            L.fdx_structure_factors.argtypes = [C.POINTER(Cell), C.POINTER(Atoms), C.POINTER(Broadening), C.c_int32,
+                                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                                C.c_void_p]
+            L.fdx_workspace_size.restype = C.c_size_t
+            L.fdx_workspace_size.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem))]
+            L.fdx_pattern.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem)), C.POINTER(C.c_void_p), C.c_void_p,
+                                      C.c_size_t, C.c_void_p]
+            L.fdx_pattern_evals.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            _lib = L
+    return _lib
+
+
+def error_string(code: int) -> str:
+    return lib().fdx_error_string(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != FDX_OK:
+        raise FdxError(rc, where)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# struct builders (from plain values or a workloads.Problem)
+# ---------------------------------------------------------------------------
+
+def make_cell(cell) -> Cell:
+    return Cell(*[float(x) for x in cell])
+
+
+def make_broadening(br) -> Broadening:
+    b = Broadening()
+    b.L[:] = [float(x) for x in br.L]
+    b.g[:] = [float(x) for x in br.g]
+    b.B_axis[:] = [float(x) for x in br.B_axis]
+    b.lineshape = int(br.lineshape)
+    b.intensity_model = int(br.intensity_model)
+    b.sigma, b.gamma, b.sigma_r, b.T = float(br.sigma), float(br.gamma), float(br.sigma_r), float(br.T)
+    b.n_nodes = int(br.n_nodes)
+    b.K_z = float(br.K_z)
+    return b
+
+
+def make_geometry(ge) -> Geometry:
+    g = Geometry()
+    g.wavelength, g.distance, g.pixel = float(ge.wavelength), float(ge.distance), float(ge.pixel)
+    g.n_x, g.n_y = int(ge.n_x), int(ge.n_y)
+    g.fiber_axis[:] = [float(x) for x in ge.fiber_axis]
+    g.beam_axis[:] = [float(x) for x in ge.beam_axis]
+    g.delta_L = float(ge.delta_L)
+    return g
+
+
+def make_problem(cell, br, geom, hkl, M) -> Problem:
+    """hkl: int32 [n, 3] and M: float32 [n] CUDA tensors (kept alive by the caller)."""
+    p = Problem()
+    p.cell = make_cell(cell)
+    p.br = make_broadening(br)
+    p.geom = make_geometry(geom)
+    p.n_refl = int(hkl.shape[0])
+    p.hkl = hkl.data_ptr() if p.n_refl else None
+    p.M = M.data_ptr() if p.n_refl else None
+    return p
+
+
+class DeviceAtoms:
+    """Device copies of an atom set in the C-ABI's dtypes (frac f64, B/occ/ff f32, elem u8)."""
+
+    def __init__(self, atoms, device="cuda"):
+        import torch
+        self.frac = torch.as_tensor(np.ascontiguousarray(atoms.frac, np.float64), device=device)
+        self.B = torch.as_tensor(np.ascontiguousarray(atoms.B, np.float32), device=device)
+        self.occ = torch.as_tensor(np.ascontiguousarray(atoms.occ, np.float32), device=device)
+        self.elem = torch.as_tensor(np.ascontiguousarray(atoms.elem, np.uint8), device=device)
+        self.ff = torch.as_tensor(np.ascontiguousarray(atoms.ff, np.float32).reshape(-1, 9), device=device)
+
+    def struct(self) -> Atoms:
+        a = Atoms()
+        a.n_atoms = int(self.frac.shape[0])
+        a.n_elem = int(self.ff.shape[0])
+        a.frac, a.B, a.occ = self.frac.data_ptr(), self.B.data_ptr(), self.occ.data_ptr()
+        a.elem, a.ff = self.elem.data_ptr(), self.ff.data_ptr()
+        return a
+
+
+# ---------------------------------------------------------------------------
+# entry points (names of include/fdx.h)
+# ---------------------------------------------------------------------------
+
+def fdx_version() -> int:
+    return int(lib().fdx_version())
+
+
+def fdx_reflections(cell, d_min, d_max=0.0) -> np.ndarray:
+    """Reflection list as a host int32 [n, 3] array (count, then fill)."""
+    c = make_cell(cell)
+    n = C.c_int32(0)
+    _check(lib().fdx_reflections(C.byref(c), float(d_min), float(d_max), 0, None, C.byref(n)), "fdx_reflections")
+    out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check(lib().fdx_reflections(C.byref(c), float(d_min), float(d_max), n.value, out.ctypes.data_as(C.c_void_p),
+                                 C.byref(n)), "fdx_reflections")
+    return out[:n.value]
+
+
+def fdx_sf_workspace_size(n_atoms: int, n_refl: int) -> int:
+    return int(lib().fdx_sf_workspace_size(int(n_atoms), int(n_refl)))
+
+
+def fdx_structure_factors(cell, datoms: DeviceAtoms, hkl, br=None, F_out=None, M_out=None, workspace=None,
+                          stream=None):
+    """F (float32 [n, 2]) and M (float32 [n]) for device hkl (int32 [n, 3])."""
+    import torch
+    n = int(hkl.shape[0])
+    dev = hkl.device
+    if F_out is None:
+        F_out = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    if M_out is None:
+        M_out = torch.empty((n,), dtype=torch.float32, device=dev)
+    need = fdx_sf_workspace_size(int(datoms.frac.shape[0]), n)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    c = make_cell(cell)
+    a = datoms.struct()
+    b = make_broadening(br) if br is not None else None
+    _check(lib().fdx_structure_factors(C.byref(c), C.byref(a), C.byref(b) if b is not None else None, n,
+                                       _ptr(hkl), _ptr(F_out), _ptr(M_out), _ptr(workspace),
+                                       int(workspace.numel()), _stream(stream)), "fdx_structure_factors")
+    return F_out, M_out
+
+
+def _problem_array(problems):
+    arr = (C.POINTER(Problem) * len(problems))(*[C.pointer(p) for p in problems])
+    return arr
+
+
+def fdx_workspace_size(problems) -> int:
+    return int(lib().fdx_workspace_size(len(problems), _problem_array(problems)))
+
+
+def fdx_pattern(problems, images, workspace=None, stream=None):
+    """images: list of float32 [n_y, n_x] CUDA tensors, one per problem."""
+    import torch
+    arr = _problem_array(problems)
+    need = fdx_workspace_size(problems)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=images[0].device)
+    ims = (C.c_void_p * len(images))(*[im.data_ptr() for im in images])
+    _check(lib().fdx_pattern(len(problems), arr, ims, _ptr(workspace), int(workspace.numel()), _stream(stream)),
+           "fdx_pattern")
+    return images
+
+
+def fdx_pattern_evals(problem, counts, workspace=None, stream=None):
+    import torch
+    need = fdx_workspace_size([problem])
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=counts.device)
+    _check(lib().fdx_pattern_evals(C.byref(problem), _ptr(counts), _ptr(workspace), int(workspace.numel()),
+                                   _stream(stream)), "fdx_pattern_evals")
+    return counts
+
+
+# ---------------------------------------------------------------------------
+# convenience: the whole forward path for one workloads.Problem
+# ---------------------------------------------------------------------------
+
+class Simulation:
+    """Device-resident state for one problem: reflections, atoms, workspaces."""
+
+    def __init__(self, problem, device="cuda"):
+        import torch
+        self.problem = problem
+        self.device = device
+        self.hkl_host = fdx_reflections(problem.cell, problem.d_min, problem.d_max)
+        self.hkl = torch.as_tensor(self.hkl_host, device=device).contiguous()
+        self.atoms = DeviceAtoms(problem.atoms, device)
+        n = self.hkl.shape[0]
+        self.F = torch.empty((n, 2), dtype=torch.float32, device=device)
+        self.M = torch.empty((n,), dtype=torch.float32, device=device)
+        self.sf_ws = torch.empty(max(fdx_sf_workspace_size(problem.atoms.n, n), 256), dtype=torch.uint8,
+                                 device=device)
+        self.prob = make_problem(problem.cell, problem.br, problem.geom, self.hkl, self.M)
+        self.image = torch.empty((problem.geom.n_y, problem.geom.n_x), dtype=torch.float32, device=device)
+        self.ws = torch.empty(max(fdx_workspace_size([self.prob]), 256), dtype=torch.uint8, device=device)
+
+    def structure_factors(self, stream=None):
+        fdx_structure_factors(self.problem.cell, self.atoms, self.hkl, self.problem.br, self.F, self.M, self.sf_ws,
+                              stream)
+        return self.F, self.M
+
+    def pattern(self, stream=None):
+        fdx_pattern([self.prob], [self.image], self.ws, stream)
+        return self.image
+
+    def forward(self, stream=None):
+        self.structure_factors(stream)
+        return self.pattern(stream)
+
+    def evals(self, stream=None):
+        import torch
+        counts = torch.empty_like(self.image, dtype=torch.int32)
+        fdx_pattern_evals(self.prob, counts, self.ws, stream)
+        return counts

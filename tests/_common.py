@@ -1,0 +1,30 @@
+"""Shared test helpers: input rounding to the C-ABI's dtypes and the parity
+metrics of the scope (max |dI| <= 1e-5 max I, relative L2 <= 1e-6)."""
+from dataclasses import replace
+
+import numpy as np
+
+# Accuracy gates for FP32 results against the FP64 oracle.
+MAX_REL = 1e-5   # max |dI| / max |I_oracle|
+L2_REL = 1e-6    # ||dI||_2 / ||I_oracle||_2
+
+
+def api_precision(problem):
+    """The problem with B, occupancy and form factors rounded to float32, the
+    precision the C-ABI takes them in, so oracle and GPU see identical inputs."""
+    a = problem.atoms
+    atoms = replace(a, B=a.B.astype(np.float32).astype(np.float64),
+                    occ=a.occ.astype(np.float32).astype(np.float64),
+                    ff=a.ff.astype(np.float32).astype(np.float64))
+    return replace(problem, atoms=atoms)
+
+
+def parity(got, ref):
+    got = np.asarray(got, dtype=np.float64).reshape(-1)
+    ref = np.asarray(ref, dtype=np.float64).reshape(-1)
+    d = got - ref
+    mx = float(np.max(np.abs(ref))) if ref.size else 0.0
+    max_rel = float(np.max(np.abs(d)) / mx) if mx > 0 else float(np.max(np.abs(d)) if d.size else 0.0)
+    nrm = float(np.linalg.norm(ref))
+    l2 = float(np.linalg.norm(d) / nrm) if nrm > 0 else float(np.linalg.norm(d))
+    return max_rel, l2

@@ -1,0 +1,118 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point
+declared in include/fdx.h, and rejects bad arguments on the host before any
+device work (these calls return before touching a GPU)."""
+import ctypes as C
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fdx():
+    from paper_2608_23245_b300 import _build, fdx
+    _build.build()
+    return fdx
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "fdx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fdx_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fdx):
+    names = _declared()
+    assert {"fdx_reflections", "fdx_structure_factors", "fdx_pattern", "fdx_workspace_size"} <= set(names)
+    lib = fdx.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_version_and_errors(fdx):
+    assert fdx.fdx_version() >= 100
+    for code in (0, -1, -2, -3, -4, -5, -6):
+        assert fdx.error_string(code)
+    assert fdx.error_string(1234) == "unknown error"
+
+
+def _problem(fdx, **geo):
+    from paper_2608_23245_b300 import workloads as W
+    p = W.small_helix()
+    g = p.geom
+    for k, v in geo.items():
+        g = type(g)(**{**g.__dict__, k: v})
+    prob = fdx.Problem()
+    prob.cell = fdx.make_cell(p.cell)
+    prob.br = fdx.make_broadening(p.br)
+    prob.geom = fdx.make_geometry(g)
+    prob.n_refl = 3
+    prob.hkl = 16   # never dereferenced: validation fails first
+    prob.M = 16
+    return prob
+
+
+def test_pattern_rejects_nonorthogonal_beam(fdx):
+    """Sect. Experimental geometry: beam and fiber must be orthogonal within 1e-3."""
+    lib = fdx.lib()
+    prob = _problem(fdx, beam_axis=(1.0, 0.0, 0.01))
+    arr = fdx._problem_array([prob])
+    ims = (C.c_void_p * 1)(16)
+    assert lib.fdx_pattern(1, arr, ims, C.c_void_p(256), 1 << 30, None) == -2
+    prob = _problem(fdx, beam_axis=(1.0, 0.0, 0.0009))
+    assert lib.fdx_workspace_size(1, fdx._problem_array([prob])) > 0
+
+
+def test_pattern_rejects_bad_arguments(fdx):
+    lib = fdx.lib()
+    ims = (C.c_void_p * 1)(16)
+    for kw in ({"n_x": 0}, {"pixel": -1.0}, {"wavelength": float("nan")}, {"delta_L": 0.0}):
+        prob = _problem(fdx, **kw)
+        assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(256), 1 << 30, None) == -1
+    prob = _problem(fdx)
+    prob.br.n_nodes = 0
+    assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(256), 1 << 30, None) == -1
+    prob = _problem(fdx)
+    prob.br.lineshape = 7
+    assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(256), 1 << 30, None) == -1
+    prob = _problem(fdx)
+    assert lib.fdx_pattern(0, fdx._problem_array([prob]), ims, C.c_void_p(256), 1 << 30, None) == -1
+    # workspace too small / misaligned
+    need = lib.fdx_workspace_size(1, fdx._problem_array([prob]))
+    assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(256), need - 1, None) == -3
+    assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(260), need, None) == -3
+
+
+def test_reflections_count_mode_and_capacity(fdx):
+    """Count/fill protocol on a host buffer (integer enumeration only)."""
+    lib = fdx.lib()
+    cell = fdx.make_cell((9.0, 9.0, 15.0, math.pi / 2, math.pi / 2, math.pi / 2))
+    n = C.c_int32(-1)
+    assert lib.fdx_reflections(C.byref(cell), 2.5, 0.0, 0, None, C.byref(n)) == 0
+    assert n.value == 304
+    buf = (C.c_int32 * 30)()
+    assert lib.fdx_reflections(C.byref(cell), 2.5, 0.0, 10, buf, C.byref(n)) == -5
+    assert lib.fdx_reflections(C.byref(cell), 0.0, 0.0, 0, None, C.byref(n)) == -2
+    bad = fdx.make_cell((9.0, 9.0, 15.0, math.pi / 2, math.pi / 2, 3 * math.pi / 2))
+    assert lib.fdx_reflections(C.byref(bad), 2.5, 0.0, 0, None, C.byref(n)) == -2
+
+
+def test_structure_factor_argument_checks(fdx):
+    lib = fdx.lib()
+    cell = fdx.make_cell((9.0, 9.0, 15.0, math.pi / 2, math.pi / 2, math.pi / 2))
+    a = fdx.Atoms()
+    a.n_atoms, a.n_elem = 0, 1
+    assert lib.fdx_structure_factors(C.byref(cell), C.byref(a), None, 5, C.c_void_p(16), C.c_void_p(16), None,
+                                     C.c_void_p(256), 1 << 20, None) == -1
+    a.n_atoms, a.n_elem = 10, 65
+    a.frac = a.B = a.elem = a.ff = 16
+    assert lib.fdx_structure_factors(C.byref(cell), C.byref(a), None, 5, C.c_void_p(16), C.c_void_p(16), None,
+                                     C.c_void_p(256), 1 << 20, None) == -1
+    a.n_elem = 4
+    need = lib.fdx_sf_workspace_size(10, 5)
+    assert need > 0
+    assert lib.fdx_structure_factors(C.byref(cell), C.byref(a), None, 5, C.c_void_p(16), C.c_void_p(16), None,
+                                     C.c_void_p(256), need - 1, None) == -3
