@@ -68,6 +68,13 @@ __host__ __device__ __forceinline__ void split_double(double x, float &hi, float
     lo = (float)(x - (double)hi);
 }
 
+// Reciprocal on the SFU (rcp.approx.ftz.f32: max error 1 ulp for normal inputs).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Horner evaluation with coefficients in increasing order.
 template <int N>
 __device__ __forceinline__ float horner(const float (&c)[N], float x) {
@@ -79,7 +86,7 @@ __device__ __forceinline__ float horner(const float (&c)[N], float x) {
 
 // sin^2(pi t) for |t| <= 1/2: t^2 Q(t^2), Q fitted by fit_poly.py.
 __device__ __forceinline__ float sinpi_sq(float t) {
-    const float Q[7] = FDX_SINPI2_C;
+    const float Q[6] = FDX_SINPI2_C;
     float x = t * t;
     return x * horner(Q, x);
 }

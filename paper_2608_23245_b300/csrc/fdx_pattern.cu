@@ -8,14 +8,17 @@
 // and processes the survivors in list order (deterministic).  For a surviving
 // reflection each lane projects the 8 corners of its support box onto the
 // gnomonic plane, which bounds the node rows/columns that can be in support;
-// the warp takes the union.  The warp then stages, for the nodes of that
-// union, sigma_i(k) = a_i . (s_k - p_ref) (p_ref = the query point of lane 0's
-// pixel) into its shared-memory buffer, computed with float-float differences
-// so that the small offsets survive FP32 rounding.  Every lane then walks the
-// staged nodes with warp-uniform bounds: t_i = tau_i - sigma_i, where
-// tau_i = a_i . (p - p_ref) is the lane's own small offset, tests the support
-// and accumulates w_k prod_i K_i(t_i).  Row sums are folded into a
-// float-float pair sum, pair sums into a float-float pixel sum.
+// the warp takes the union.  For the nodes of that union the warp computes,
+// one node per lane, sigma_i(k) = a_i . (s_k - p_ref) (p_ref = the query point
+// of lane 0's pixel) with float-float differences so that the small offsets
+// survive FP32 rounding, and keeps only the nodes that can lie in the support
+// of some lane of the warp (sigma_i within the warp's range of tau_i widened
+// by the support half-width); the survivors are compacted into the warp's
+// shared-memory buffer.  Every lane then walks the buffer with warp-uniform
+// bounds: t_i = tau_i - sigma_i, where tau_i = a_i . (p - p_ref) is the lane's
+// own small offset, tests the support and accumulates w_k prod_i K_i(t_i).
+// Sums of 32 nodes are folded into a float-float pair sum, pair sums into a
+// float-float pixel sum.
 #include "fdx_internal.cuh"
 
 namespace fdx {
@@ -34,35 +37,38 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-template <int LS>
-__device__ __forceinline__ float node_term(float ta, float tb, float tc, const float *la, const float *lb) {
-    if (LS == FDX_LINESHAPE_HOSEMANN) {
-        // K_i = beta_i / (beta_i^2 + (1 - beta_i^2) sin^2(pi t_i)); prod beta_i is in the pair factor
-        const float da = fmaf(lb[0], sinpi_sq(ta), la[0]);
-        const float db = fmaf(lb[1], sinpi_sq(tb), la[1]);
-        const float dc = fmaf(lb[2], sinpi_sq(tc), la[2]);
-        return __fdividef(1.0f, da * db * dc);
-    } else {
-        // K_i = N_i sinc^2(N_i t_i); with x = N t, y = x - rint(x):
-        // sinc^2(x) = Q(y^2) (y^2 / x^2) / pi^2, the ratio being 1 when rint(x) = 0.
-        // prod N_i / pi^6 is in the pair factor.
-        const float Qc[7] = FDX_SINPI2_C;
-        float num = 1.0f, den = 1.0f, q = 1.0f;
-        const float tt[3] = {ta, tb, tc};
+// Hosemann denominators: den_i = beta_i^2 + (1 - beta_i^2) sin^2(pi t_i), with
+// sin^2(pi t) = x Q(x), x = t^2, folded into one degree-6 polynomial in x whose
+// coefficients cf[i][.] are scaled per reflection.  K_i = beta_i / den_i; the
+// product of the beta_i is in the pair factor.
+__device__ __forceinline__ float hosemann_den(float t, const float (&c)[7]) {
+    const float x = t * t;
+    float d = c[6];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float x = la[i] * tt[i];
-            const float k = rintf(x);
-            const float y = x - k;
-            const float y2 = y * y;
-            q *= horner(Qc, y2);
-            if (k != 0.0f) {
-                num *= y2;
-                den *= x * x;
-            }
+    for (int k = 5; k >= 0; --k) d = fmaf(d, x, c[k]);
+    return d;
+}
+
+// Sinc lineshape: K_i = N_i sinc^2(N_i t_i); with x = N t, y = x - rint(x):
+// sinc^2(x) = Q(y^2) (y^2 / x^2) / pi^2, the ratio being 1 when rint(x) = 0.
+// prod N_i / pi^6 is in the pair factor.
+__device__ __forceinline__ float sinc_term(float ta, float tb, float tc, const float *la) {
+    const float Qc[6] = FDX_SINPI2_C;
+    float num = 1.0f, den = 1.0f, q = 1.0f;
+    const float tt[3] = {ta, tb, tc};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float x = la[i] * tt[i];
+        const float k = rintf(x);
+        const float y = x - k;
+        const float y2 = y * y;
+        q *= horner(Qc, y2);
+        if (k != 0.0f) {
+            num *= y2;
+            den *= x * x;
         }
-        return q * __fdividef(num, den);
     }
+    return q * __fdividef(num, den);
 }
 
 template <int LS, bool COUNT>
@@ -155,9 +161,18 @@ __global__ void __launch_bounds__(WARPS * 32, 4) pattern_kernel(PatternParams P)
             float tau[3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) tau[i] = valid ? fmaf(dZl, P.AZ[i], dRl * rec[REC_AR + i]) : 3.0e30f;
-            float la[3], lb[3], tm[3];
+            float la[3], tm[3], cf[3][7];
+            {
+                const float Qc[6] = FDX_SINPI2_C;
 #pragma unroll
-            for (int i = 0; i < 3; ++i) la[i] = rec[REC_LA + i], lb[i] = rec[REC_LB + i], tm[i] = rec[REC_TM + i];
+                for (int i = 0; i < 3; ++i) {
+                    la[i] = rec[REC_LA + i], tm[i] = rec[REC_TM + i];
+                    const float lb = rec[REC_LB + i];
+                    cf[i][0] = la[i];
+#pragma unroll
+                    for (int k = 1; k < 7; ++k) cf[i][k] = lb * Qc[k - 1];
+                }
+            }
             const float hh[3] = {rec[REC_H], rec[REC_H + 1], rec[REC_H + 2]};
             const float E1[3] = {rec[REC_E1], rec[REC_E1 + 1], rec[REC_E1 + 2]};
             const float E2[3] = {rec[REC_E2], rec[REC_E2 + 1], rec[REC_E2 + 2]};
@@ -172,15 +187,28 @@ __global__ void __launch_bounds__(WARPS * 32, 4) pattern_kernel(PatternParams P)
                                ff_mul(dRr, ff{rec[REC_EFR + q], rec[REC_EFR + 3 + q]}));
             }
 
+            // Warp-wide tau box: a node can be in the support of some lane only if
+            // sigma_i lies within [min tau_i - tm_i, max tau_i + tm_i] for every i.
+            float tc[3], th[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float lo = warp_min(valid ? tau[i] : 3.0e38f), hi = warp_max(valid ? tau[i] : -3.0e38f);
+                tc[i] = 0.5f * (lo + hi);
+                th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
+            }
             const int ncols = M1 - M0 + 1;
-            const int rows_per_chunk = NODE_BUF / ncols;
+            const int total = (J1 - J0 + 1) * ncols;
+            const unsigned lt_mask = (1u << lane) - 1u;
+            const int step_r = 32 / ncols, step_c = 32 - step_r * ncols;
+            int jj = J0 + lane / ncols, mm = M0 + lane % ncols;  // this lane's node in the batch
             ff pair = {0.0f, 0.0f};
-            for (int jc = J0; jc <= J1; jc += rows_per_chunk) {
-                const int nr = min(rows_per_chunk, J1 - jc + 1);
-                const int total = nr * ncols;
-                __syncwarp();
-                for (int idx = lane; idx < total; idx += 32) {
-                    const int jj = jc + idx / ncols, mm = M0 + idx % ncols;
+            int nlive = 0;
+            for (int b0 = 0; b0 < total; b0 += 32) {
+                // stage: one node per lane, keep it if it passes the warp-wide test
+                const int idx = b0 + lane;
+                bool live = false;
+                float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (idx < total) {
                     const size_t k = (size_t)jj * n + mm;
                     const float4 na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
                     // u = s_k/r0 - p_ref/r0 in the local frame = (c - 1, c d1, c d2) - dP
@@ -190,25 +218,42 @@ __global__ void __launch_bounds__(WARPS * 32, 4) pattern_kernel(PatternParams P)
                     float sg[3];
 #pragma unroll
                     for (int i = 0; i < 3; ++i) sg[i] = fmaf(hh[i], u0, fmaf(E1[i], u1, E2[i] * u2));
-                    buf[idx] = make_float4(sg[0], sg[1], sg[2], nb.z);
+                    live = (fabsf(sg[0] - tc[0]) <= th[0]) & (fabsf(sg[1] - tc[1]) <= th[1]) &
+                           (fabsf(sg[2] - tc[2]) <= th[2]);
+                    val = make_float4(sg[0], sg[1], sg[2], nb.z);
                 }
-                __syncwarp();
-                for (int row = 0; row < nr; ++row) {
-                    const float4 *nrow = buf + row * ncols;
-                    float rs = 0.0f;
+                jj += step_r, mm += step_c;
+                if (mm > M1) mm -= ncols, ++jj;
+                const unsigned bal = __ballot_sync(FDX_FULL_MASK, live);
+                if (live) buf[nlive + __popc(bal & lt_mask)] = val;
+                nlive += __popc(bal);
+                if (nlive > NODE_BUF - 32 || (b0 + 32 >= total && nlive > 0)) {
+                    __syncwarp();
+                    // walk the live nodes: 32 at a time into a row sum, then into the pair sum
+                    for (int q0 = 0; q0 < nlive; q0 += 32) {
+                        const int qe = min(q0 + 32, nlive);
+                        float rs = 0.0f;
 #pragma unroll 4
-                    for (int c = 0; c < ncols; ++c) {
-                        const float4 q = nrow[c];
-                        const float ta = tau[0] - q.x, tb = tau[1] - q.y, tc = tau[2] - q.z;
-                        const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tc) <= tm[2]);
-                        if (COUNT) {
-                            cnt += in ? 1 : 0;
-                        } else {
-                            const float k = q.w * node_term<LS>(ta, tb, tc, la, lb);
-                            rs += in ? k : 0.0f;
+                        for (int q = q0; q < qe; ++q) {
+                            const float4 nq = buf[q];
+                            const float ta = tau[0] - nq.x, tb = tau[1] - nq.y, tcc = tau[2] - nq.z;
+                            const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tcc) <= tm[2]);
+                            if (COUNT) {
+                                cnt += in ? 1 : 0;
+                            } else if (LS == FDX_LINESHAPE_HOSEMANN) {
+                                const float d = hosemann_den(ta, cf[0]) * hosemann_den(tb, cf[1]) *
+                                                hosemann_den(tcc, cf[2]);
+                                const float kv = nq.w * rcp_approx(d);
+                                rs += in ? kv : 0.0f;
+                            } else {
+                                const float kv = nq.w * sinc_term(ta, tb, tcc, la);
+                                rs += in ? kv : 0.0f;
+                            }
                         }
+                        if (!COUNT) pair = ff_add_f(pair, rs);
                     }
-                    if (!COUNT) pair = ff_add_f(pair, rs);
+                    nlive = 0;
+                    __syncwarp();
                 }
             }
             if (!COUNT) acc = ff_add(acc, ff_mul_f(pair, rec[REC_FR]));

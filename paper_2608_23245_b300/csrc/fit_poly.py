@@ -36,7 +36,7 @@ def main():
     S, eS = lawson(lambda u: np.sin(2 * np.pi * np.sqrt(u)) / np.sqrt(u), u, 3, rel=True)
     Cc, eC = lawson(lambda u: np.cos(2 * np.pi * np.sqrt(u)), u, 4, rel=False)
     v = cheb(1e-12, 0.25)
-    Q, eQ = lawson(lambda v: np.sin(np.pi * np.sqrt(v)) ** 2 / v, v, 6, rel=True)
+    Q, eQ = lawson(lambda v: np.sin(np.pi * np.sqrt(v)) ** 2 / v, v, 5, rel=True)
     out = ["/* Generated by fit_poly.py (weighted least squares + Lawson iterations). */",
            "#pragma once",
            "/* sin(2 pi r) = r * S(r^2), |r| <= 1/8; max rel err %.2e */" % eS,

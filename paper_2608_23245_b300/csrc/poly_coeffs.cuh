@@ -4,5 +4,5 @@
 #define FDX_SIN2PI_C {6.283185287e+00f, -4.134166145e+01f, 8.159235355e+01f, -7.539356270e+01f}
 /* cos(2 pi r) = C(r^2), |r| <= 1/8; max abs err 4.74e-11 */
 #define FDX_COS2PI_C {1.000000000e+00f, -1.973920865e+01f, 6.493931621e+01f, -8.544285212e+01f, 5.922040724e+01f}
-/* sin^2(pi t) = t^2 * Q(t^2), |t| <= 1/2; max rel err 1.45e-10 */
-#define FDX_SINPI2_C {9.869604400e+00f, -3.246969651e+01f, 4.272837910e+01f, -3.012165487e+01f, 1.320586176e+01f, -3.910468516e+00f, 7.385572356e-01f}
+/* sin^2(pi t) = t^2 * Q(t^2), |t| <= 1/2; max rel err 1.39e-08 */
+#define FDX_SINPI2_C {9.869604264e+00f, -3.246966236e+01f, 4.272692743e+01f, -3.009855317e+01f, 1.303711163e+01f, -3.336210712e+00f}
