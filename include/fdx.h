@@ -148,6 +148,30 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
                           const int32_t *hkl, float *F_out, float *M_out, void *workspace, size_t ws_bytes,
                           void *stream);
 
+/*
+ * fdx_structure_factors_noalloc -- the same computation as
+ * fdx_structure_factors, for callers that cannot allocate device memory at
+ * call time (for example a plugin inside a host application whose caching
+ * allocator owns all device memory, or a real-time loop that must not call
+ * cudaMalloc after start-up because it can synchronise the device).  The paper
+ * has no counterpart: this is a deployment convenience of the library.
+ *   - No workspace argument: the kernels' scratch is a fixed array of
+ *     FDX_NOALLOC_SF_SCRATCH_BYTES (8 MiB) in device memory that every GPU
+ *     loading libfdx holds until the process exits.  It must fit 24 bytes per
+ *     atom plus 16 bytes per reflection (per atom split; the call uses as many
+ *     splits as fit, at most 64); larger sizes return FDX_ERR_WORKSPACE before
+ *     any work is queued.  The call allocates nothing.
+ *   - The first call on a device looks up the array's address on that device
+ *     and caches it; make that first call before any stream capture.
+ *   - All calls share the array.  Calls whose work overlaps on the GPU race on
+ *     it: serialise them (one stream, or events between streams).  Nothing in
+ *     it needs to start at zero.
+ * Inputs, outputs and return codes as fdx_structure_factors.  Asynchronous.
+ */
+#define FDX_NOALLOC_SF_SCRATCH_BYTES (8u << 20)
+int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_atoms *atoms, const fdx_broadening *br,
+                                  int32_t n_refl, const int32_t *hkl, float *F_out, float *M_out, void *stream);
+
 /* Bytes of workspace fdx_pattern / fdx_pattern_evals need for these problems. */
 size_t fdx_workspace_size(int32_t n_models, const fdx_problem *const *probs);
 

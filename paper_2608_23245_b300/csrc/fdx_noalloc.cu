@@ -1,0 +1,134 @@
+// Structure factors without a caller-provided workspace.
+//
+// Who needs this: some callers cannot call cudaMalloc (or any allocating
+// routine) at the point where they want structure factors -- for example a
+// plugin running inside a host application whose own caching allocator owns
+// all device memory, or a real-time refinement loop that must not allocate
+// after start-up because cudaMalloc can synchronise the device and take an
+// unbounded time.  Such callers still own their inputs and outputs; only the
+// scratch space of the structure-factor kernels is provided here, as a
+// fixed-size array in device memory that the library reserves when it is
+// loaded.
+//
+// Contract (also stated in include/fdx.h):
+//   - the scratch is one file-scope __device__ array of FDX_NOALLOC_SF_SCRATCH_BYTES
+//     (8 MiB); every GPU that loads libfdx keeps it until the process exits;
+//   - sizes whose scratch does not fit are rejected with FDX_ERR_WORKSPACE
+//     before any work is queued;
+//   - the first call on a device looks up the array's device address on that
+//     device (cudaGetSymbolAddress) and caches it; make that first call before
+//     any stream capture;
+//   - all calls share the one array and leave their partial sums in it; calls
+//     whose work overlaps on the GPU (different streams, or different host
+//     threads without ordering) race on it and must be serialised by the
+//     caller;
+//   - nothing in the scratch has to start at zero: every kernel writes each
+//     scratch element it later reads within the same call.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "fdx_internal.cuh"
+
+using namespace fdx;
+
+namespace {
+
+constexpr size_t kScratchBytes = FDX_NOALLOC_SF_SCRATCH_BYTES;
+constexpr size_t kAlign = 256;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_sf_scratch[kScratchBytes];
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+std::mutex g_mu;
+void *g_ptr[kMaxDevices] = {nullptr};
+
+// Device address of g_sf_scratch on the current device (looked up once per device).
+int scratch_address(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FDX_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_sf_scratch) != cudaSuccess || !p) return FDX_ERR_CUDA;
+        g_ptr[dev] = p;
+    }
+    *out = g_ptr[dev];
+    return FDX_OK;
+}
+
+}  // namespace
+
+extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_atoms *atoms,
+                                             const fdx_broadening *br, int32_t n_refl, const int32_t *hkl,
+                                             float *F_out, float *M_out, void *stream) {
+    if (!cell || !atoms) return FDX_ERR_ARG;
+    const double cv[6] = {cell->a, cell->b, cell->c, cell->alpha, cell->beta, cell->gamma};
+    for (double x : cv)
+        if (!isfinite(x)) return FDX_ERR_ARG;
+    if (cell->a <= 0 || cell->b <= 0 || cell->c <= 0) return FDX_ERR_GEOMETRY;
+    if (atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
+    if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
+    if (n_refl < 0) return FDX_ERR_ARG;
+    if (n_refl > 0 && (!hkl || !F_out)) return FDX_ERR_ARG;
+    if (br) {
+        for (int i = 0; i < 3; ++i)
+            if (!(br->g[i] >= 0) || !isfinite(br->g[i]) || !isfinite(br->B_axis[i])) return FDX_ERR_ARG;
+        if (br->intensity_model != FDX_INTENSITY_NONE && br->intensity_model != FDX_INTENSITY_HOSEMANN)
+            return FDX_ERR_ARG;
+    }
+    if (n_refl == 0) return FDX_OK;
+
+    // Scratch: packed atoms (uint4 + float2 each) and one float4 partial per
+    // (atom split, reflection).  Use as many splits as fit, at most 64.
+    const size_t atoms_bytes = align_up(sizeof(uint4) * (size_t)atoms->n_atoms) +
+                               align_up(sizeof(float2) * (size_t)atoms->n_atoms);
+    const size_t per_split = sizeof(float4) * (size_t)n_refl;
+    if (atoms_bytes + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
+    int max_split = (int)((kScratchBytes - atoms_bytes) / per_split);
+    if (max_split > 64) max_split = 64;
+    const int refl_blocks = (n_refl + 127) / 128;
+    int n_split = (600 + refl_blocks - 1) / refl_blocks;
+    const int by_atoms = (atoms->n_atoms + 511) / 512;
+    if (n_split > by_atoms) n_split = by_atoms;
+    if (n_split > max_split) n_split = max_split;
+    if (n_split < 1) n_split = 1;
+    int per = (atoms->n_atoms + n_split - 1) / n_split;
+    per = (per + 255) / 256 * 256;
+    n_split = (atoms->n_atoms + per - 1) / per;
+    if (atoms_bytes + align_up(per_split * (size_t)n_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
+
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+
+    SFParams p;
+    memset(&p, 0, sizeof p);
+    double A[9], As[9];
+    cell_basis(*cell, A, As);
+    memcpy(p.As, As, sizeof As);
+    p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
+    p.n_split = n_split, p.atoms_per_split = per;
+    p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
+    char *ws = static_cast<char *>(base);
+    size_t off = 0;
+    p.atoms_q = reinterpret_cast<uint4 *>(ws + off);
+    off += align_up(sizeof(uint4) * (size_t)atoms->n_atoms);
+    p.atoms_w = reinterpret_cast<float2 *>(ws + off);
+    off += align_up(sizeof(float2) * (size_t)atoms->n_atoms);
+    p.partial = reinterpret_cast<float4 *>(ws + off);
+    p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;
+    p.has_br = br ? 1 : 0;
+    if (br) {
+        p.intensity_model = br->intensity_model;
+        for (int i = 0; i < 3; ++i) {
+            p.g[i] = br->g[i], p.Bax[i] = br->B_axis[i];
+            p.alen[i] = sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]);
+        }
+    }
+    if (launch_structure_factors(p, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FDX_ERR_CUDA;
+    return FDX_OK;
+}

@@ -76,6 +76,8 @@ def lib():
             L.fdx_structure_factors.argtypes = [C.POINTER(Cell), C.POINTER(Atoms), C.POINTER(Broadening), C.c_int32,
                                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                                                 C.c_void_p]
+            L.fdx_structure_factors_noalloc.argtypes = [C.POINTER(Cell), C.POINTER(Atoms), C.POINTER(Broadening),
+                                                        C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.fdx_workspace_size.restype = C.c_size_t
             L.fdx_workspace_size.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem))]
             L.fdx_pattern.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem)), C.POINTER(C.c_void_p), C.c_void_p,
@@ -209,6 +211,27 @@ def fdx_structure_factors(cell, datoms: DeviceAtoms, hkl, br=None, F_out=None, M
     _check(lib().fdx_structure_factors(C.byref(c), C.byref(a), C.byref(b) if b is not None else None, n,
                                        _ptr(hkl), _ptr(F_out), _ptr(M_out), _ptr(workspace),
                                        int(workspace.numel()), _stream(stream)), "fdx_structure_factors")
+    return F_out, M_out
+
+
+def fdx_structure_factors_noalloc(cell, datoms: DeviceAtoms, hkl, br=None, F_out=None, M_out=None, stream=None):
+    """fdx_structure_factors without a workspace: the library's fixed device
+    scratch (FDX_NOALLOC_SF_SCRATCH_BYTES) is used instead, so nothing is
+    allocated for scratch.  Calls sharing that scratch must not overlap on the
+    GPU."""
+    import torch
+    n = int(hkl.shape[0])
+    dev = hkl.device
+    if F_out is None:
+        F_out = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    if M_out is None:
+        M_out = torch.empty((n,), dtype=torch.float32, device=dev)
+    c = make_cell(cell)
+    a = datoms.struct()
+    b = make_broadening(br) if br is not None else None
+    _check(lib().fdx_structure_factors_noalloc(C.byref(c), C.byref(a), C.byref(b) if b is not None else None, n,
+                                               _ptr(hkl), _ptr(F_out), _ptr(M_out), _stream(stream)),
+           "fdx_structure_factors_noalloc")
     return F_out, M_out
 
 

@@ -28,3 +28,20 @@ def parity(got, ref):
     nrm = float(np.linalg.norm(ref))
     l2 = float(np.linalg.norm(d) / nrm) if nrm > 0 else float(np.linalg.norm(d))
     return max_rel, l2
+
+
+def amp_scale(p, hkl):
+    """sqrt(sum_j amp_j^2) per reflection (amp_j = occ_j f_j(s) exp(-B_j s^2/4)):
+    the natural scale of a direct sum's rounding error, used only to set the
+    structure-factor tolerance |dF| <= SF_TOL * amp_scale."""
+    a = p.atoms
+    from oracle import basis
+    _, As = basis(p.cell)
+    s2 = np.sum((np.asarray(hkl, np.float64) @ As) ** 2, axis=1)
+    ff = a.ff[a.elem]
+    f = ff[:, 8][None, :] + np.sum(ff[None, :, 0:4] * np.exp(-ff[None, :, 4:8] * s2[:, None, None] / 4), axis=2)
+    amp = a.occ[None, :] * f * np.exp(-a.B[None, :] * s2[:, None] / 4)
+    return np.sqrt(np.sum(amp * amp, axis=1))
+
+
+SF_TOL = 2e-6   # |F_gpu - F_ref| <= SF_TOL * amp_scale per reflection

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, api_precision, parity
+from _common import L2_REL, MAX_REL, SF_TOL, amp_scale as _amp_scale, api_precision, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -32,19 +32,6 @@ SMALL = [W.small_sinc, W.small_helix, W.small_lorentz, W.small_triclinic]
 def _sync():
     import torch
     torch.cuda.synchronize()
-
-
-def _amp_scale(p, hkl):
-    """sqrt(sum_j amp_j^2) per reflection: the natural scale of a direct sum's
-    rounding error (used only to set the tolerance)."""
-    from oracle import basis
-    _, As = basis(p.cell)
-    s2 = np.sum((hkl @ As) ** 2, axis=1)
-    a = p.atoms
-    ff = a.ff[a.elem]                                   # [n_atoms, 9]
-    f = ff[:, 8][None, :] + np.sum(ff[None, :, 0:4] * np.exp(-ff[None, :, 4:8] * s2[:, None, None] / 4), axis=2)
-    amp = a.occ[None, :] * f * np.exp(-a.B[None, :] * s2[:, None] / 4)
-    return np.sqrt(np.sum(amp * amp, axis=1))
 
 
 def test_reflections_device_buffer(gpu, orc):
@@ -76,7 +63,7 @@ def test_structure_factors(gpu, orc, make):
     Mo = orc.intensities_M(p, sim.hkl_host, Fo)
     scale = _amp_scale(p, sim.hkl_host)
     err = np.abs(Fg - Fo) / scale
-    assert err.max() <= 2e-6, err.max()
+    assert err.max() <= SF_TOL, err.max()
     Mg = M.cpu().numpy().astype(np.float64)
     _, P, DW = orc.refl_scalars(p, sim.hkl_host)
     merr = np.abs(Mg - Mo) / ((2 * np.abs(Fo) + scale) * scale * P * DW)
@@ -97,7 +84,7 @@ def test_structure_factors_large_subset(gpu, orc):
     Fg = Fg[:, 0] + 1j * Fg[:, 1]
     Fo = orc.structure_factors(p.cell, p.atoms, hkl)
     err = np.abs(Fg - Fo) / _amp_scale(p, hkl)
-    assert err.max() <= 2e-6, err.max()
+    assert err.max() <= SF_TOL, err.max()
 
 
 def _gpu_pattern(gpu, p, hkl, M):
