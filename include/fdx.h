@@ -196,6 +196,44 @@ int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const 
  */
 int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream);
 
+/* Gradients written by fdx_pattern_backward; every pointer is a device pointer
+ * or NULL (not written). */
+typedef struct fdx_grads {
+    double *dfrac;    /* [n_atoms][3] dLoss/d(fractional coordinates) */
+    double *dB;       /* [n_atoms] dLoss/dB */
+    double *dglobal;  /* [8] dLoss/d(L_a, L_b, L_c, g_a, g_b, g_c, sigma, gamma) */
+    float *dM;        /* [n_refl] dLoss/dM */
+} fdx_grads;
+
+/* Bytes of workspace fdx_pattern_backward needs. */
+size_t fdx_backward_workspace_size(const fdx_problem *prob, int32_t n_atoms, int32_t n_elem);
+
+/*
+ * fdx_pattern_backward -- hand-written adjoint of fdx_structure_factors +
+ * fdx_pattern for an upstream gradient dL_dI ([n_y][n_x] float, device).
+ * Recomputes the profiles (nothing is stored by the forward); takes the
+ * forward's F ([n_refl][2], device) and the problem's M.  Writes the
+ * gradients requested in `grads` with respect to the fractional coordinates,
+ * isotropic B, crystallite sizes L_i, Hosemann g_i, sigma and gamma (T held
+ * fixed; the pure-Gaussian branch reports 0 for gamma).  Hosemann lineshape
+ * only (FDX_ERR_ARG for the sinc lineshape).  Deterministic (no atomics).
+ * Asynchronous.
+ */
+int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const float *F, const float *dL_dI,
+                         const fdx_grads *grads, void *workspace, size_t ws_bytes, void *stream);
+
+/* Bytes of workspace fdx_loss needs for n_px pixels. */
+size_t fdx_loss_workspace_size(int64_t n_px);
+
+/*
+ * fdx_loss -- refinement loss L = sum_px m_px (I - I_t)^2 / (I_t + 1) (mask m
+ * optional, NULL = 1) into *loss_out (device double) and, when dL_dI is not
+ * NULL, dL/dI = 2 m (I - I_t)/(I_t + 1) (device float).  FP64 reduction in a
+ * fixed order.  Asynchronous.
+ */
+int fdx_loss(int64_t n_px, const float *I, const float *I_target, const float *mask, double *loss_out,
+             float *dL_dI, void *workspace, size_t ws_bytes, void *stream);
+
 /* Human-readable text for a return code (static storage). */
 const char *fdx_error_string(int code);
 

@@ -1,0 +1,375 @@
+// Refinement path: loss, pattern adjoint, structure-factor adjoint, and the
+// chain rule to the global disorder parameters.
+//
+// Loss (refinement loss of the scope): L = sum_px m_px w_px (I - I_t)^2,
+// w = 1/(I_t + 1), optional mask m; dL/dI = 2 m w (I - I_t).
+//
+// Pattern adjoint.  I_px = L_px sum_r M_r r0^2 B_r S_r(px), B_r = prod_i beta_i,
+// S_r(px) = sum_k w_k prod_i 1/den_i (Hosemann).  Per reflection:
+//   dL/dM_r        = r0^2 B_r sum_px c_px S_r(px),                c_px = dL/dI_px L_px
+//   dL/dbeta_{r,i} = M_r r0^2 B_r sum_px c_px (S/beta_i - 2 beta_i/(1 - beta_i^2) Sb_i),
+//                    Sb_i = sum_k w_k prod 1/den (1/den_i - 1)  (from dK_i/dbeta_i)
+//   dL/dsigma_r    = M_r r0^2 B_r sum_px c_px sum_k (dw_k/dsigma) prod 1/den, same for gamma.
+// The profiles are recomputed, not stored.  Work decomposition is
+// reflection-major so that per-reflection sums stay in one warp: a work item
+// is (reflection, band of pixel-patch rows); its warp walks the band's 8 x 4
+// patches that pass the reach test and evaluates each (patch, reflection) pair
+// with the forward's eval_pair in adjoint mode.  Items write their six sums;
+// a second kernel adds the bands of each reflection in fixed order.  No atomics.
+//
+// Structure-factor adjoint (M = |F|^2 P DW):
+//   dL/dx_{j,c} = sum_r -4 pi h_c Im(c_r T_jr),  dL/dB_j = sum_r -(s_r^2/2) Re(c_r T_jr),
+//   c_r = dL/dM_r P_r DW_r conj(F_r),  T_jr = occ_j f_j(s_r) exp(-B_j s_r^2/4) exp(2 pi i h_r . x_j).
+// Chain rule (reading R4/R5, Eqs. Ah/Neff/Ipara): beta = min(1, |a_i|/L_i + tanh x),
+// x = pi^2 g^2 h^2; dbeta/dL = -|a_i|/L_i^2, dbeta/dg = sech^2(x) 2 pi^2 g h^2 (0 when
+// clamped); dP/dg_i = -P tanh(2x_i) 4 pi^2 g_i h_i^2.
+#include "fdx_adjoint.cuh"
+#include "fdx_pair.cuh"
+
+namespace fdx {
+
+static constexpr int ADJ_ITEM_VALS = 6;
+static constexpr int ADJ_NODE_BUF = 384;  // keeps the CTA's static shared memory under 48 KB
+
+__device__ __forceinline__ bool reach_overlap(float4 q, float4 b) {
+    // q = (r0, rho_B, psi_D, dpsi); b = (rmin, rmax, psimin, psimax)
+    return (q.x - q.y <= b.y) && (q.x + q.y >= b.x) && (q.z - q.w <= b.w) && (q.z + q.w >= b.z);
+}
+
+// Bounds (|S| min/max, psi min/max) of every 8 x 4 patch; one warp per patch.
+__global__ void patch_bounds_kernel(AdjParams A) {
+    const int warp_g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp_g >= A.npx * A.npy) return;
+    const int pi = warp_g % A.npx, pj = warp_g / A.npx;
+    const int px = 8 * pi + (lane & 7), py = 4 * pj + (lane >> 3);
+    const bool valid = px < A.P.nx && py < A.P.ny;
+    float r = 3.0e38f, rr = -3.0e38f, p = 3.0e38f, pp = -3.0e38f;
+    if (valid) {
+        const float4 g = A.P.pixgeo[(size_t)py * A.P.nx + px];
+        r = rr = sqrtf(g.x * g.x + g.z * g.z);
+        p = pp = atan2f(g.x, g.z);
+    }
+    r = warp_min(r), rr = warp_max(rr), p = warp_min(p), pp = warp_max(pp);
+    if (lane == 0) A.patch_bounds[warp_g] = make_float4(r, rr, p, pp);
+}
+
+// Bounds of each band of patch rows; one block per band (min/max are exact).
+__global__ void band_bounds_kernel(AdjParams A) {
+    __shared__ float4 red[256];
+    const int b = blockIdx.x;
+    const int pj0 = b * A.rows_per_band, pj1 = min(A.npy, pj0 + A.rows_per_band);
+    float4 acc = make_float4(3.0e38f, -3.0e38f, 3.0e38f, -3.0e38f);
+    for (int k = threadIdx.x; k < (pj1 - pj0) * A.npx; k += blockDim.x) {
+        const float4 v = A.patch_bounds[(size_t)pj0 * A.npx + k];
+        acc.x = fminf(acc.x, v.x), acc.y = fmaxf(acc.y, v.y), acc.z = fminf(acc.z, v.z), acc.w = fmaxf(acc.w, v.w);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const float4 o = red[threadIdx.x + s];
+            float4 &m = red[threadIdx.x];
+            m.x = fminf(m.x, o.x), m.y = fmaxf(m.y, o.y), m.z = fminf(m.z, o.z), m.w = fmaxf(m.w, o.w);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A.band_bounds[b] = red[0];
+}
+
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
+    __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];
+    __shared__ float2 s_dn[PAIR_WARPS][ADJ_NODE_BUF];
+    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
+    const long long n_items = (long long)A.P.n_refl * A.n_bands;
+    if (item >= n_items) return;
+    const int r = (int)(item / A.n_bands), b = (int)(item % A.n_bands);
+    double acc[ADJ_ITEM_VALS] = {0, 0, 0, 0, 0, 0};
+    const float4 q = A.P.reach[r];
+    if (reach_overlap(q, A.band_bounds[b])) {
+        float *rec = s_rec[warp];
+        load_record(A.P.recs, r, rec, lane);
+        const int pj0 = b * A.rows_per_band, pj1 = min(A.npy, pj0 + A.rows_per_band);
+        const int np = (pj1 - pj0) * A.npx;
+        for (int base = 0; base < np; base += 32) {
+            const int idx = base + lane;
+            const bool cand = idx < np && reach_overlap(q, A.patch_bounds[(size_t)pj0 * A.npx + idx]);
+            unsigned mask = __ballot_sync(FDX_FULL_MASK, cand);
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int pidx = pj0 * A.npx + base + bit;
+                const int px0 = 8 * (pidx % A.npx), py0 = 4 * (pidx / A.npx);
+                const PatchPix g = load_patch(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
+                float c = 0.0f;
+                if (g.valid) {
+                    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
+                    const double R = (double)g.Rh + (double)g.Rl;
+                    c = (float)((double)A.gI[(size_t)py * A.P.nx + px] * A.P.delta_L / (R + A.P.delta_L));
+                }
+                if (__ballot_sync(FDX_FULL_MASK, c != 0.0f) == 0) continue;
+                PairAcc pa;
+                pa.s0 = pa.sb[0] = pa.sb[1] = pa.sb[2] = pa.ss = pa.sg = ff{0.0f, 0.0f};
+                pa.cnt = 0;
+                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF>(A.P, g, rec, s_nodes[warp], s_dn[warp], lane, pa))
+                    continue;
+                const double cd = (double)c;
+                acc[0] += warp_sum_d(cd * ((double)pa.s0.hi + (double)pa.s0.lo));
+                acc[1] += warp_sum_d(cd * ((double)pa.sb[0].hi + (double)pa.sb[0].lo));
+                acc[2] += warp_sum_d(cd * ((double)pa.sb[1].hi + (double)pa.sb[1].lo));
+                acc[3] += warp_sum_d(cd * ((double)pa.sb[2].hi + (double)pa.sb[2].lo));
+                acc[4] += warp_sum_d(cd * ((double)pa.ss.hi + (double)pa.ss.lo));
+                acc[5] += warp_sum_d(cd * ((double)pa.sg.hi + (double)pa.sg.lo));
+            }
+        }
+    }
+    if (lane < ADJ_ITEM_VALS) {
+        double o = acc[0];
+#pragma unroll
+        for (int k = 1; k < ADJ_ITEM_VALS; ++k)
+            if (lane == k) o = acc[k];
+        A.item_out[item * ADJ_ITEM_VALS + lane] = o;
+    }
+}
+
+// Per reflection: add the bands in order and form dL/dM, dL/dbeta, dL/dsigma,
+// dL/dgamma; then chain to the global parameters and the structure-factor
+// adjoint's coefficient c_r = dL/dM P DW conj(F).  FP64.
+__global__ void adjoint_reflection_kernel(AdjParams A) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= A.P.n_refl) return;
+    double s[ADJ_ITEM_VALS] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < A.n_bands; ++b)
+        for (int k = 0; k < ADJ_ITEM_VALS; ++k) s[k] += A.item_out[((size_t)r * A.n_bands + b) * ADJ_ITEM_VALS + k];
+    const float *rec = A.P.recs + (size_t)r * REC_SIZE;
+    const double r2b = rec[REC_R2B], M = rec[REC_M];
+    const double G = r2b * s[0];
+    double dbeta[3];
+    for (int i = 0; i < 3; ++i) dbeta[i] = M * r2b * (s[0] / (double)rec[REC_BETA + i] - (double)rec[REC_DBF + i] * s[1 + i]);
+    const double dsig = M * r2b * s[4], dgam = M * r2b * s[5];
+    if (A.dM) A.dM[r] = (float)G;
+
+    // chain rule to L_i, g_i; P and DW for the structure-factor adjoint
+    double P = 1.0, dw = 0.0, x[3];
+    int hk[3];
+    for (int i = 0; i < 3; ++i) {
+        hk[i] = A.hkl[3 * r + i];
+        x[i] = FDX_PI * FDX_PI * A.g[i] * A.g[i] * (double)hk[i] * hk[i];
+        if (A.intensity_model == FDX_INTENSITY_HOSEMANN) P *= 1.0 / cosh(2.0 * x[i]);
+        const double sa = hk[i] / A.alen[i];
+        dw += A.Bax[i] * sa * sa;
+    }
+    const double DW = exp(-0.25 * dw);
+    const double Fr = A.F[2 * r], Fi = A.F[2 * r + 1];
+    const double F2 = Fr * Fr + Fi * Fi;
+    double *o = A.refl_out + (size_t)r * 8;
+    for (int i = 0; i < 3; ++i) {
+        const double braw = A.alen[i] / A.L[i] + tanh(x[i]);
+        double dLi = 0.0, dgi = 0.0;
+        if (braw < 1.0) {
+            dLi = dbeta[i] * (-A.alen[i] / (A.L[i] * A.L[i]));
+            const double sh = 1.0 / cosh(x[i]);
+            dgi = dbeta[i] * sh * sh * 2.0 * FDX_PI * FDX_PI * A.g[i] * (double)hk[i] * hk[i];
+        }
+        if (A.intensity_model == FDX_INTENSITY_HOSEMANN)
+            dgi += G * F2 * DW * (-P * tanh(2.0 * x[i]) * 4.0 * FDX_PI * FDX_PI * A.g[i] * (double)hk[i] * hk[i]);
+        o[i] = dLi;
+        o[3 + i] = dgi;
+    }
+    o[6] = dsig;
+    o[7] = dgam;
+    const double Gw = G * P * DW;
+    double D[3];
+    for (int q = 0; q < 3; ++q) D[q] = hk[0] * A.As[q] + hk[1] * A.As[3 + q] + hk[2] * A.As[6 + q];
+    const double s2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+    A.cF[r] = make_float4((float)(Gw * Fr), (float)(-Gw * Fi), (float)s2, 0.0f);  // Gw conj(F), s^2
+    for (int e = 0; e < A.n_elem; ++e) {
+        const float *f = A.ff + 9 * e;
+        double v = f[8];
+        for (int m = 0; m < 4; ++m) v += (double)f[m] * exp(-(double)f[4 + m] * s2 * 0.25);
+        A.fe[(size_t)r * A.n_elem + e] = (float)v;
+    }
+}
+
+// Sum the per-reflection global contributions in a fixed order (one block).
+__global__ void adjoint_globals_kernel(AdjParams A) {
+    __shared__ double red[256][8];
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int r = threadIdx.x; r < A.P.n_refl; r += blockDim.x)
+        for (int k = 0; k < 8; ++k) acc[k] += A.refl_out[(size_t)r * 8 + k];
+    for (int k = 0; k < 8; ++k) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int k = 0; k < 8; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8 && A.dglobal) A.dglobal[threadIdx.x] = red[0][threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------
+// Structure-factor adjoint: one thread per atom, reflections staged through
+// shared memory in tiles, reflection list split over blockIdx.y; partial sums
+// per split reduced in a second kernel (fixed order).
+// ---------------------------------------------------------------------------
+static constexpr int SFA_THREADS = 128;
+static constexpr int SFA_TILE = 128;
+
+__device__ __forceinline__ void sincos_turns_adj(unsigned u, float &s, float &c) {
+    const unsigned qd = (u + 0x20000000u) >> 30;
+    const int rem = (int)(u - (qd << 30));
+    const int rh = rem >> 8, rl = rem & 255;
+    const float fh = __int_as_float(0x4B400000 + rh) - 12582912.0f;
+    const float fl = __int_as_float(0x4B000000 + rl) - 8388608.0f;
+    const float r = fmaf(fh, 5.9604644775390625e-08f, fl * 2.3283064365386963e-10f);
+    const float Sc[4] = FDX_SIN2PI_C;
+    const float Cc[5] = FDX_COS2PI_C;
+    const float r2 = r * r;
+    const float sn = r * horner(Sc, r2);
+    const float cs = horner(Cc, r2);
+    const float s1 = (qd & 1) ? cs : sn;
+    const float c1 = (qd & 1) ? -sn : cs;
+    s = (qd & 2) ? -s1 : s1;
+    c = (qd & 2) ? -c1 : c1;
+}
+
+__global__ void __launch_bounds__(SFA_THREADS) sf_adjoint_kernel(SFAdjParams p) {
+    __shared__ int4 s_h[SFA_TILE];           // h, k, l, -
+    __shared__ float4 s_c[SFA_TILE];         // c re, c im, s^2, -
+    extern __shared__ float s_fe[];          // [SFA_TILE][n_elem]
+    const int j = blockIdx.x * SFA_THREADS + threadIdx.x;
+    const bool active = j < p.n_atoms;
+    uint4 aq = make_uint4(0, 0, 0, 0);
+    float2 aw = make_float2(0.0f, -INFINITY);
+    if (active) aq = p.atoms_q[j], aw = p.atoms_w[j];
+    const int r_begin = blockIdx.y * p.refl_per_split, r_end = min(p.n_refl, r_begin + p.refl_per_split);
+    ff ax = {0, 0}, ay = {0, 0}, az = {0, 0}, ab = {0, 0};
+    for (int t0 = r_begin; t0 < r_end; t0 += SFA_TILE) {
+        const int cnt = min(SFA_TILE, r_end - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < SFA_TILE; i += SFA_THREADS) {
+            if (i < cnt) {
+                const int r = t0 + i;
+                s_h[i] = make_int4(p.hkl[3 * r], p.hkl[3 * r + 1], p.hkl[3 * r + 2], 0);
+                s_c[i] = p.cF[r];
+                for (int e = 0; e < p.n_elem; ++e) s_fe[i * p.n_elem + e] = p.fe[(size_t)r * p.n_elem + e];
+            } else {
+                s_h[i] = make_int4(0, 0, 0, 0);
+                s_c[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                for (int e = 0; e < p.n_elem; ++e) s_fe[i * p.n_elem + e] = 0.0f;
+            }
+        }
+        __syncthreads();
+        const int cnt8 = (cnt + 7) & ~7;
+        for (int i0 = 0; i0 < cnt8; i0 += 8) {
+            float bx = 0.f, by = 0.f, bz = 0.f, bb = 0.f;
+#pragma unroll
+            for (int i = i0; i < i0 + 8; ++i) {
+                const int4 hk = s_h[i];
+                const float4 c = s_c[i];
+                const unsigned ph = (unsigned)hk.x * aq.x + (unsigned)hk.y * aq.y + (unsigned)hk.z * aq.z;
+                float sn, cs;
+                sincos_turns_adj(ph, sn, cs);
+                const float a = s_fe[i * p.n_elem + aq.w] * exp2f(fmaf(aw.x, c.z, aw.y));
+                const float im = a * fmaf(c.x, sn, c.y * cs);
+                const float re = a * fmaf(c.x, cs, -c.y * sn);
+                bx = fmaf((float)hk.x, im, bx);
+                by = fmaf((float)hk.y, im, by);
+                bz = fmaf((float)hk.z, im, bz);
+                bb = fmaf(c.z, re, bb);
+            }
+            ax = ff_add_f(ax, bx), ay = ff_add_f(ay, by), az = ff_add_f(az, bz), ab = ff_add_f(ab, bb);
+        }
+    }
+    if (active) {
+        double *o = p.partial + ((size_t)blockIdx.y * p.n_atoms + j) * 4;
+        o[0] = (double)ax.hi + ax.lo;
+        o[1] = (double)ay.hi + ay.lo;
+        o[2] = (double)az.hi + az.lo;
+        o[3] = (double)ab.hi + ab.lo;
+    }
+}
+
+__global__ void sf_adjoint_reduce_kernel(SFAdjParams p) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= p.n_atoms) return;
+    double s[4] = {0, 0, 0, 0};
+    for (int sp = 0; sp < p.n_split; ++sp)
+        for (int k = 0; k < 4; ++k) s[k] += p.partial[((size_t)sp * p.n_atoms + j) * 4 + k];
+    if (p.dfrac) {
+        p.dfrac[3 * j] = -4.0 * FDX_PI * s[0];
+        p.dfrac[3 * j + 1] = -4.0 * FDX_PI * s[1];
+        p.dfrac[3 * j + 2] = -4.0 * FDX_PI * s[2];
+    }
+    if (p.dB) p.dB[j] = -0.5 * s[3];
+}
+
+// ---------------------------------------------------------------------------
+// Loss L = sum m w (I - I_t)^2, w = 1/(I_t + 1); dL/dI = 2 m w (I - I_t).
+// Per-block partial sums in a fixed tree, then one block adds them in order.
+// ---------------------------------------------------------------------------
+__global__ void loss_kernel(LossParams p) {
+    __shared__ double red[256];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < p.n) {
+        const double It = p.It[i], I = p.I[i];
+        const double m = p.mask ? (double)p.mask[i] : 1.0;
+        const double w = m / (It + 1.0);
+        const double d = I - It;
+        v = w * d * d;
+        if (p.gI) p.gI[i] = (float)(2.0 * w * d);
+    }
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) p.partial[blockIdx.x] = red[0];
+}
+
+__global__ void loss_final_kernel(LossParams p, int nblocks) {
+    __shared__ double red[256];
+    double v = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) v += p.partial[k];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *p.loss = red[0];
+}
+
+// ---------------------------------------------------------------------------
+cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
+    const int n_patch = A.npx * A.npy;
+    patch_bounds_kernel<<<(n_patch * 32 + 127) / 128, 128, 0, s>>>(A);
+    band_bounds_kernel<<<A.n_bands, 256, 0, s>>>(A);
+    if (A.P.n_refl > 0) {
+        const long long items = (long long)A.P.n_refl * A.n_bands;
+        adjoint_kernel<<<(unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS), PAIR_WARPS * 32, 0, s>>>(A);
+        adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
+    }
+    adjoint_globals_kernel<<<1, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sf_adjoint(SFAdjParams &p, cudaStream_t s) {
+    dim3 grid((p.n_atoms + SFA_THREADS - 1) / SFA_THREADS, p.n_split);
+    const size_t shm = sizeof(float) * SFA_TILE * p.n_elem;
+    sf_adjoint_kernel<<<grid, SFA_THREADS, shm, s>>>(p);
+    sf_adjoint_reduce_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(LossParams &p, cudaStream_t s) {
+    const int nb = (int)((p.n + 255) / 256);
+    loss_kernel<<<nb, 256, 0, s>>>(p);
+    loss_final_kernel<<<1, 256, 0, s>>>(p, nb);
+    return cudaGetLastError();
+}
+
+}  // namespace fdx

@@ -1,0 +1,52 @@
+// Parameters of the refinement kernels (fdx_adjoint.cu).
+#pragma once
+
+#include "fdx_internal.cuh"
+
+namespace fdx {
+
+struct AdjParams {
+    PatternParams P;           // geometry, records, node tables (image/counts unused)
+    float4 *patch_bounds;      // [npy][npx] (|S| min, max, psi min, max)
+    float4 *band_bounds;       // [n_bands]
+    int npx, npy, n_bands, rows_per_band;
+    const float *gI;           // [ny][nx] dL/dI
+    double *item_out;          // [n_refl * n_bands][6]
+    double *refl_out;          // [n_refl][8] per-reflection global contributions
+    float4 *cF;                // [n_refl] (dL/dM P DW conj(F), s^2)
+    float *fe;                 // [n_refl][n_elem] form factors at the reflection
+    float *dM;                 // [n_refl] dL/dM (may be null)
+    double *dglobal;           // [8] (may be null)
+    const int32_t *hkl;
+    const float *F;            // [n_refl][2]
+    const float *ff;           // [n_elem][9]
+    int n_elem, intensity_model;
+    double As[9];
+    double alen[3], L[3], g[3], Bax[3];
+};
+
+struct SFAdjParams {
+    int n_atoms, n_elem, n_refl, n_split, refl_per_split;
+    const uint4 *atoms_q;
+    const float2 *atoms_w;
+    const int32_t *hkl;
+    const float4 *cF;
+    const float *fe;
+    double *partial;           // [n_split][n_atoms][4]
+    double *dfrac, *dB;
+};
+
+struct LossParams {
+    long long n;
+    const float *I, *It, *mask;
+    float *gI;
+    double *partial;           // [n_blocks]
+    double *loss;
+};
+
+cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s);
+cudaError_t launch_sf_adjoint(SFAdjParams &p, cudaStream_t s);
+cudaError_t launch_loss(LossParams &p, cudaStream_t s);
+cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s);
+
+}  // namespace fdx

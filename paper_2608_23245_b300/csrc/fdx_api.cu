@@ -5,6 +5,7 @@
 
 #include <vector>
 
+#include "fdx_adjoint.cuh"
 #include "fdx_internal.cuh"
 
 using namespace fdx;
@@ -79,7 +80,7 @@ int validate_problem(const fdx_problem *p) {
 }
 
 struct Layout {
-    size_t pixgeo, nodes, recs, reach, total;
+    size_t pixgeo, nodes, dnodes, recs, reach, total;
 };
 
 Layout layout_for(const fdx_problem *p) {
@@ -89,6 +90,8 @@ Layout layout_for(const fdx_problem *p) {
     off += align_up(sizeof(float4) * (size_t)p->geom.n_x * p->geom.n_y);
     L.nodes = off;
     off += align_up(2 * sizeof(float4) * (size_t)p->br.n_nodes * p->br.n_nodes);
+    L.dnodes = off;
+    off += align_up(sizeof(float2) * (size_t)p->br.n_nodes * p->br.n_nodes);
     L.recs = off;
     off += align_up(sizeof(float) * REC_SIZE * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
     L.reach = off;
@@ -108,8 +111,9 @@ void cross3(const double *x, const double *y, double *z) {
     z[2] = x[0] * y[1] - x[1] * y[0];
 }
 
-// Queue set-up kernels and the pattern kernel for one problem.
-int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, cudaStream_t st) {
+// Queue the set-up kernels (pixel geometry, node table, reflection records)
+// for one problem and fill the pattern kernel's parameters.
+int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes) {
     const Layout L = layout_for(p);
     double A[9], As[9];
     cell_basis(p->cell, A, As);
@@ -131,6 +135,7 @@ int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, c
     np.n = p->br.n_nodes, np.T = p->br.T, np.h = 2.0 * p->br.T / p->br.n_nodes;
     np.sigma = p->br.sigma, np.gamma = p->br.gamma, np.sigma_r = p->br.sigma_r;
     np.nodes = reinterpret_cast<float4 *>(ws + L.nodes);
+    np.dnodes = with_dnodes ? reinterpret_cast<float2 *>(ws + L.dnodes) : nullptr;
     if (launch_nodes(np, weideman_coeffs(), st) != cudaSuccess) return FDX_ERR_CUDA;
 
     ReflSetupParams rp;
@@ -148,7 +153,6 @@ int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, c
     rp.reach = reinterpret_cast<float4 *>(ws + L.reach);
     if (launch_refl_setup(rp, st) != cudaSuccess) return FDX_ERR_CUDA;
 
-    PatternParams P;
     P.nx = p->geom.n_x, P.ny = p->geom.n_y, P.n_refl = p->n_refl, P.n_nodes = p->br.n_nodes;
     P.T = (float)p->br.T;
     P.inv_h = (float)(p->br.n_nodes / (2.0 * p->br.T));
@@ -158,10 +162,68 @@ int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, c
     P.reach = rp.reach;
     P.recs = rp.recs;
     P.nodes = np.nodes;
+    P.dnodes = np.dnodes;
+    P.image = nullptr;
+    P.counts = nullptr;
+    return FDX_OK;
+}
+
+// Queue set-up kernels and the pattern kernel for one problem.
+int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, cudaStream_t st) {
+    PatternParams P;
+    int rc = setup_pattern(p, ws, st, P, false);
+    if (rc) return rc;
     P.image = image;
     P.counts = counts;
     if (launch_pattern(P, p->br.lineshape, counts != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
+}
+
+// Backward workspace: the forward layout followed by the adjoint buffers.
+struct BackLayout {
+    size_t fwd, patch_bounds, band_bounds, item_out, refl_out, cF, fe, atoms_q, atoms_w, sf_partial, total;
+    int npx, npy, n_bands, rows_per_band, sf_split, refl_per_split;
+};
+
+BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
+    BackLayout B;
+    const size_t nr = (size_t)(p->n_refl > 0 ? p->n_refl : 1);
+    B.npx = (p->geom.n_x + 7) / 8, B.npy = (p->geom.n_y + 3) / 4;
+    B.n_bands = B.npy < 16 ? B.npy : 16;
+    B.rows_per_band = (B.npy + B.n_bands - 1) / B.n_bands;
+    B.n_bands = (B.npy + B.rows_per_band - 1) / B.rows_per_band;
+    const int atom_blocks = (n_atoms + 127) / 128;
+    int split = (600 + atom_blocks - 1) / atom_blocks;
+    const int by_refl = (int)((nr + 255) / 256);
+    if (split > by_refl) split = by_refl;
+    if (split > 64) split = 64;
+    if (split < 1) split = 1;
+    int per = (int)((nr + split - 1) / split);
+    per = (per + 127) / 128 * 128;
+    split = (int)((nr + per - 1) / per);
+    B.sf_split = split, B.refl_per_split = per;
+    size_t off = layout_for(p).total;
+    B.fwd = 0;
+    B.patch_bounds = off;
+    off += align_up(sizeof(float4) * (size_t)B.npx * B.npy);
+    B.band_bounds = off;
+    off += align_up(sizeof(float4) * (size_t)B.n_bands);
+    B.item_out = off;
+    off += align_up(sizeof(double) * 6 * nr * B.n_bands);
+    B.refl_out = off;
+    off += align_up(sizeof(double) * 8 * nr);
+    B.cF = off;
+    off += align_up(sizeof(float4) * nr);
+    B.fe = off;
+    off += align_up(sizeof(float) * nr * (size_t)(n_elem > 0 ? n_elem : 1));
+    B.atoms_q = off;
+    off += align_up(sizeof(uint4) * (size_t)n_atoms);
+    B.atoms_w = off;
+    off += align_up(sizeof(float2) * (size_t)n_atoms);
+    B.sf_partial = off;
+    off += align_up(sizeof(double) * 4 * (size_t)split * (size_t)n_atoms);
+    B.total = off;
+    return B;
 }
 
 }  // namespace
@@ -314,6 +376,96 @@ int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const 
         int rc = run_pattern(probs[m], images[m], nullptr, static_cast<char *>(workspace), st);
         if (rc) return rc;
     }
+    return FDX_OK;
+}
+
+size_t fdx_backward_workspace_size(const fdx_problem *prob, int32_t n_atoms, int32_t n_elem) {
+    if (!prob || n_atoms < 1 || n_elem < 1) return 0;
+    return back_layout(prob, n_atoms, n_elem).total;
+}
+
+int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const float *F, const float *dL_dI,
+                         const fdx_grads *grads, void *workspace, size_t ws_bytes, void *stream) {
+    int rc = validate_problem(prob);
+    if (rc) return rc;
+    if (prob->br.lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
+    if (!atoms || atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
+    if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
+    if (!dL_dI || !grads || (prob->n_refl > 0 && !F)) return FDX_ERR_ARG;
+    const BackLayout B = back_layout(prob, atoms->n_atoms, atoms->n_elem);
+    if (!workspace || ws_bytes < B.total || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    if (prob->n_refl == 0) {
+        if (grads->dfrac && cudaMemsetAsync(grads->dfrac, 0, sizeof(double) * 3 * atoms->n_atoms, st)) return FDX_ERR_CUDA;
+        if (grads->dB && cudaMemsetAsync(grads->dB, 0, sizeof(double) * atoms->n_atoms, st)) return FDX_ERR_CUDA;
+        if (grads->dglobal && cudaMemsetAsync(grads->dglobal, 0, sizeof(double) * 8, st)) return FDX_ERR_CUDA;
+        return FDX_OK;
+    }
+    AdjParams A;
+    memset(&A, 0, sizeof A);
+    rc = setup_pattern(prob, ws, st, A.P, true);
+    if (rc) return rc;
+    double Am[9], As[9];
+    cell_basis(prob->cell, Am, As);
+    memcpy(A.As, As, sizeof As);
+    for (int i = 0; i < 3; ++i) {
+        A.alen[i] = sqrt(Am[3 * i] * Am[3 * i] + Am[3 * i + 1] * Am[3 * i + 1] + Am[3 * i + 2] * Am[3 * i + 2]);
+        A.L[i] = prob->br.L[i], A.g[i] = prob->br.g[i], A.Bax[i] = prob->br.B_axis[i];
+    }
+    A.patch_bounds = reinterpret_cast<float4 *>(ws + B.patch_bounds);
+    A.band_bounds = reinterpret_cast<float4 *>(ws + B.band_bounds);
+    A.npx = B.npx, A.npy = B.npy, A.n_bands = B.n_bands, A.rows_per_band = B.rows_per_band;
+    A.gI = dL_dI;
+    A.item_out = reinterpret_cast<double *>(ws + B.item_out);
+    A.refl_out = reinterpret_cast<double *>(ws + B.refl_out);
+    A.cF = reinterpret_cast<float4 *>(ws + B.cF);
+    A.fe = reinterpret_cast<float *>(ws + B.fe);
+    A.dM = grads->dM;
+    A.dglobal = grads->dglobal;
+    A.hkl = prob->hkl;
+    A.F = F;
+    A.ff = atoms->ff;
+    A.n_elem = atoms->n_elem;
+    A.intensity_model = prob->br.intensity_model;
+    if (launch_adjoint(A, st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    if (grads->dfrac || grads->dB) {
+        SFParams sp;
+        memset(&sp, 0, sizeof sp);
+        sp.n_atoms = atoms->n_atoms, sp.n_elem = atoms->n_elem;
+        sp.frac = atoms->frac, sp.B = atoms->B, sp.occ = atoms->occ, sp.ff = atoms->ff, sp.elem = atoms->elem;
+        sp.atoms_q = reinterpret_cast<uint4 *>(ws + B.atoms_q);
+        sp.atoms_w = reinterpret_cast<float2 *>(ws + B.atoms_w);
+        if (launch_sf_pack(sp, st) != cudaSuccess) return FDX_ERR_CUDA;
+        SFAdjParams q;
+        memset(&q, 0, sizeof q);
+        q.n_atoms = atoms->n_atoms, q.n_elem = atoms->n_elem, q.n_refl = prob->n_refl;
+        q.n_split = B.sf_split, q.refl_per_split = B.refl_per_split;
+        q.atoms_q = sp.atoms_q, q.atoms_w = sp.atoms_w;
+        q.hkl = prob->hkl, q.cF = A.cF, q.fe = A.fe;
+        q.partial = reinterpret_cast<double *>(ws + B.sf_partial);
+        q.dfrac = grads->dfrac, q.dB = grads->dB;
+        if (launch_sf_adjoint(q, st) != cudaSuccess) return FDX_ERR_CUDA;
+    }
+    return FDX_OK;
+}
+
+size_t fdx_loss_workspace_size(int64_t n_px) {
+    if (n_px < 1) return 0;
+    return align_up(sizeof(double) * (size_t)((n_px + 255) / 256));
+}
+
+int fdx_loss(int64_t n_px, const float *I, const float *I_target, const float *mask, double *loss_out, float *dL_dI,
+             void *workspace, size_t ws_bytes, void *stream) {
+    if (n_px < 1 || !I || !I_target || !loss_out) return FDX_ERR_ARG;
+    if (!workspace || ws_bytes < fdx_loss_workspace_size(n_px) || ((uintptr_t)workspace % kAlign))
+        return FDX_ERR_WORKSPACE;
+    LossParams lp;
+    lp.n = n_px, lp.I = I, lp.It = I_target, lp.mask = mask, lp.gI = dL_dI;
+    lp.partial = static_cast<double *>(workspace);
+    lp.loss = loss_out;
+    if (launch_loss(lp, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
 }
 

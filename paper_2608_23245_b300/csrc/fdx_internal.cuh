@@ -112,6 +112,10 @@ enum RecField {
     REC_LB = 43,   // Hosemann: 1 - beta_i^2
     REC_TM = 46,   // support half-widths tmax_i
     REC_FR = 49,   // pair factor: Hosemann M r0^2 prod beta_i; sinc M r0^2 prod N_i / pi^6
+    REC_R2B = 50,  // r0^2 prod beta_i (Hosemann; dI/dM = L r0^2 prod beta_i S)
+    REC_BETA = 51, // beta_i
+    REC_M = 54,    // M
+    REC_DBF = 55,  // 2 beta_i / (1 - beta_i^2), 0 when beta_i is clamped at 1 (adjoint)
     REC_SIZE = 64
 };
 
@@ -124,6 +128,7 @@ struct PatternParams {
     const float4 *reach;  // [n_refl] (r0, rho_B, psi_D, dpsi)
     const float *recs;    // [n_refl][REC_SIZE]
     const float4 *nodes;  // [n*n][2]: (cm1 hi, cm1 lo, cd1 hi, cd1 lo), (cd2 hi, cd2 lo, w, 0)
+    const float2 *dnodes; // [n*n]: (dw/dsigma, dw/dgamma)
     float *image;         // [ny][nx]
     int32_t *counts;      // [ny][nx] (count mode)
 };
@@ -145,6 +150,7 @@ struct NodeParams {
     int n;
     double T, h, sigma, gamma, sigma_r;
     float4 *nodes;
+    float2 *dnodes;  // may be null
 };
 
 struct PixelParams {

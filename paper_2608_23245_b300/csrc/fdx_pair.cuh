@@ -1,0 +1,283 @@
+// One (pixel patch, reflection) pair of the shell quadrature, shared by the
+// forward pattern kernel (pixel-major) and the adjoint kernel
+// (reflection-major).  A warp owns an 8 x 4 pixel patch, one pixel per lane.
+//
+// For the pair the warp
+//   1. bounds the node rows/columns that can be in any lane's support by the
+//      gnomonic projection of each lane's support-box corners (union over lanes);
+//   2. computes, one node per lane, sigma_i(k) = a_i . (s_k - p_ref) relative to
+//      the query point of lane 0's pixel, with float-float differences, keeps
+//      the nodes whose sigma lies within the warp's tau range widened by the
+//      support half-width, and compacts them into the warp's shared buffer;
+//   3. every lane walks the buffer: t_i = tau_i - sigma_i with
+//      tau_i = a_i . (p - p_ref), support test, lineshape product, weight.
+// Partial sums of 32 nodes are folded into float-float accumulators.
+#pragma once
+
+#include "fdx_internal.cuh"
+
+namespace fdx {
+
+static constexpr int PAIR_WARPS = 4;     // warps per CTA in the pattern kernels
+static constexpr int NODE_BUF = 512;     // staged nodes per warp
+
+enum PairMode { MODE_FWD = 0, MODE_CNT = 1, MODE_ADJ = 2 };
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FDX_FULL_MASK, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FDX_FULL_MASK, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FDX_FULL_MASK, v, o);
+    return v;
+}
+
+// Hosemann denominator den = beta^2 + (1 - beta^2) sin^2(pi t), sin^2(pi t) =
+// x Q(x), x = t^2, folded into one degree-6 polynomial in x (coefficients c
+// scaled per reflection).  K = beta / den.
+__device__ __forceinline__ float hosemann_den(float t, const float (&c)[7]) {
+    const float x = t * t;
+    float d = c[6];
+#pragma unroll
+    for (int k = 5; k >= 0; --k) d = fmaf(d, x, c[k]);
+    return d;
+}
+
+// Sinc lineshape product: with x = N t, y = x - rint(x),
+// sinc^2(x) = Q(y^2) (y^2 / x^2) / pi^2 (the ratio is 1 when rint(x) = 0);
+// returns prod_i Q(y_i^2) (y_i^2 / x_i^2), the factor prod N_i / pi^6 being in
+// the pair factor.
+__device__ __forceinline__ float sinc_term(float ta, float tb, float tc, const float *Nn) {
+    const float Qc[6] = FDX_SINPI2_C;
+    float num = 1.0f, den = 1.0f, q = 1.0f;
+    const float tt[3] = {ta, tb, tc};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float x = Nn[i] * tt[i];
+        const float k = rintf(x);
+        const float y = x - k;
+        const float y2 = y * y;
+        q *= horner(Qc, y2);
+        if (k != 0.0f) {
+            num *= y2;
+            den *= x * x;
+        }
+    }
+    return q * __fdividef(num, den);
+}
+
+// The lane's pixel and the warp's reference pixel (lane 0), float-float.
+struct PatchPix {
+    float Rh, Rl, Zh, Zl;      // this lane's (R, Z)
+    float Rrh, Rrl, Zrh, Zrl;  // reference (lane 0)
+    float dRl, dZl;            // (R, Z) - reference, small
+    bool valid;
+};
+
+__device__ __forceinline__ PatchPix load_patch(const float4 *pixgeo, int nx, int ny, int px0, int py0, int lane) {
+    PatchPix g;
+    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
+    g.valid = (px < nx) && (py < ny);
+    const size_t pidx = g.valid ? (size_t)py * nx + px : (size_t)py0 * nx + px0;
+    const float4 v = pixgeo[pidx];
+    g.Rh = v.x, g.Rl = v.y, g.Zh = v.z, g.Zl = v.w;
+    g.Rrh = __shfl_sync(FDX_FULL_MASK, g.Rh, 0), g.Rrl = __shfl_sync(FDX_FULL_MASK, g.Rl, 0);
+    g.Zrh = __shfl_sync(FDX_FULL_MASK, g.Zh, 0), g.Zrl = __shfl_sync(FDX_FULL_MASK, g.Zl, 0);
+    g.dRl = (g.Rh - g.Rrh) + (g.Rl - g.Rrl);
+    g.dZl = (g.Zh - g.Zrh) + (g.Zl - g.Zrl);
+    return g;
+}
+
+struct PairAcc {
+    ff s0;           // sum of w / prod den (Hosemann) or w * sinc product
+    ff sb[3];        // adjoint: sum of (w / prod den) (1/den_i - 1)
+    ff ss, sg;       // adjoint: sums of dw/dsigma / prod den and dw/dgamma / prod den
+    int32_t cnt;     // count mode: in-support terms
+};
+
+// Evaluate the pair; `rec` is the reflection record in shared memory, `buf`
+// (and `buf2` in adjoint mode) the warp's node buffers of NB entries.  Returns false when no
+// node can be in any lane's support (nothing accumulated).
+template <int LS, int MODE, int NB = NODE_BUF>
+__device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix &g, const float *rec, float4 *buf,
+                                          float2 *buf2, int lane, PairAcc &acc) {
+    const int n = P.n_nodes;
+    // (p - D)/r0 in the local frame, FP32 (only bounds the node range)
+    const float dZ = (g.Zh - rec[REC_ZD]) + (g.Zl - rec[REC_ZD + 1]);
+    const float dR = (g.Rh - rec[REC_RD]) + (g.Rl - rec[REC_RD + 1]);
+    const float P0 = fmaf(dZ, rec[REC_NFR], dR * rec[REC_EFR]);
+    const float P1 = fmaf(dZ, rec[REC_NFR + 1], dR * rec[REC_EFR + 1]);
+    const float P2 = fmaf(dZ, rec[REC_NFR + 2], dR * rec[REC_EFR + 2]);
+    float d1lo = 3.0e38f, d1hi = -3.0e38f, d2lo = 3.0e38f, d2hi = -3.0e38f;
+    bool degenerate = false;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sg = s ? -1.0f : 1.0f;
+            const float X0 = 1.0f + P0 + sg * rec[REC_CR + 3 * v];
+            const float X1 = P1 + sg * rec[REC_CR + 3 * v + 1];
+            const float X2 = P2 + sg * rec[REC_CR + 3 * v + 2];
+            degenerate |= !(X0 > 0.05f);
+            const float inv = 1.0f / X0;
+            const float d1 = X1 * inv, d2 = X2 * inv;
+            d1lo = fminf(d1lo, d1), d1hi = fmaxf(d1hi, d1);
+            d2lo = fminf(d2lo, d2), d2hi = fmaxf(d2hi, d2);
+        }
+    }
+    int j0 = n, j1 = -1, m0 = n, m1 = -1;
+    if (g.valid) {
+        if (degenerate) {
+            j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
+        } else {
+            const float T = P.T, ih = P.inv_h;
+            j0 = max(0, (int)ceilf(fmaf(d1lo + T, ih, -0.5f)) - 1);
+            j1 = min(n - 1, (int)floorf(fmaf(d1hi + T, ih, -0.5f)) + 1);
+            m0 = max(0, (int)ceilf(fmaf(d2lo + T, ih, -0.5f)) - 1);
+            m1 = min(n - 1, (int)floorf(fmaf(d2hi + T, ih, -0.5f)) + 1);
+        }
+    }
+    const int J0 = __reduce_min_sync(FDX_FULL_MASK, j0), J1 = __reduce_max_sync(FDX_FULL_MASK, j1);
+    const int M0 = __reduce_min_sync(FDX_FULL_MASK, m0), M1 = __reduce_max_sync(FDX_FULL_MASK, m1);
+    if (J0 > J1 || M0 > M1) return false;
+
+    // tau_i = a_i . (p - p_ref), small
+    float tau[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) tau[i] = g.valid ? fmaf(g.dZl, P.AZ[i], g.dRl * rec[REC_AR + i]) : 3.0e30f;
+    float la[3], tm[3], cf[3][7];
+    {
+        const float Qc[6] = FDX_SINPI2_C;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            la[i] = rec[REC_LA + i], tm[i] = rec[REC_TM + i];
+            const float lb = rec[REC_LB + i];
+            cf[i][0] = la[i];
+#pragma unroll
+            for (int k = 1; k < 7; ++k) cf[i][k] = lb * Qc[k - 1];
+        }
+    }
+    const float hh[3] = {rec[REC_H], rec[REC_H + 1], rec[REC_H + 2]};
+    const float E1[3] = {rec[REC_E1], rec[REC_E1 + 1], rec[REC_E1 + 2]};
+    const float E2[3] = {rec[REC_E2], rec[REC_E2 + 1], rec[REC_E2 + 2]};
+
+    // (p_ref - D)/r0 in the local frame, float-float (every lane computes it for lane 0's pixel)
+    const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
+    const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
+    ff dP[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        dP[q] = ff_add(ff_mul(dZr, ff{rec[REC_NFR + q], rec[REC_NFR + 3 + q]}),
+                       ff_mul(dRr, ff{rec[REC_EFR + q], rec[REC_EFR + 3 + q]}));
+    }
+
+    // warp-wide tau box: a node can be in some lane's support only if sigma_i
+    // lies within [min tau_i - tm_i, max tau_i + tm_i] for every i
+    float tc[3], th[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float lo = warp_min(g.valid ? tau[i] : 3.0e38f), hi = warp_max(g.valid ? tau[i] : -3.0e38f);
+        tc[i] = 0.5f * (lo + hi);
+        th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
+    }
+    const int ncols = M1 - M0 + 1;
+    const int total = (J1 - J0 + 1) * ncols;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int step_r = 32 / ncols, step_c = 32 - step_r * ncols;
+    int jj = J0 + lane / ncols, mm = M0 + lane % ncols;  // this lane's node in the batch
+    int nlive = 0;
+    for (int b0 = 0; b0 < total; b0 += 32) {
+        const int idx = b0 + lane;
+        bool live = false;
+        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 val2 = make_float2(0.f, 0.f);
+        if (idx < total) {
+            const size_t k = (size_t)jj * n + mm;
+            const float4 na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
+            // u = s_k/r0 - p_ref/r0 in the local frame = (c - 1, c d1, c d2) - dP
+            const float u0 = (na.x - dP[0].hi) + (na.y - dP[0].lo);
+            const float u1 = (na.z - dP[1].hi) + (na.w - dP[1].lo);
+            const float u2 = (nb.x - dP[2].hi) + (nb.y - dP[2].lo);
+            float sg[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) sg[i] = fmaf(hh[i], u0, fmaf(E1[i], u1, E2[i] * u2));
+            live = (fabsf(sg[0] - tc[0]) <= th[0]) & (fabsf(sg[1] - tc[1]) <= th[1]) & (fabsf(sg[2] - tc[2]) <= th[2]);
+            val = make_float4(sg[0], sg[1], sg[2], nb.z);
+            if (MODE == MODE_ADJ) val2 = P.dnodes[k];
+        }
+        jj += step_r, mm += step_c;
+        if (mm > M1) mm -= ncols, ++jj;
+        const unsigned bal = __ballot_sync(FDX_FULL_MASK, live);
+        if (live) {
+            const int pos = nlive + __popc(bal & lt_mask);
+            buf[pos] = val;
+            if (MODE == MODE_ADJ) buf2[pos] = val2;
+        }
+        nlive += __popc(bal);
+        if (nlive > NB - 32 || (b0 + 32 >= total && nlive > 0)) {
+            __syncwarp();
+            for (int q0 = 0; q0 < nlive; q0 += 32) {
+                const int qe = min(q0 + 32, nlive);
+                float r0 = 0.0f, rb0 = 0.0f, rb1 = 0.0f, rb2 = 0.0f, rss = 0.0f, rsg = 0.0f;
+#pragma unroll 4
+                for (int q = q0; q < qe; ++q) {
+                    const float4 nq = buf[q];
+                    const float ta = tau[0] - nq.x, tb = tau[1] - nq.y, tcc = tau[2] - nq.z;
+                    const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tcc) <= tm[2]);
+                    if (MODE == MODE_CNT) {
+                        acc.cnt += in ? 1 : 0;
+                    } else if (LS == FDX_LINESHAPE_HOSEMANN) {
+                        const float da = hosemann_den(ta, cf[0]), db = hosemann_den(tb, cf[1]);
+                        const float dc = hosemann_den(tcc, cf[2]);
+                        const float dab = da * db;
+                        const float rp = rcp_approx(dab * dc);
+                        const float kv = nq.w * rp;
+                        r0 += in ? kv : 0.0f;
+                        if (MODE == MODE_ADJ) {
+                            const float2 dw = buf2[q];
+                            const float dbc = db * dc, dac = da * dc;
+                            // 1/den_i = (product of the other two) * rp
+                            rb0 += in ? kv * fmaf(dbc, rp, -1.0f) : 0.0f;
+                            rb1 += in ? kv * fmaf(dac, rp, -1.0f) : 0.0f;
+                            rb2 += in ? kv * fmaf(dab, rp, -1.0f) : 0.0f;
+                            rss += in ? dw.x * rp : 0.0f;
+                            rsg += in ? dw.y * rp : 0.0f;
+                        }
+                    } else {
+                        const float kv = nq.w * sinc_term(ta, tb, tcc, la);
+                        r0 += in ? kv : 0.0f;
+                    }
+                }
+                if (MODE != MODE_CNT) acc.s0 = ff_add_f(acc.s0, r0);
+                if (MODE == MODE_ADJ) {
+                    acc.sb[0] = ff_add_f(acc.sb[0], rb0);
+                    acc.sb[1] = ff_add_f(acc.sb[1], rb1);
+                    acc.sb[2] = ff_add_f(acc.sb[2], rb2);
+                    acc.ss = ff_add_f(acc.ss, rss);
+                    acc.sg = ff_add_f(acc.sg, rsg);
+                }
+            }
+            nlive = 0;
+            __syncwarp();
+        }
+    }
+    return true;
+}
+
+// Copy a 64-float reflection record into the warp's shared slot.
+__device__ __forceinline__ void load_record(const float *recs, int r, float *rec, int lane) {
+    const float *grec = recs + (size_t)r * REC_SIZE;
+    __syncwarp();
+    rec[lane] = grec[lane];
+    rec[lane + 32] = grec[lane + 32];
+    __syncwarp();
+}
+
+}  // namespace fdx

@@ -63,11 +63,12 @@ const WeidemanCoeffs &weideman_coeffs() {
     return wc;
 }
 
-__device__ double faddeeva_re(double x, double y, const WeidemanCoeffs &wc) {
-    // w(z) for z = x + i y, y >= 0.  L - i z = (L + y) - i x ; L + i z = (L - y) + i x.
+// w(z) for z = x + i y, y >= 0, as (re, im).  L - i z = (L + y) - i x ;
+// L + i z = (L - y) + i x.
+__device__ void faddeeva(double x, double y, const WeidemanCoeffs &wc, double &wr, double &wi) {
     const double L = wc.L;
-    const double dr = L + y, di = -x;          // den = L - i z
-    const double nr = L - y, ni = x;           // num = L + i z
+    const double dr = L + y, di = -x;  // den = L - i z
+    const double nr = L - y, ni = x;   // num = L + i z
     const double dd = dr * dr + di * di;
     const double Zr = (nr * dr + ni * di) / dd, Zi = (ni * dr - nr * di) / dd;
     double pr = wc.a[FDX_WEIDEMAN_N - 1], pi = 0.0;
@@ -79,17 +80,45 @@ __device__ double faddeeva_re(double x, double y, const WeidemanCoeffs &wc) {
     // 2 p / den^2 + 1 / (sqrt(pi) den)
     const double d2r = dr * dr - di * di, d2i = 2.0 * dr * di;
     const double d2d = d2r * d2r + d2i * d2i;
-    const double t1r = 2.0 * (pr * d2r + pi * d2i) / d2d;
-    const double t2r = dr / (dd * sqrt(FDX_PI));
-    return t1r + t2r;
+    const double t1r = 2.0 * (pr * d2r + pi * d2i) / d2d, t1i = 2.0 * (pi * d2r - pr * d2i) / d2d;
+    const double isp = 1.0 / sqrt(FDX_PI);
+    wr = t1r + isp * dr / dd;
+    wi = t1i - isp * di / dd;
 }
 
-// Angular shape g(Delta; sigma, gamma), g(0) = 1 (Sect. "Angular peak shapes").
-__device__ double angular_shape(double D, double sigma, double gamma, const WeidemanCoeffs &wc) {
-    if (gamma == 0.0) return exp(-D * D / (2.0 * sigma * sigma));
-    if (sigma < 1e-12) return gamma * gamma / (D * D + gamma * gamma);
+// Angular shape g(Delta; sigma, gamma), g(0) = 1 (Sect. "Angular peak shapes"),
+// and its derivatives.  Voigt: g = Re w(z)/Re w(z0), z = (Delta + i gamma)/(sigma sqrt 2),
+// z0 = i gamma/(sigma sqrt 2); w'(z) = -2 z w(z) + 2i/sqrt(pi), dz/dsigma = -z/sigma,
+// dz/dgamma = i/(sigma sqrt 2).  The pure-Gaussian branch has no gamma derivative.
+__device__ double angular_shape(double D, double sigma, double gamma, const WeidemanCoeffs &wc, double &dgs,
+                                double &dgg) {
+    if (gamma == 0.0) {
+        const double g = exp(-D * D / (2.0 * sigma * sigma));
+        dgs = g * D * D / (sigma * sigma * sigma);
+        dgg = 0.0;
+        return g;
+    }
+    if (sigma < 1e-12) {
+        const double den = D * D + gamma * gamma;
+        dgs = 0.0;
+        dgg = 2.0 * gamma * D * D / (den * den);
+        return gamma * gamma / den;
+    }
     const double s = 1.0 / (sigma * sqrt(2.0));
-    return faddeeva_re(D * s, gamma * s, wc) / faddeeva_re(0.0, gamma * s, wc);
+    double w1r, w1i, w0r, w0i;
+    const double x1 = D * s, y = gamma * s;
+    faddeeva(x1, y, wc, w1r, w1i);
+    faddeeva(0.0, y, wc, w0r, w0i);
+    const double c2 = 2.0 / sqrt(FDX_PI);
+    // w' = -2 z w + 2i/sqrt(pi)
+    const double d1r = -2.0 * (x1 * w1r - y * w1i), d1i = -2.0 * (x1 * w1i + y * w1r) + c2;
+    const double d0r = -2.0 * (0.0 * w0r - y * w0i), d0i = -2.0 * (0.0 * w0i + y * w0r) + c2;
+    // d Re w / dsigma = Re(w' * (-z/sigma)); d Re w / dgamma = Re(w' * i s) = -s Im w'
+    const double a1s = -(d1r * x1 - d1i * y) / sigma, a0s = -(d0r * 0.0 - d0i * y) / sigma;
+    const double a1g = -s * d1i, a0g = -s * d0i;
+    dgs = (a1s * w0r - w1r * a0s) / (w0r * w0r);
+    dgg = (a1g * w0r - w1r * a0g) / (w0r * w0r);
+    return w1r / w0r;
 }
 
 // ---------------------------------------------------------------------------
@@ -135,8 +164,10 @@ __global__ void nodes_kernel(NodeParams p, WeidemanCoeffs wc) {
     const double q = sqrt(1.0 + rho2), c = 1.0 / q;
     const double cm1 = -rho2 / (q * (1.0 + q));
     const double Delta = atan(sqrt(rho2));
-    const double g = angular_shape(Delta, p.sigma, p.gamma, wc);
-    const double w = p.sigma_r * sqrt(2.0 * FDX_PI) * g * c * c * c * p.h * p.h;
+    double dgs, dgg;
+    const double g = angular_shape(Delta, p.sigma, p.gamma, wc, dgs, dgg);
+    const double pre = p.sigma_r * sqrt(2.0 * FDX_PI) * c * c * c * p.h * p.h;
+    const double w = pre * g;
     float4 a, b;
     split_double(cm1, a.x, a.y);
     split_double(d1 * c, a.z, a.w);
@@ -146,6 +177,7 @@ __global__ void nodes_kernel(NodeParams p, WeidemanCoeffs wc) {
     const size_t k = (size_t)j * p.n + m;
     p.nodes[2 * k] = a;
     p.nodes[2 * k + 1] = b;
+    if (p.dnodes) p.dnodes[k] = make_float2((float)(pre * dgs), (float)(pre * dgg));
 }
 
 // ---------------------------------------------------------------------------
@@ -237,6 +269,12 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
     }
     o[REC_FR] = (float)fr;
     for (int k = REC_FR + 1; k < REC_SIZE; ++k) o[k] = 0.0f;
+    o[REC_R2B] = (float)(r0 * r0 * beta[0] * beta[1] * beta[2]);
+    for (int i = 0; i < 3; ++i) {
+        o[REC_BETA + i] = (float)beta[i];
+        o[REC_DBF + i] = beta[i] < 1.0 ? (float)(2.0 * beta[i] / (1.0 - beta[i] * beta[i])) : 0.0f;
+    }
+    o[REC_M] = (float)M;
     const double psiD = atan2(RD, ZD);
     const double dpsi = atan(p.T * sqrt(2.0)) + (rhoB < r0 ? asin(rhoB / r0) : FDX_PI);
     p.reach[r] = make_float4((float)r0, (float)(rhoB * (1.0 + 1e-4) + 1e-6), (float)psiD,

@@ -148,6 +148,11 @@ __global__ void sf_reduce_kernel(SFParams p) {
     }
 }
 
+cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
+    sf_pack_atoms_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s) {
     if (p.n_refl <= 0) return cudaSuccess;
     sf_pack_atoms_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);

@@ -308,3 +308,65 @@ class Simulation:
         counts = torch.empty_like(self.image, dtype=torch.int32)
         fdx_pattern_evals(self.prob, counts, self.ws, stream)
         return counts
+
+
+# ---------------------------------------------------------------------------
+# refinement path: loss and the hand-written adjoint
+# ---------------------------------------------------------------------------
+
+class Grads(C.Structure):
+    _fields_ = [("dfrac", C.c_void_p), ("dB", C.c_void_p), ("dglobal", C.c_void_p), ("dM", C.c_void_p)]
+
+
+def _bind_refine(L):
+    if getattr(L, "_refine_bound", False):
+        return L
+    L.fdx_backward_workspace_size.restype = C.c_size_t
+    L.fdx_backward_workspace_size.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32]
+    L.fdx_pattern_backward.argtypes = [C.POINTER(Problem), C.POINTER(Atoms), C.c_void_p, C.c_void_p,
+                                       C.POINTER(Grads), C.c_void_p, C.c_size_t, C.c_void_p]
+    L.fdx_loss_workspace_size.restype = C.c_size_t
+    L.fdx_loss_workspace_size.argtypes = [C.c_int64]
+    L.fdx_loss.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_size_t, C.c_void_p]
+    L._refine_bound = True
+    return L
+
+
+def fdx_backward_workspace_size(problem, n_atoms: int, n_elem: int) -> int:
+    return int(_bind_refine(lib()).fdx_backward_workspace_size(C.byref(problem), int(n_atoms), int(n_elem)))
+
+
+def fdx_pattern_backward(problem, datoms: DeviceAtoms, F, dL_dI, dfrac=None, dB=None, dglobal=None, dM=None,
+                         workspace=None, stream=None):
+    """Gradients of a loss w.r.t. fractional coordinates, B, sizes, g, sigma
+    and gamma given dL/dI; tensors passed as None are not written."""
+    import torch
+    L = _bind_refine(lib())
+    a = datoms.struct()
+    need = fdx_backward_workspace_size(problem, a.n_atoms, a.n_elem)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=dL_dI.device)
+    g = Grads(dfrac.data_ptr() if dfrac is not None else None, dB.data_ptr() if dB is not None else None,
+              dglobal.data_ptr() if dglobal is not None else None, dM.data_ptr() if dM is not None else None)
+    _check(L.fdx_pattern_backward(C.byref(problem), C.byref(a), _ptr(F), _ptr(dL_dI), C.byref(g), _ptr(workspace),
+                                  int(workspace.numel()), _stream(stream)), "fdx_pattern_backward")
+    return dfrac, dB, dglobal, dM
+
+
+def fdx_loss_workspace_size(n_px: int) -> int:
+    return int(_bind_refine(lib()).fdx_loss_workspace_size(int(n_px)))
+
+
+def fdx_loss(I, I_target, mask=None, loss_out=None, dL_dI=None, workspace=None, stream=None):
+    """L = sum m (I - I_t)^2 / (I_t + 1) (device float64 scalar) and dL/dI."""
+    import torch
+    L = _bind_refine(lib())
+    n = I.numel()
+    if loss_out is None:
+        loss_out = torch.empty((), dtype=torch.float64, device=I.device)
+    if workspace is None:
+        workspace = torch.empty(fdx_loss_workspace_size(n), dtype=torch.uint8, device=I.device)
+    _check(L.fdx_loss(n, _ptr(I), _ptr(I_target), _ptr(mask), _ptr(loss_out), _ptr(dL_dI), _ptr(workspace),
+                      int(workspace.numel()), _stream(stream)), "fdx_loss")
+    return loss_out, dL_dI
