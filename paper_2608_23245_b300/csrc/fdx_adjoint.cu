@@ -29,7 +29,7 @@
 namespace fdx {
 
 static constexpr int ADJ_ITEM_VALS = 6;
-static constexpr int ADJ_NODE_BUF = 384;  // keeps the CTA's static shared memory under 48 KB
+static constexpr int ADJ_NODE_BUF = 224;  // keeps the CTA's static shared memory under 48 KB
 
 __device__ __forceinline__ bool reach_overlap(float4 q, float4 b) {
     // q = (r0, rho_B, psi_D, dpsi); b = (rmin, rmax, psimin, psimax)
@@ -79,6 +79,8 @@ __global__ void band_bounds_kernel(AdjParams A) {
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
     __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];
     __shared__ float2 s_dn[PAIR_WARPS][ADJ_NODE_BUF];
+    __shared__ float4 s_sc[PAIR_WARPS][ADJ_NODE_BUF];
+    __shared__ float2 s_sc2[PAIR_WARPS][ADJ_NODE_BUF];
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
                 PairAcc pa;
                 pa.s0 = pa.sb[0] = pa.sb[1] = pa.sb[2] = pa.ss = pa.sg = ff{0.0f, 0.0f};
                 pa.cnt = 0;
-                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF>(A.P, g, rec, s_nodes[warp], s_dn[warp], lane, pa))
+                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF>(A.P, g, rec, s_nodes[warp], s_dn[warp], s_sc[warp],
+                                                                          s_sc2[warp], lane, pa))
                     continue;
                 const double cd = (double)c;
                 acc[0] += warp_sum_d(cd * ((double)pa.s0.hi + (double)pa.s0.lo));

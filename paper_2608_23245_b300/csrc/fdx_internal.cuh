@@ -116,6 +116,8 @@ enum RecField {
     REC_BETA = 51, // beta_i
     REC_M = 54,    // M
     REC_DBF = 55,  // 2 beta_i / (1 - beta_i^2), 0 when beta_i is clamped at 1 (adjoint)
+    REC_AR0 = 58,  // |a_i| r0: Lipschitz constant of sigma_i along the gnomonic plane
+    REC_SLB = 61,  // sqrt(1 - beta_i^2) (Hosemann)
     REC_SIZE = 64
 };
 

@@ -73,6 +73,24 @@ __device__ __forceinline__ float sinc_term(float ta, float tb, float tc, const f
     return q * __fdividef(num, den);
 }
 
+// sin(pi x), cos(pi x) for |x| < 2^20: x = q/2 + f with q = rint(2x), |f| <= 1/4,
+// so pi x = q pi/2 + pi f; sin(pi f), cos(pi f) from the sin(2 pi r)/cos(2 pi r)
+// polynomials at r = f/2, then a rotation by q quarter turns.
+__device__ __forceinline__ void sincospi_f(float x, float &s, float &c) {
+    const float q = rintf(2.0f * x);
+    const float r = 0.5f * fmaf(-0.5f, q, x);
+    const float Sc[4] = FDX_SIN2PI_C;
+    const float Cc[5] = FDX_COS2PI_C;
+    const float r2 = r * r;
+    const float sn = r * horner(Sc, r2);
+    const float cs = horner(Cc, r2);
+    const int qi = (int)q;
+    const float s1 = (qi & 1) ? cs : sn;
+    const float c1 = (qi & 1) ? -sn : cs;
+    s = (qi & 2) ? -s1 : s1;
+    c = (qi & 2) ? -c1 : c1;
+}
+
 // The lane's pixel and the warp's reference pixel (lane 0), float-float.
 struct PatchPix {
     float Rh, Rl, Zh, Zl;      // this lane's (R, Z)
@@ -102,12 +120,20 @@ struct PairAcc {
     int32_t cnt;     // count mode: in-support terms
 };
 
-// Evaluate the pair; `rec` is the reflection record in shared memory, `buf`
-// (and `buf2` in adjoint mode) the warp's node buffers of NB entries.  Returns false when no
-// node can be in any lane's support (nothing accumulated).
+// Evaluate the pair; `rec` is the reflection record in shared memory; `buf`
+// (sigma_a, sigma_b, sigma_c, w), `buf2` (adjoint: dw/dsigma, dw/dgamma) and,
+// for the Hosemann lineshape, `bsc`/`bsc2` (cos, sin of pi sigma_i) are the
+// warp's node buffers of NB entries.  Returns false when no node can be in
+// any lane's support (nothing accumulated).
+//
+// Hosemann denominators by angle addition: with t = tau - sigma,
+//   sin(pi t) = sin(pi tau) cos(pi sigma) - cos(pi tau) sin(pi sigma),
+//   den_i = beta_i^2 + (1 - beta_i^2) sin^2(pi t_i),
+// sin/cos(pi tau) once per lane and pair, sin/cos(pi sigma) once per staged
+// node, so the per-evaluation cost is 4 operations per axis.
 template <int LS, int MODE, int NB = NODE_BUF>
 __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix &g, const float *rec, float4 *buf,
-                                          float2 *buf2, int lane, PairAcc &acc) {
+                                          float2 *buf2, float4 *bsc, float2 *bsc2, int lane, PairAcc &acc) {
     const int n = P.n_nodes;
     // (p - D)/r0 in the local frame, FP32 (only bounds the node range)
     const float dZ = (g.Zh - rec[REC_ZD]) + (g.Zl - rec[REC_ZD + 1]);
@@ -151,19 +177,15 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     // tau_i = a_i . (p - p_ref), small
     float tau[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) tau[i] = g.valid ? fmaf(g.dZl, P.AZ[i], g.dRl * rec[REC_AR + i]) : 3.0e30f;
-    float la[3], tm[3], cf[3][7];
-    {
-        const float Qc[6] = FDX_SINPI2_C;
+    for (int i = 0; i < 3; ++i) tau[i] = g.valid ? fmaf(g.dZl, P.AZ[i], g.dRl * rec[REC_AR + i]) : 1.0e4f;
+    float st[3], ct[3];
+    if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            la[i] = rec[REC_LA + i], tm[i] = rec[REC_TM + i];
-            const float lb = rec[REC_LB + i];
-            cf[i][0] = la[i];
-#pragma unroll
-            for (int k = 1; k < 7; ++k) cf[i][k] = lb * Qc[k - 1];
-        }
+        for (int i = 0; i < 3; ++i) sincospi_f(tau[i], st[i], ct[i]);
     }
+    float la[3], tm[3], slb[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) la[i] = rec[REC_LA + i], tm[i] = rec[REC_TM + i], slb[i] = rec[REC_SLB + i];
     const float hh[3] = {rec[REC_H], rec[REC_H + 1], rec[REC_H + 2]};
     const float E1[3] = {rec[REC_E1], rec[REC_E1 + 1], rec[REC_E1 + 2]};
     const float E2[3] = {rec[REC_E2], rec[REC_E2 + 1], rec[REC_E2 + 2]};
@@ -187,42 +209,37 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
         tc[i] = 0.5f * (lo + hi);
         th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
     }
-    const int ncols = M1 - M0 + 1;
-    const int total = (J1 - J0 + 1) * ncols;
-    const unsigned lt_mask = (1u << lane) - 1u;
-    const int step_r = 32 / ncols, step_c = 32 - step_r * ncols;
-    int jj = J0 + lane / ncols, mm = M0 + lane % ncols;  // this lane's node in the batch
-    int nlive = 0;
-    for (int b0 = 0; b0 < total; b0 += 32) {
-        const int idx = b0 + lane;
-        bool live = false;
-        float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-        float2 val2 = make_float2(0.f, 0.f);
-        if (idx < total) {
-            const size_t k = (size_t)jj * n + mm;
-            const float4 na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
-            // u = s_k/r0 - p_ref/r0 in the local frame = (c - 1, c d1, c d2) - dP
-            const float u0 = (na.x - dP[0].hi) + (na.y - dP[0].lo);
-            const float u1 = (na.z - dP[1].hi) + (na.w - dP[1].lo);
-            const float u2 = (nb.x - dP[2].hi) + (nb.y - dP[2].lo);
-            float sg[3];
+    const int nrows = J1 - J0 + 1, ncols = M1 - M0 + 1;
+    // Block culling: the bounding box is cut into 4 x 8-node blocks; a block is
+    // skipped when, at its centre, sigma_i is farther from the warp's tau
+    // window than |a_i| r0 rho_b, rho_b being the block's half-diagonal in the
+    // gnomonic plane (|d s / d d| <= r0, so sigma_i varies by at most that).
+    constexpr int BR = 4, BC = 8;
+    const int nbr = (nrows + BR - 1) / BR, nbc = (ncols + BC - 1) / BC, nblk = nbr * nbc;
+    const float hgrid = 1.0f / P.inv_h;
+    const float rho_b = hgrid * 3.8079f;  // sqrt(1.5^2 + 3.5^2)
+    float bw[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) sg[i] = fmaf(hh[i], u0, fmaf(E1[i], u1, E2[i] * u2));
-            live = (fabsf(sg[0] - tc[0]) <= th[0]) & (fabsf(sg[1] - tc[1]) <= th[1]) & (fabsf(sg[2] - tc[2]) <= th[2]);
-            val = make_float4(sg[0], sg[1], sg[2], nb.z);
-            if (MODE == MODE_ADJ) val2 = P.dnodes[k];
-        }
-        jj += step_r, mm += step_c;
-        if (mm > M1) mm -= ncols, ++jj;
-        const unsigned bal = __ballot_sync(FDX_FULL_MASK, live);
-        if (live) {
-            const int pos = nlive + __popc(bal & lt_mask);
-            buf[pos] = val;
-            if (MODE == MODE_ADJ) buf2[pos] = val2;
-        }
-        nlive += __popc(bal);
-        if (nlive > NB - 32 || (b0 + 32 >= total && nlive > 0)) {
+    for (int i = 0; i < 3; ++i) bw[i] = th[i] + rec[REC_AR0 + i] * rho_b + 1e-4f;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const int bj_lane = lane / BC, bm_lane = lane % BC;  // this lane's node inside a block
+    int nlive = 0;
+    // Walk the compacted nodes (all lanes, warp-uniform bounds) and empty the buffer.
+    auto flush = [&]() {
             __syncwarp();
+            if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
+                for (int q = lane; q < nlive; q += 32) {
+                    const float4 nq = buf[q];
+                    float sa, ca, sb, cb, sc, cc;
+                    sincospi_f(nq.x, sa, ca);
+                    sincospi_f(nq.y, sb, cb);
+                    sincospi_f(nq.z, sc, cc);
+                    // scaled by sqrt(1 - beta_i^2): den_i = beta_i^2 + (scaled sin(pi t_i))^2
+                    bsc[q] = make_float4(slb[0] * ca, slb[0] * sa, slb[1] * cb, slb[1] * sb);
+                    bsc2[q] = make_float2(slb[2] * cc, slb[2] * sc);
+                }
+                __syncwarp();
+            }
             for (int q0 = 0; q0 < nlive; q0 += 32) {
                 const int qe = min(q0 + 32, nlive);
                 float r0 = 0.0f, rb0 = 0.0f, rb1 = 0.0f, rb2 = 0.0f, rss = 0.0f, rsg = 0.0f;
@@ -234,8 +251,14 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                     if (MODE == MODE_CNT) {
                         acc.cnt += in ? 1 : 0;
                     } else if (LS == FDX_LINESHAPE_HOSEMANN) {
-                        const float da = hosemann_den(ta, cf[0]), db = hosemann_den(tb, cf[1]);
-                        const float dc = hosemann_den(tcc, cf[2]);
+                        const float4 sc4 = bsc[q];
+                        const float2 sc2 = bsc2[q];
+                        const float sa = fmaf(st[0], sc4.x, -ct[0] * sc4.y);
+                        const float sb = fmaf(st[1], sc4.z, -ct[1] * sc4.w);
+                        const float sc = fmaf(st[2], sc2.x, -ct[2] * sc2.y);
+                        const float da = fmaf(sa, sa, la[0]);
+                        const float db = fmaf(sb, sb, la[1]);
+                        const float dc = fmaf(sc, sc, la[2]);
                         const float dab = da * db;
                         const float rp = rcp_approx(dab * dc);
                         const float kv = nq.w * rp;
@@ -264,10 +287,65 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                     acc.sg = ff_add_f(acc.sg, rsg);
                 }
             }
-            nlive = 0;
-            __syncwarp();
+        nlive = 0;
+        __syncwarp();
+    };
+    for (int blk0 = 0; blk0 < nblk; blk0 += 32) {
+        bool blive = false;
+        {
+            const int blk = blk0 + lane;
+            if (blk < nblk) {
+                const int bj = blk / nbc, bm = blk - bj * nbc;
+                const float d1 = -P.T + (J0 + bj * BR + 0.5f * (BR - 1) + 0.5f) * hgrid;
+                const float d2 = -P.T + (M0 + bm * BC + 0.5f * (BC - 1) + 0.5f) * hgrid;
+                const float rho2 = fmaf(d1, d1, d2 * d2);
+                const float q = sqrtf(1.0f + rho2);
+                const float c = 1.0f / q;
+                const float u0 = -rho2 / (q * (1.0f + q)) - dP[0].hi;
+                const float u1 = d1 * c - dP[1].hi, u2 = d2 * c - dP[2].hi;
+                blive = true;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float sgc = fmaf(hh[i], u0, fmaf(E1[i], u1, E2[i] * u2));
+                    blive &= fabsf(sgc - tc[i]) <= bw[i];
+                }
+            }
+        }
+        unsigned bmask = __ballot_sync(FDX_FULL_MASK, blive);
+        while (bmask) {
+            const int blk = blk0 + __ffs(bmask) - 1;
+            bmask &= bmask - 1;
+            const int bj = blk / nbc, bm = blk - bj * nbc;
+            const int jj = J0 + bj * BR + bj_lane, mm = M0 + bm * BC + bm_lane;
+            bool live = false;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 val2 = make_float2(0.f, 0.f);
+            if (jj <= J1 && mm <= M1) {
+                const size_t k = (size_t)jj * n + mm;
+                const float4 na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
+                // u = s_k/r0 - p_ref/r0 in the local frame = (c - 1, c d1, c d2) - dP
+                const float u0 = (na.x - dP[0].hi) + (na.y - dP[0].lo);
+                const float u1 = (na.z - dP[1].hi) + (na.w - dP[1].lo);
+                const float u2 = (nb.x - dP[2].hi) + (nb.y - dP[2].lo);
+                float sg[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) sg[i] = fmaf(hh[i], u0, fmaf(E1[i], u1, E2[i] * u2));
+                live = (fabsf(sg[0] - tc[0]) <= th[0]) & (fabsf(sg[1] - tc[1]) <= th[1]) &
+                       (fabsf(sg[2] - tc[2]) <= th[2]);
+                val = make_float4(sg[0], sg[1], sg[2], nb.z);
+                if (MODE == MODE_ADJ) val2 = P.dnodes[k];
+            }
+            const unsigned bal = __ballot_sync(FDX_FULL_MASK, live);
+            if (live) {
+                const int pos = nlive + __popc(bal & lt_mask);
+                buf[pos] = val;
+                if (MODE == MODE_ADJ) buf2[pos] = val2;
+            }
+            nlive += __popc(bal);
+            if (nlive > NB - 32) flush();
         }
     }
+    if (nlive > 0) flush();
     return true;
 }
 

@@ -13,9 +13,13 @@
 
 namespace fdx {
 
+static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp; 4 warps x 288 x 40 B keeps static shared memory < 48 KB
+
 template <int LS, int MODE>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternParams P) {
-    __shared__ float4 s_nodes[PAIR_WARPS][NODE_BUF];
+    __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];
+    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1];
+    __shared__ float2 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1];
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -48,7 +52,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
             PairAcc pa;
             pa.s0 = {0.0f, 0.0f};
             pa.cnt = 0;
-            if (!eval_pair<LS, MODE>(P, g, rec, buf, nullptr, lane, pa)) continue;
+            if (!eval_pair<LS, MODE, FWD_NODE_BUF>(P, g, rec, buf, nullptr, s_sc[warp], s_sc2[warp], lane, pa)) continue;
             if (MODE == MODE_CNT)
                 cnt += pa.cnt;
             else

@@ -271,6 +271,8 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
     for (int k = REC_FR + 1; k < REC_SIZE; ++k) o[k] = 0.0f;
     o[REC_R2B] = (float)(r0 * r0 * beta[0] * beta[1] * beta[2]);
     for (int i = 0; i < 3; ++i) {
+        o[REC_AR0 + i] = (float)(p.alen[i] * r0);
+        o[REC_SLB + i] = p.lineshape == FDX_LINESHAPE_HOSEMANN ? (float)sqrt(fmax(0.0, 1.0 - beta[i] * beta[i])) : 0.0f;
         o[REC_BETA + i] = (float)beta[i];
         o[REC_DBF + i] = beta[i] < 1.0 ? (float)(2.0 * beta[i] / (1.0 - beta[i] * beta[i])) : 0.0f;
     }
