@@ -103,27 +103,27 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
                 mask &= mask - 1;
                 const int pidx = pj0 * A.npx + base + bit;
                 const int px0 = 8 * (pidx % A.npx), py0 = 4 * (pidx / A.npx);
-                const PatchPix g = load_patch(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
+                const PatchPix<1> g = load_patch<1>(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
                 float c = 0.0f;
-                if (g.valid) {
+                if (g.valid[0]) {
                     const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
-                    const double R = (double)g.Rh + (double)g.Rl;
+                    const double R = (double)g.Rh[0] + (double)g.Rl[0];
                     c = (float)((double)A.gI[(size_t)py * A.P.nx + px] * A.P.delta_L / (R + A.P.delta_L));
                 }
                 if (__ballot_sync(FDX_FULL_MASK, c != 0.0f) == 0) continue;
-                PairAcc pa;
-                pa.s0 = pa.sb[0] = pa.sb[1] = pa.sb[2] = pa.ss = pa.sg = ff{0.0f, 0.0f};
-                pa.cnt = 0;
-                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF>(A.P, g, rec, s_nodes[warp], s_dn[warp], s_sc[warp],
-                                                                          s_sc2[warp], lane, pa))
+                PairAcc pa[1];
+                clear(pa[0]);
+                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, 1>(A.P, g, rec, s_nodes[warp], s_dn[warp],
+                                                                             s_sc[warp], s_sc2[warp], lane, pa))
                     continue;
                 const double cd = (double)c;
-                acc[0] += warp_sum_d(cd * ((double)pa.s0.hi + (double)pa.s0.lo));
-                acc[1] += warp_sum_d(cd * ((double)pa.sb[0].hi + (double)pa.sb[0].lo));
-                acc[2] += warp_sum_d(cd * ((double)pa.sb[1].hi + (double)pa.sb[1].lo));
-                acc[3] += warp_sum_d(cd * ((double)pa.sb[2].hi + (double)pa.sb[2].lo));
-                acc[4] += warp_sum_d(cd * ((double)pa.ss.hi + (double)pa.ss.lo));
-                acc[5] += warp_sum_d(cd * ((double)pa.sg.hi + (double)pa.sg.lo));
+                const PairAcc &a = pa[0];
+                acc[0] += warp_sum_d(cd * ((double)a.s0.hi + (double)a.s0.lo));
+                acc[1] += warp_sum_d(cd * ((double)a.sb[0].hi + (double)a.sb[0].lo));
+                acc[2] += warp_sum_d(cd * ((double)a.sb[1].hi + (double)a.sb[1].lo));
+                acc[3] += warp_sum_d(cd * ((double)a.sb[2].hi + (double)a.sb[2].lo));
+                acc[4] += warp_sum_d(cd * ((double)a.ss.hi + (double)a.ss.lo));
+                acc[5] += warp_sum_d(cd * ((double)a.sg.hi + (double)a.sg.lo));
             }
         }
     }

@@ -158,6 +158,15 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
     P.inv_h = (float)(p->br.n_nodes / (2.0 * p->br.T));
     for (int i = 0; i < 3; ++i) P.AZ[i] = (float)(A[3 * i] * nh[0] + A[3 * i + 1] * nh[1] + A[3 * i + 2] * nh[2]);
     P.delta_L = p->geom.delta_L;
+    // Two pixels per lane (8 x 8 warp patches) when the patch spans at most half
+    // a lattice period along every cell axis: pitch in S (largest at the beam
+    // centre) x 8 sqrt 2 x max |a_i| <= 0.5; otherwise one (8 x 4).
+    {
+        const double pitch = p->geom.pixel / (p->geom.wavelength * p->geom.distance);
+        double amax = 0.0;
+        for (int q = 0; q < 3; ++q) amax = fmax(amax, rp.alen[q]);
+        P.ppl = pitch * 8.0 * sqrt(2.0) * amax <= 0.5 ? 2 : 1;
+    }
     P.pixgeo = pp.pixgeo;
     P.reach = rp.reach;
     P.recs = rp.recs;

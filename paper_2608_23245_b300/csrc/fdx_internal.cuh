@@ -123,6 +123,7 @@ enum RecField {
 
 struct PatternParams {
     int nx, ny, n_refl, n_nodes;
+    int ppl;              // pixels per lane of the forward kernel (1 or 2)
     float T, inv_h;       // grid half-extent, 1 / node spacing
     float AZ[3];          // a_i . n (cell constants)
     double delta_L;

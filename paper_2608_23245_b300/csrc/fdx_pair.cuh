@@ -1,6 +1,7 @@
 // One (pixel patch, reflection) pair of the shell quadrature, shared by the
 // forward pattern kernel (pixel-major) and the adjoint kernel
-// (reflection-major).  A warp owns an 8 x 4 pixel patch, one pixel per lane.
+// (reflection-major).  A warp owns an 8 x (4 PPL) pixel patch, PPL pixels per
+// lane.
 //
 // For the pair the warp
 //   1. bounds the node rows/columns that can be in any lane's support by the
@@ -91,25 +92,43 @@ __device__ __forceinline__ void sincospi_f(float x, float &s, float &c) {
     c = (qi & 2) ? -c1 : c1;
 }
 
-// The lane's pixel and the warp's reference pixel (lane 0), float-float.
+// A warp's pixels: PPL pixels per lane at (px0 + lane % 8, py0 + lane / 8 + 4 p),
+// p < PPL, so the warp covers an 8 x 4 PPL patch.  The reference pixel is the
+// patch's central pixel (column 4, row 2 PPL) when it lies on the detector,
+// else the first pixel: offsets from it (tau) stay small, which is what keeps
+// t = tau - sigma accurate in FP32.  (R, Z) as float-float.
+template <int PPL>
 struct PatchPix {
-    float Rh, Rl, Zh, Zl;      // this lane's (R, Z)
-    float Rrh, Rrl, Zrh, Zrl;  // reference (lane 0)
-    float dRl, dZl;            // (R, Z) - reference, small
-    bool valid;
+    float Rh[PPL], Rl[PPL], Zh[PPL], Zl[PPL];  // this lane's pixels
+    float dRl[PPL], dZl[PPL];                  // (R, Z) - reference, small
+    bool valid[PPL];
+    float Rrh, Rrl, Zrh, Zrl;                  // reference
 };
 
-__device__ __forceinline__ PatchPix load_patch(const float4 *pixgeo, int nx, int ny, int px0, int py0, int lane) {
-    PatchPix g;
-    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
-    g.valid = (px < nx) && (py < ny);
-    const size_t pidx = g.valid ? (size_t)py * nx + px : (size_t)py0 * nx + px0;
-    const float4 v = pixgeo[pidx];
-    g.Rh = v.x, g.Rl = v.y, g.Zh = v.z, g.Zl = v.w;
-    g.Rrh = __shfl_sync(FDX_FULL_MASK, g.Rh, 0), g.Rrl = __shfl_sync(FDX_FULL_MASK, g.Rl, 0);
-    g.Zrh = __shfl_sync(FDX_FULL_MASK, g.Zh, 0), g.Zrl = __shfl_sync(FDX_FULL_MASK, g.Zl, 0);
-    g.dRl = (g.Rh - g.Rrh) + (g.Rl - g.Rrl);
-    g.dZl = (g.Zh - g.Zrh) + (g.Zl - g.Zrl);
+template <int PPL>
+__device__ __forceinline__ PatchPix<PPL> load_patch(const float4 *pixgeo, int nx, int ny, int px0, int py0, int lane) {
+    PatchPix<PPL> g;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
+        g.valid[p] = (px < nx) && (py < ny);
+        const size_t pidx = g.valid[p] ? (size_t)py * nx + px : (size_t)py0 * nx + px0;
+        const float4 v = pixgeo[pidx];
+        g.Rh[p] = v.x, g.Rl[p] = v.y, g.Zh[p] = v.z, g.Zl[p] = v.w;
+    }
+    // central pixel: row 2 PPL = lane-row (2 PPL) % 4 of pixel set (2 PPL) / 4
+    constexpr int cp = (2 * PPL) / 4, clane = 4 + 8 * ((2 * PPL) % 4);
+    const bool cvalid = __shfl_sync(FDX_FULL_MASK, g.valid[cp], clane);
+    const int rl = cvalid ? clane : 0;
+    const float rRh = cvalid ? g.Rh[cp] : g.Rh[0], rRl = cvalid ? g.Rl[cp] : g.Rl[0];
+    const float rZh = cvalid ? g.Zh[cp] : g.Zh[0], rZl = cvalid ? g.Zl[cp] : g.Zl[0];
+    g.Rrh = __shfl_sync(FDX_FULL_MASK, rRh, rl), g.Rrl = __shfl_sync(FDX_FULL_MASK, rRl, rl);
+    g.Zrh = __shfl_sync(FDX_FULL_MASK, rZh, rl), g.Zrl = __shfl_sync(FDX_FULL_MASK, rZl, rl);
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        g.dRl[p] = (g.Rh[p] - g.Rrh) + (g.Rl[p] - g.Rrl);
+        g.dZl[p] = (g.Zh[p] - g.Zrh) + (g.Zl[p] - g.Zrl);
+    }
     return g;
 }
 
@@ -120,68 +139,84 @@ struct PairAcc {
     int32_t cnt;     // count mode: in-support terms
 };
 
-// Evaluate the pair; `rec` is the reflection record in shared memory; `buf`
-// (sigma_a, sigma_b, sigma_c, w), `buf2` (adjoint: dw/dsigma, dw/dgamma) and,
-// for the Hosemann lineshape, `bsc`/`bsc2` (cos, sin of pi sigma_i) are the
-// warp's node buffers of NB entries.  Returns false when no node can be in
-// any lane's support (nothing accumulated).
+__device__ __forceinline__ void clear(PairAcc &a) {
+    a.s0 = a.sb[0] = a.sb[1] = a.sb[2] = a.ss = a.sg = ff{0.0f, 0.0f};
+    a.cnt = 0;
+}
+
+// Evaluate the pair for all PPL pixels of every lane; `rec` is the reflection
+// record in shared memory; `buf` (sigma_a, sigma_b, sigma_c, w), `buf2`
+// (adjoint: dw/dsigma, dw/dgamma) and, for the Hosemann lineshape,
+// `bsc`/`bsc2` (cos, sin of pi sigma_i) are the warp's node buffers of NB
+// entries.  Returns false when no node can be in any pixel's support.
 //
 // Hosemann denominators by angle addition: with t = tau - sigma,
 //   sin(pi t) = sin(pi tau) cos(pi sigma) - cos(pi tau) sin(pi sigma),
 //   den_i = beta_i^2 + (1 - beta_i^2) sin^2(pi t_i),
-// sin/cos(pi tau) once per lane and pair, sin/cos(pi sigma) once per staged
-// node, so the per-evaluation cost is 4 operations per axis.
-template <int LS, int MODE, int NB = NODE_BUF>
-__device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix &g, const float *rec, float4 *buf,
-                                          float2 *buf2, float4 *bsc, float2 *bsc2, int lane, PairAcc &acc) {
+// sin/cos(pi tau) once per pixel and pair, sin/cos(pi sigma) (scaled by
+// sqrt(1 - beta_i^2)) once per staged node: one FMA per denominator on top of
+// the two products.
+template <int LS, int MODE, int NB, int PPL>
+__device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix<PPL> &g, const float *rec,
+                                          float4 *buf, float2 *buf2, float4 *bsc, float2 *bsc2, int lane,
+                                          PairAcc (&acc)[PPL]) {
     const int n = P.n_nodes;
-    // (p - D)/r0 in the local frame, FP32 (only bounds the node range)
-    const float dZ = (g.Zh - rec[REC_ZD]) + (g.Zl - rec[REC_ZD + 1]);
-    const float dR = (g.Rh - rec[REC_RD]) + (g.Rl - rec[REC_RD + 1]);
-    const float P0 = fmaf(dZ, rec[REC_NFR], dR * rec[REC_EFR]);
-    const float P1 = fmaf(dZ, rec[REC_NFR + 1], dR * rec[REC_EFR + 1]);
-    const float P2 = fmaf(dZ, rec[REC_NFR + 2], dR * rec[REC_EFR + 2]);
-    float d1lo = 3.0e38f, d1hi = -3.0e38f, d2lo = 3.0e38f, d2hi = -3.0e38f;
-    bool degenerate = false;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const float sg = s ? -1.0f : 1.0f;
-            const float X0 = 1.0f + P0 + sg * rec[REC_CR + 3 * v];
-            const float X1 = P1 + sg * rec[REC_CR + 3 * v + 1];
-            const float X2 = P2 + sg * rec[REC_CR + 3 * v + 2];
-            degenerate |= !(X0 > 0.05f);
-            const float inv = 1.0f / X0;
-            const float d1 = X1 * inv, d2 = X2 * inv;
-            d1lo = fminf(d1lo, d1), d1hi = fmaxf(d1hi, d1);
-            d2lo = fminf(d2lo, d2), d2hi = fmaxf(d2hi, d2);
-        }
-    }
+    // node rows/columns that can be in each pixel's support: gnomonic
+    // projection of the support box's corners around (p - D)/r0 (FP32, bounds only)
     int j0 = n, j1 = -1, m0 = n, m1 = -1;
-    if (g.valid) {
-        if (degenerate) {
-            j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
-        } else {
-            const float T = P.T, ih = P.inv_h;
-            j0 = max(0, (int)ceilf(fmaf(d1lo + T, ih, -0.5f)) - 1);
-            j1 = min(n - 1, (int)floorf(fmaf(d1hi + T, ih, -0.5f)) + 1);
-            m0 = max(0, (int)ceilf(fmaf(d2lo + T, ih, -0.5f)) - 1);
-            m1 = min(n - 1, (int)floorf(fmaf(d2hi + T, ih, -0.5f)) + 1);
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        const float dZ = (g.Zh[p] - rec[REC_ZD]) + (g.Zl[p] - rec[REC_ZD + 1]);
+        const float dR = (g.Rh[p] - rec[REC_RD]) + (g.Rl[p] - rec[REC_RD + 1]);
+        const float P0 = fmaf(dZ, rec[REC_NFR], dR * rec[REC_EFR]);
+        const float P1 = fmaf(dZ, rec[REC_NFR + 1], dR * rec[REC_EFR + 1]);
+        const float P2 = fmaf(dZ, rec[REC_NFR + 2], dR * rec[REC_EFR + 2]);
+        float d1lo = 3.0e38f, d1hi = -3.0e38f, d2lo = 3.0e38f, d2hi = -3.0e38f;
+        bool degenerate = false;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const float sg = s ? -1.0f : 1.0f;
+                const float X0 = 1.0f + P0 + sg * rec[REC_CR + 3 * v];
+                const float X1 = P1 + sg * rec[REC_CR + 3 * v + 1];
+                const float X2 = P2 + sg * rec[REC_CR + 3 * v + 2];
+                degenerate |= !(X0 > 0.05f);
+                const float inv = 1.0f / X0;
+                const float d1 = X1 * inv, d2 = X2 * inv;
+                d1lo = fminf(d1lo, d1), d1hi = fmaxf(d1hi, d1);
+                d2lo = fminf(d2lo, d2), d2hi = fmaxf(d2hi, d2);
+            }
+        }
+        if (g.valid[p]) {
+            if (degenerate) {
+                j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
+            } else {
+                const float T = P.T, ih = P.inv_h;
+                j0 = min(j0, max(0, (int)ceilf(fmaf(d1lo + T, ih, -0.5f)) - 1));
+                j1 = max(j1, min(n - 1, (int)floorf(fmaf(d1hi + T, ih, -0.5f)) + 1));
+                m0 = min(m0, max(0, (int)ceilf(fmaf(d2lo + T, ih, -0.5f)) - 1));
+                m1 = max(m1, min(n - 1, (int)floorf(fmaf(d2hi + T, ih, -0.5f)) + 1));
+            }
         }
     }
     const int J0 = __reduce_min_sync(FDX_FULL_MASK, j0), J1 = __reduce_max_sync(FDX_FULL_MASK, j1);
     const int M0 = __reduce_min_sync(FDX_FULL_MASK, m0), M1 = __reduce_max_sync(FDX_FULL_MASK, m1);
     if (J0 > J1 || M0 > M1) return false;
 
-    // tau_i = a_i . (p - p_ref), small
-    float tau[3];
+    // tau_i = a_i . (p - p_ref), small; invalid pixels get a value far outside any support
+    float tau[PPL][3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) tau[i] = g.valid ? fmaf(g.dZl, P.AZ[i], g.dRl * rec[REC_AR + i]) : 1.0e4f;
-    float st[3], ct[3];
+    for (int p = 0; p < PPL; ++p)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            tau[p][i] = g.valid[p] ? fmaf(g.dZl[p], P.AZ[i], g.dRl[p] * rec[REC_AR + i]) : 1.0e4f;
+    float st[PPL][3], ct[PPL][3];
     if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sincospi_f(tau[i], st[i], ct[i]);
+        for (int p = 0; p < PPL; ++p)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) sincospi_f(tau[p][i], st[p][i], ct[p][i]);
     }
     float la[3], tm[3], slb[3];
 #pragma unroll
@@ -190,7 +225,7 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     const float E1[3] = {rec[REC_E1], rec[REC_E1 + 1], rec[REC_E1 + 2]};
     const float E2[3] = {rec[REC_E2], rec[REC_E2 + 1], rec[REC_E2 + 2]};
 
-    // (p_ref - D)/r0 in the local frame, float-float (every lane computes it for lane 0's pixel)
+    // (p_ref - D)/r0 in the local frame, float-float (every lane computes it for the reference pixel)
     const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
     const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
     ff dP[3];
@@ -200,12 +235,16 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                        ff_mul(dRr, ff{rec[REC_EFR + q], rec[REC_EFR + 3 + q]}));
     }
 
-    // warp-wide tau box: a node can be in some lane's support only if sigma_i
+    // warp-wide tau box: a node can be in some pixel's support only if sigma_i
     // lies within [min tau_i - tm_i, max tau_i + tm_i] for every i
     float tc[3], th[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        const float lo = warp_min(g.valid ? tau[i] : 3.0e38f), hi = warp_max(g.valid ? tau[i] : -3.0e38f);
+        float lo = 3.0e38f, hi = -3.0e38f;
+#pragma unroll
+        for (int p = 0; p < PPL; ++p)
+            if (g.valid[p]) lo = fminf(lo, tau[p][i]), hi = fmaxf(hi, tau[p][i]);
+        lo = warp_min(lo), hi = warp_max(hi);
         tc[i] = 0.5f * (lo + hi);
         th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
     }
@@ -224,72 +263,83 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bj_lane = lane / BC, bm_lane = lane % BC;  // this lane's node inside a block
     int nlive = 0;
-    // Walk the compacted nodes (all lanes, warp-uniform bounds) and empty the buffer.
+
+    // Walk the compacted nodes (warp-uniform bounds) and empty the buffer.
     auto flush = [&]() {
-            __syncwarp();
-            if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
-                for (int q = lane; q < nlive; q += 32) {
-                    const float4 nq = buf[q];
-                    float sa, ca, sb, cb, sc, cc;
-                    sincospi_f(nq.x, sa, ca);
-                    sincospi_f(nq.y, sb, cb);
-                    sincospi_f(nq.z, sc, cc);
-                    // scaled by sqrt(1 - beta_i^2): den_i = beta_i^2 + (scaled sin(pi t_i))^2
-                    bsc[q] = make_float4(slb[0] * ca, slb[0] * sa, slb[1] * cb, slb[1] * sb);
-                    bsc2[q] = make_float2(slb[2] * cc, slb[2] * sc);
-                }
-                __syncwarp();
+        __syncwarp();
+        if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
+            for (int q = lane; q < nlive; q += 32) {
+                const float4 nq = buf[q];
+                float sa, ca, sb, cb, sc, cc;
+                sincospi_f(nq.x, sa, ca);
+                sincospi_f(nq.y, sb, cb);
+                sincospi_f(nq.z, sc, cc);
+                // scaled by sqrt(1 - beta_i^2): den_i = beta_i^2 + (scaled sin(pi t_i))^2
+                bsc[q] = make_float4(slb[0] * ca, slb[0] * sa, slb[1] * cb, slb[1] * sb);
+                bsc2[q] = make_float2(slb[2] * cc, slb[2] * sc);
             }
-            for (int q0 = 0; q0 < nlive; q0 += 32) {
-                const int qe = min(q0 + 32, nlive);
-                float r0 = 0.0f, rb0 = 0.0f, rb1 = 0.0f, rb2 = 0.0f, rss = 0.0f, rsg = 0.0f;
-#pragma unroll 4
-                for (int q = q0; q < qe; ++q) {
-                    const float4 nq = buf[q];
-                    const float ta = tau[0] - nq.x, tb = tau[1] - nq.y, tcc = tau[2] - nq.z;
+            __syncwarp();
+        }
+        for (int q0 = 0; q0 < nlive; q0 += 32) {
+            const int qe = min(q0 + 32, nlive);
+            float r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = 0.0f;
+#pragma unroll 2
+            for (int q = q0; q < qe; ++q) {
+                const float4 nq = buf[q];
+                float4 sc4;
+                float2 sc2, dw;
+                if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) sc4 = bsc[q], sc2 = bsc2[q];
+                if (MODE == MODE_ADJ) dw = buf2[q];
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) {
+                    const float ta = tau[p][0] - nq.x, tb = tau[p][1] - nq.y, tcc = tau[p][2] - nq.z;
                     const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tcc) <= tm[2]);
                     if (MODE == MODE_CNT) {
-                        acc.cnt += in ? 1 : 0;
+                        acc[p].cnt += in ? 1 : 0;
                     } else if (LS == FDX_LINESHAPE_HOSEMANN) {
-                        const float4 sc4 = bsc[q];
-                        const float2 sc2 = bsc2[q];
-                        const float sa = fmaf(st[0], sc4.x, -ct[0] * sc4.y);
-                        const float sb = fmaf(st[1], sc4.z, -ct[1] * sc4.w);
-                        const float sc = fmaf(st[2], sc2.x, -ct[2] * sc2.y);
+                        const float sa = fmaf(st[p][0], sc4.x, -ct[p][0] * sc4.y);
+                        const float sb = fmaf(st[p][1], sc4.z, -ct[p][1] * sc4.w);
+                        const float sc = fmaf(st[p][2], sc2.x, -ct[p][2] * sc2.y);
                         const float da = fmaf(sa, sa, la[0]);
                         const float db = fmaf(sb, sb, la[1]);
                         const float dc = fmaf(sc, sc, la[2]);
                         const float dab = da * db;
                         const float rp = rcp_approx(dab * dc);
                         const float kv = nq.w * rp;
-                        r0 += in ? kv : 0.0f;
+                        r0[p] += in ? kv : 0.0f;
                         if (MODE == MODE_ADJ) {
-                            const float2 dw = buf2[q];
                             const float dbc = db * dc, dac = da * dc;
                             // 1/den_i = (product of the other two) * rp
-                            rb0 += in ? kv * fmaf(dbc, rp, -1.0f) : 0.0f;
-                            rb1 += in ? kv * fmaf(dac, rp, -1.0f) : 0.0f;
-                            rb2 += in ? kv * fmaf(dab, rp, -1.0f) : 0.0f;
-                            rss += in ? dw.x * rp : 0.0f;
-                            rsg += in ? dw.y * rp : 0.0f;
+                            rb0[p] += in ? kv * fmaf(dbc, rp, -1.0f) : 0.0f;
+                            rb1[p] += in ? kv * fmaf(dac, rp, -1.0f) : 0.0f;
+                            rb2[p] += in ? kv * fmaf(dab, rp, -1.0f) : 0.0f;
+                            rss[p] += in ? dw.x * rp : 0.0f;
+                            rsg[p] += in ? dw.y * rp : 0.0f;
                         }
                     } else {
                         const float kv = nq.w * sinc_term(ta, tb, tcc, la);
-                        r0 += in ? kv : 0.0f;
+                        r0[p] += in ? kv : 0.0f;
                     }
                 }
-                if (MODE != MODE_CNT) acc.s0 = ff_add_f(acc.s0, r0);
+            }
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) {
+                if (MODE != MODE_CNT) acc[p].s0 = ff_add_f(acc[p].s0, r0[p]);
                 if (MODE == MODE_ADJ) {
-                    acc.sb[0] = ff_add_f(acc.sb[0], rb0);
-                    acc.sb[1] = ff_add_f(acc.sb[1], rb1);
-                    acc.sb[2] = ff_add_f(acc.sb[2], rb2);
-                    acc.ss = ff_add_f(acc.ss, rss);
-                    acc.sg = ff_add_f(acc.sg, rsg);
+                    acc[p].sb[0] = ff_add_f(acc[p].sb[0], rb0[p]);
+                    acc[p].sb[1] = ff_add_f(acc[p].sb[1], rb1[p]);
+                    acc[p].sb[2] = ff_add_f(acc[p].sb[2], rb2[p]);
+                    acc[p].ss = ff_add_f(acc[p].ss, rss[p]);
+                    acc[p].sg = ff_add_f(acc[p].sg, rsg[p]);
                 }
             }
+        }
         nlive = 0;
         __syncwarp();
     };
+
     for (int blk0 = 0; blk0 < nblk; blk0 += 32) {
         bool blive = false;
         {

@@ -1,9 +1,9 @@
 // Gather-form pattern kernel (Eq. direct_sum at every pixel's query point,
 // times the Lorentz factor of Eq. lorentz).
 //
-// Work decomposition.  A CTA of 4 warps covers a 16 x 8 pixel block; each warp
-// owns an 8 x 4 pixel patch, one pixel per lane, and accumulates its pixels in
-// registers (no atomics).  The warp scans the reflection list 32 at a time
+// Work decomposition.  A CTA of 4 warps covers a 16 x 16 pixel block; each warp
+// owns an 8 x 8 pixel patch, two pixels per lane, and accumulates its pixels
+// in registers (no atomics).  The warp scans the reflection list 32 at a time
 // with a conservative radial/polar test against its patch's (|S|, psi) bounds
 // and evaluates the surviving (patch, reflection) pairs in list order
 // (deterministic) with eval_pair (fdx_pair.cuh).  Pair sums are weighted by
@@ -14,8 +14,11 @@
 namespace fdx {
 
 static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp; 4 warps x 288 x 40 B keeps static shared memory < 48 KB
+// Pixels per lane (PPL): 2 (a warp owns 8 x 8 pixels, a CTA 16 x 16) when
+// the patch spans a small fraction of a lattice period, else 1 (8 x 4, 16 x 8);
+// chosen on the host from the pixel pitch and the cell.
 
-template <int LS, int MODE>
+template <int LS, int MODE, int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternParams P) {
     __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];
     __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1];
@@ -23,19 +26,25 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * 8 + (warp >> 1) * 4;
-    const bool lane_valid = (px0 + (lane & 7) < P.nx) && (py0 + (lane >> 3) < P.ny);
-    if (__ballot_sync(FDX_FULL_MASK, lane_valid) == 0) return;  // lane 0 is valid from here on
-    const PatchPix g = load_patch(P.pixgeo, P.nx, P.ny, px0, py0, lane);
+    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * (8 * PPL) + (warp >> 1) * (4 * PPL);
+    if (px0 >= P.nx || py0 >= P.ny) return;  // the whole patch is outside; lane 0's first pixel is valid otherwise
+    const PatchPix<PPL> g = load_patch<PPL>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
 
-    const float rlen = sqrtf(g.Rh * g.Rh + g.Zh * g.Zh), psi = atan2f(g.Rh, g.Zh);
-    const float rmin = warp_min(g.valid ? rlen : 3.0e38f), rmax = warp_max(g.valid ? rlen : -3.0e38f);
-    const float pmin = warp_min(g.valid ? psi : 3.0e38f), pmax = warp_max(g.valid ? psi : -3.0e38f);
+    float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        if (!g.valid[p]) continue;
+        const float rlen = sqrtf(g.Rh[p] * g.Rh[p] + g.Zh[p] * g.Zh[p]), psi = atan2f(g.Rh[p], g.Zh[p]);
+        rmin = fminf(rmin, rlen), rmax = fmaxf(rmax, rlen), pmin = fminf(pmin, psi), pmax = fmaxf(pmax, psi);
+    }
+    rmin = warp_min(rmin), rmax = warp_max(rmax), pmin = warp_min(pmin), pmax = warp_max(pmax);
 
     float *rec = s_rec[warp];
     float4 *buf = s_nodes[warp];
-    ff acc = {0.0f, 0.0f};
-    int32_t cnt = 0;
+    ff acc[PPL];
+    int32_t cnt[PPL];
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) acc[p] = ff{0.0f, 0.0f}, cnt[p] = 0;
 
     for (int base = 0; base < P.n_refl; base += 32) {
         bool cand = false;
@@ -49,42 +58,57 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
             const int b = __ffs(mask) - 1;
             mask &= mask - 1;
             load_record(P.recs, base + b, rec, lane);
-            PairAcc pa;
-            pa.s0 = {0.0f, 0.0f};
-            pa.cnt = 0;
-            if (!eval_pair<LS, MODE, FWD_NODE_BUF>(P, g, rec, buf, nullptr, s_sc[warp], s_sc2[warp], lane, pa)) continue;
-            if (MODE == MODE_CNT)
-                cnt += pa.cnt;
-            else
-                acc = ff_add(acc, ff_mul_f(pa.s0, rec[REC_FR]));
+            PairAcc pa[PPL];
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) clear(pa[p]);
+            if (!eval_pair<LS, MODE, FWD_NODE_BUF, PPL>(P, g, rec, buf, nullptr, s_sc[warp], s_sc2[warp], lane, pa))
+                continue;
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) {
+                if (MODE == MODE_CNT)
+                    cnt[p] += pa[p].cnt;
+                else
+                    acc[p] = ff_add(acc[p], ff_mul_f(pa[p].s0, rec[REC_FR]));
+            }
         }
     }
-    if (!g.valid) return;
-    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
-    const size_t out = (size_t)py * P.nx + px;
-    if (MODE == MODE_CNT) {
-        P.counts[out] = cnt;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        if (!g.valid[p]) continue;
+        const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
+        const size_t out = (size_t)py * P.nx + px;
+        if (MODE == MODE_CNT) {
+            P.counts[out] = cnt[p];
+        } else {
+            const double R = (double)g.Rh[p] + (double)g.Rl[p];
+            const double L = P.delta_L / (R + P.delta_L);
+            P.image[out] = (float)(L * ((double)acc[p].hi + (double)acc[p].lo));
+        }
+    }
+}
+
+template <int PPL>
+static void launch_ppl(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+    dim3 grid((p.nx + 15) / 16, (p.ny + 8 * PPL - 1) / (8 * PPL));
+    dim3 block(PAIR_WARPS * 32);
+    if (lineshape == FDX_LINESHAPE_HOSEMANN) {
+        if (count_mode)
+            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
+        else
+            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
     } else {
-        const double R = (double)g.Rh + (double)g.Rl;
-        const double L = P.delta_L / (R + P.delta_L);
-        P.image[out] = (float)(L * ((double)acc.hi + (double)acc.lo));
+        if (count_mode)
+            pattern_kernel<FDX_LINESHAPE_SINC, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
+        else
+            pattern_kernel<FDX_LINESHAPE_SINC, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
     }
 }
 
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
-    dim3 grid((p.nx + 15) / 16, (p.ny + 7) / 8);
-    dim3 block(PAIR_WARPS * 32);
-    if (lineshape == FDX_LINESHAPE_HOSEMANN) {
-        if (count_mode)
-            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_CNT><<<grid, block, 0, s>>>(p);
-        else
-            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_FWD><<<grid, block, 0, s>>>(p);
-    } else {
-        if (count_mode)
-            pattern_kernel<FDX_LINESHAPE_SINC, MODE_CNT><<<grid, block, 0, s>>>(p);
-        else
-            pattern_kernel<FDX_LINESHAPE_SINC, MODE_FWD><<<grid, block, 0, s>>>(p);
-    }
+    if (p.ppl == 2)
+        launch_ppl<2>(p, lineshape, count_mode, s);
+    else
+        launch_ppl<1>(p, lineshape, count_mode, s);
     return cudaGetLastError();
 }
 
