@@ -133,6 +133,73 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
+def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
+    """Refinement step = structure factors + pattern + loss + hand-written
+    adjoint (all gradients), on the config-3 model against its perturbed
+    target.  Timed at full size for the FP32 path, and on a central roi x roi
+    detector for both the FP32 path and the plain FP64 GPU form of the same
+    method (models/s = 1 / step time)."""
+    import torch
+    from dataclasses import replace
+    from paper_2608_23245_b300 import fdx, workloads as W
+    model, target = W.config3()
+
+    def fp32_setup(m, t):
+        sim = fdx.Simulation(m)
+        tsim = fdx.Simulation(t)
+        It = tsim.forward().clone()
+        na, n = m.atoms.n, sim.hkl.shape[0]
+        bufs = dict(gI=torch.empty_like(sim.image), loss=torch.empty((), dtype=torch.float64, device="cuda"),
+                    dfrac=torch.empty((na, 3), dtype=torch.float64, device="cuda"),
+                    dB=torch.empty(na, dtype=torch.float64, device="cuda"),
+                    dglob=torch.empty(8, dtype=torch.float64, device="cuda"),
+                    bws=torch.empty(max(fdx.fdx_backward_workspace_size(sim.prob, na, sim.atoms.ff.shape[0]), 256),
+                                    dtype=torch.uint8, device="cuda"),
+                    lws=torch.empty(fdx.fdx_loss_workspace_size(sim.image.numel()), dtype=torch.uint8, device="cuda"))
+
+        def step():
+            sim.forward()
+            fdx.fdx_loss(sim.image, It, None, bufs["loss"], bufs["gI"], bufs["lws"])
+            fdx.fdx_pattern_backward(sim.prob, sim.atoms, sim.F, bufs["gI"], bufs["dfrac"], bufs["dB"], bufs["dglob"],
+                                     None, bufs["bws"])
+        return step
+
+    def timed(step, k, w):
+        for _ in range(w):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            step()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / k
+
+    full = timed(fp32_setup(model, target), steps, warmup)
+    mr = replace(model, geom=replace(model.geom, n_x=roi, n_y=roi))
+    tr = replace(target, geom=replace(target.geom, n_x=roi, n_y=roi))
+    roi32 = timed(fp32_setup(mr, tr), steps, warmup)
+    sim = fdx.Simulation(mr)
+    It = fdx.Simulation(tr).forward().to(torch.float64)
+    img = torch.empty((roi, roi), dtype=torch.float64, device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    dfrac = torch.empty((mr.atoms.n, 3), dtype=torch.float64, device="cuda")
+    dB = torch.empty(mr.atoms.n, dtype=torch.float64, device="cuda")
+    dglob = torch.empty(8, dtype=torch.float64, device="cuda")
+    ws = torch.empty(fdx.fdx_plain64_workspace_size(sim.prob, mr.atoms.n, sim.atoms.ff.shape[0]), dtype=torch.uint8,
+                     device="cuda")
+
+    def plain_step():
+        fdx.fdx_plain64_refine(sim.prob, sim.atoms, img, It, None, loss, dfrac, dB, dglob, ws)
+    roi64 = timed(plain_step, plain_steps, 1)
+    return {"workload": "helix model vs seeded perturbed target (config-3 recipe): SF + pattern + loss + adjoint",
+            "fp32_models_per_s": 1.0 / full, "fp32_ms_per_step": 1e3 * full,
+            "roi": "central %dx%d pixels (same pixel size)" % (roi, roi),
+            "fp32_roi_models_per_s": 1.0 / roi32, "plain_fp64_roi_models_per_s": 1.0 / roi64,
+            "fp32_over_plain_fp64_roi": roi64 / roi32}
+
+
 def cpu_baseline(problem, budget_s=12.0, n_pix=None, seed=5):
     """Time the FP64 oracle (as it stands) on a bounded pixel sample."""
     import oracle
@@ -196,6 +263,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdx", choices=["fdx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-refine", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -297,6 +365,8 @@ def main():
         "clocks": clocks,
         "wall_s": wall,
     }
+    if not args.no_refine:
+        line["refine"] = refine_measurements()
     if not args.no_cpu_baseline:
         cb, _ = cpu_baseline(p)
         line["cpu_baseline"] = cb

@@ -234,6 +234,23 @@ size_t fdx_loss_workspace_size(int64_t n_px);
 int fdx_loss(int64_t n_px, const float *I, const float *I_target, const float *mask, double *loss_out,
              float *dL_dI, void *workspace, size_t ws_bytes, void *stream);
 
+/* Bytes of workspace fdx_plain64_refine needs. */
+size_t fdx_plain64_workspace_size(const fdx_problem *prob, int32_t n_atoms, int32_t n_elem);
+
+/*
+ * fdx_plain64_refine -- the same method in plain FP64 on the GPU (the
+ * comparison form of the refinement-throughput metric): FP64 structure
+ * factors, FP64 pattern (every term of each pixel's node range evaluated
+ * directly with sinpi), and, when I_target is not NULL, the FP64 loss of
+ * fdx_loss (mask optional) into *loss and the FP64 adjoint into `grads`
+ * (dfrac, dB, dglobal; dM is not written).  image and I_target are
+ * [n_y][n_x] double (device).  prob->M is ignored.  Hosemann lineshape only.
+ * Asynchronous.
+ */
+int fdx_plain64_refine(const fdx_problem *prob, const fdx_atoms *atoms, const double *I_target, const float *mask,
+                       double *image, double *loss, const fdx_grads *grads, void *workspace, size_t ws_bytes,
+                       void *stream);
+
 /* Human-readable text for a return code (static storage). */
 const char *fdx_error_string(int code);
 

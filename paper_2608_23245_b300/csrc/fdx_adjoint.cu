@@ -360,6 +360,18 @@ cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s) {
+    const int n_patch = A.npx * A.npy;
+    patch_bounds_kernel<<<(n_patch * 32 + 127) / 128, 128, 0, s>>>(A);
+    band_bounds_kernel<<<A.n_bands, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_globals_only(AdjParams &A, cudaStream_t s) {
+    adjoint_globals_kernel<<<1, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sf_adjoint(SFAdjParams &p, cudaStream_t s) {
     dim3 grid((p.n_atoms + SFA_THREADS - 1) / SFA_THREADS, p.n_split);
     const size_t shm = sizeof(float) * SFA_TILE * p.n_elem;

@@ -44,7 +44,32 @@ struct LossParams {
     double *loss;
 };
 
+struct Plain64Params {
+    int nx, ny, n_refl, n, n_atoms, n_elem, npx, npy, n_bands, rows_per_band, intensity_model;
+    double T, h, delta_L;
+    double A[9], As[9], nh[3], bh[3], alen[3], L[3], g[3], Bax[3];
+    const float4 *pixgeo, *reach, *patch_bounds, *band_bounds;
+    double *recs64;          // [n_refl][48]
+    const double *nodes64;   // [n*n][4]: w, -, dw/dsigma, dw/dgamma
+    double *image64;         // [ny][nx]
+    const double *It64;      // [ny][nx] target
+    const float *mask;       // [ny][nx] or null
+    double *gI, *loss, *loss_partial;
+    const int32_t *hkl;
+    double *F64, *M64, *Gw64;
+    double *item_out, *refl_out;
+    const double *frac;
+    const float *B, *occ, *ff;
+    const uint8_t *elem;
+    double *dfrac, *dB;
+};
+
 cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s);
+cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s);
+cudaError_t launch_globals_only(AdjParams &A, cudaStream_t s);
+cudaError_t launch_plain64_forward(Plain64Params &p, cudaStream_t s);
+cudaError_t launch_plain64_loss(Plain64Params &p, cudaStream_t s);
+cudaError_t launch_plain64_backward(Plain64Params &p, AdjParams &A, cudaStream_t s);
 cudaError_t launch_sf_adjoint(SFAdjParams &p, cudaStream_t s);
 cudaError_t launch_loss(LossParams &p, cudaStream_t s);
 cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s);

@@ -113,7 +113,8 @@ void cross3(const double *x, const double *y, double *z) {
 
 // Queue the set-up kernels (pixel geometry, node table, reflection records)
 // for one problem and fill the pattern kernel's parameters.
-int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes) {
+int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes,
+                  double *nodes64 = nullptr) {
     const Layout L = layout_for(p);
     double A[9], As[9];
     cell_basis(p->cell, A, As);
@@ -136,6 +137,7 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
     np.sigma = p->br.sigma, np.gamma = p->br.gamma, np.sigma_r = p->br.sigma_r;
     np.nodes = reinterpret_cast<float4 *>(ws + L.nodes);
     np.dnodes = with_dnodes ? reinterpret_cast<float2 *>(ws + L.dnodes) : nullptr;
+    np.nodes64 = nodes64;
     if (launch_nodes(np, weideman_coeffs(), st) != cudaSuccess) return FDX_ERR_CUDA;
 
     ReflSetupParams rp;
@@ -457,6 +459,110 @@ int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const 
         q.dfrac = grads->dfrac, q.dB = grads->dB;
         if (launch_sf_adjoint(q, st) != cudaSuccess) return FDX_ERR_CUDA;
     }
+    return FDX_OK;
+}
+
+// Plain FP64 path: the FP32 path's backward layout followed by FP64 buffers.
+struct Plain64Layout {
+    BackLayout B;
+    size_t recs64, nodes64, F64, M64, Gw64, gI, loss_partial, total;
+};
+
+Plain64Layout plain64_layout(const fdx_problem *p, int n_atoms, int n_elem) {
+    Plain64Layout L;
+    L.B = back_layout(p, n_atoms, n_elem);
+    const size_t nr = (size_t)(p->n_refl > 0 ? p->n_refl : 1);
+    const size_t npx = (size_t)p->geom.n_x * p->geom.n_y;
+    size_t off = L.B.total;
+    L.recs64 = off, off += align_up(sizeof(double) * 48 * nr);
+    L.nodes64 = off, off += align_up(sizeof(double) * 4 * (size_t)p->br.n_nodes * p->br.n_nodes);
+    L.F64 = off, off += align_up(sizeof(double) * 2 * nr);
+    L.M64 = off, off += align_up(sizeof(double) * nr);
+    L.Gw64 = off, off += align_up(sizeof(double) * nr);
+    L.gI = off, off += align_up(sizeof(double) * npx);
+    L.loss_partial = off, off += align_up(sizeof(double) * ((npx + 255) / 256));
+    L.total = off;
+    return L;
+}
+
+size_t fdx_plain64_workspace_size(const fdx_problem *prob, int32_t n_atoms, int32_t n_elem) {
+    if (!prob || n_atoms < 1 || n_elem < 1) return 0;
+    return plain64_layout(prob, n_atoms, n_elem).total;
+}
+
+int fdx_plain64_refine(const fdx_problem *prob, const fdx_atoms *atoms, const double *I_target, const float *mask,
+                       double *image, double *loss, const fdx_grads *grads, void *workspace, size_t ws_bytes,
+                       void *stream) {
+    if (!prob || !image) return FDX_ERR_ARG;
+    fdx_problem pr = *prob;
+    pr.M = nullptr;  // the FP64 path forms its own M
+    int rc = validate_cell(&pr.cell);
+    if (rc) return rc;
+    if ((rc = validate_broadening(&pr.br)) || (rc = validate_geometry(&pr.geom))) return rc;
+    if (pr.n_refl < 0 || (pr.n_refl > 0 && !pr.hkl)) return FDX_ERR_ARG;
+    if (pr.br.lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
+    if (!atoms || atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
+    if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
+    if (I_target && (!loss || !grads)) return FDX_ERR_ARG;
+    const Plain64Layout L = plain64_layout(&pr, atoms->n_atoms, atoms->n_elem);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    double *nodes64 = reinterpret_cast<double *>(ws + L.nodes64);
+    PatternParams P;
+    if ((rc = setup_pattern(&pr, ws, st, P, false, nodes64))) return rc;
+
+    Plain64Params q;
+    memset(&q, 0, sizeof q);
+    q.nx = pr.geom.n_x, q.ny = pr.geom.n_y, q.n_refl = pr.n_refl, q.n = pr.br.n_nodes;
+    q.n_atoms = atoms->n_atoms, q.n_elem = atoms->n_elem;
+    q.npx = L.B.npx, q.npy = L.B.npy, q.n_bands = L.B.n_bands, q.rows_per_band = L.B.rows_per_band;
+    q.intensity_model = pr.br.intensity_model;
+    q.T = pr.br.T, q.h = 2.0 * pr.br.T / pr.br.n_nodes, q.delta_L = pr.geom.delta_L;
+    double Am[9], As[9];
+    cell_basis(pr.cell, Am, As);
+    memcpy(q.A, Am, sizeof Am);
+    memcpy(q.As, As, sizeof As);
+    double bh[3];
+    unit3(pr.geom.fiber_axis, q.nh);
+    unit3(pr.geom.beam_axis, bh);
+    for (int i = 0; i < 3; ++i) {
+        q.bh[i] = bh[i];
+        q.alen[i] = sqrt(Am[3 * i] * Am[3 * i] + Am[3 * i + 1] * Am[3 * i + 1] + Am[3 * i + 2] * Am[3 * i + 2]);
+        q.L[i] = pr.br.L[i], q.g[i] = pr.br.g[i], q.Bax[i] = pr.br.B_axis[i];
+    }
+    q.pixgeo = P.pixgeo, q.reach = P.reach;
+    q.patch_bounds = reinterpret_cast<float4 *>(ws + L.B.patch_bounds);
+    q.band_bounds = reinterpret_cast<float4 *>(ws + L.B.band_bounds);
+    q.recs64 = reinterpret_cast<double *>(ws + L.recs64);
+    q.nodes64 = nodes64;
+    q.image64 = image;
+    q.It64 = I_target;
+    q.mask = mask;
+    q.gI = reinterpret_cast<double *>(ws + L.gI);
+    q.loss = loss;
+    q.loss_partial = reinterpret_cast<double *>(ws + L.loss_partial);
+    q.hkl = pr.hkl;
+    q.F64 = reinterpret_cast<double *>(ws + L.F64);
+    q.M64 = reinterpret_cast<double *>(ws + L.M64);
+    q.Gw64 = reinterpret_cast<double *>(ws + L.Gw64);
+    q.item_out = reinterpret_cast<double *>(ws + L.B.item_out);
+    q.refl_out = reinterpret_cast<double *>(ws + L.B.refl_out);
+    q.frac = atoms->frac, q.B = atoms->B, q.occ = atoms->occ, q.ff = atoms->ff, q.elem = atoms->elem;
+    q.dfrac = grads ? grads->dfrac : nullptr;
+    q.dB = grads ? grads->dB : nullptr;
+    if (launch_plain64_forward(q, st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (!I_target) return FDX_OK;
+    if (launch_plain64_loss(q, st) != cudaSuccess) return FDX_ERR_CUDA;
+    AdjParams A;
+    memset(&A, 0, sizeof A);
+    A.P = P;
+    A.patch_bounds = const_cast<float4 *>(q.patch_bounds);
+    A.band_bounds = const_cast<float4 *>(q.band_bounds);
+    A.npx = q.npx, A.npy = q.npy, A.n_bands = q.n_bands, A.rows_per_band = q.rows_per_band;
+    A.refl_out = q.refl_out;
+    A.dglobal = grads->dglobal;
+    if (launch_plain64_backward(q, A, st) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
 }
 

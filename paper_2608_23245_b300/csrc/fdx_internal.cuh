@@ -154,6 +154,7 @@ struct NodeParams {
     double T, h, sigma, gamma, sigma_r;
     float4 *nodes;
     float2 *dnodes;  // may be null
+    double *nodes64; // may be null: [n*n][4] = w, c, dw/dsigma, dw/dgamma in FP64
 };
 
 struct PixelParams {

@@ -178,6 +178,10 @@ __global__ void nodes_kernel(NodeParams p, WeidemanCoeffs wc) {
     p.nodes[2 * k] = a;
     p.nodes[2 * k + 1] = b;
     if (p.dnodes) p.dnodes[k] = make_float2((float)(pre * dgs), (float)(pre * dgg));
+    if (p.nodes64) {
+        p.nodes64[4 * k] = w, p.nodes64[4 * k + 1] = c;
+        p.nodes64[4 * k + 2] = pre * dgs, p.nodes64[4 * k + 3] = pre * dgg;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -370,3 +370,40 @@ def fdx_loss(I, I_target, mask=None, loss_out=None, dL_dI=None, workspace=None, 
     _check(L.fdx_loss(n, _ptr(I), _ptr(I_target), _ptr(mask), _ptr(loss_out), _ptr(dL_dI), _ptr(workspace),
                       int(workspace.numel()), _stream(stream)), "fdx_loss")
     return loss_out, dL_dI
+
+
+# ---------------------------------------------------------------------------
+# plain FP64 form of the method (comparison path)
+# ---------------------------------------------------------------------------
+
+def _bind_plain64(L):
+    if getattr(L, "_plain64_bound", False):
+        return L
+    L.fdx_plain64_workspace_size.restype = C.c_size_t
+    L.fdx_plain64_workspace_size.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32]
+    L.fdx_plain64_refine.argtypes = [C.POINTER(Problem), C.POINTER(Atoms), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p, C.POINTER(Grads), C.c_void_p, C.c_size_t, C.c_void_p]
+    L._plain64_bound = True
+    return L
+
+
+def fdx_plain64_workspace_size(problem, n_atoms: int, n_elem: int) -> int:
+    return int(_bind_plain64(lib()).fdx_plain64_workspace_size(C.byref(problem), int(n_atoms), int(n_elem)))
+
+
+def fdx_plain64_refine(problem, datoms, image, I_target=None, mask=None, loss=None, dfrac=None, dB=None,
+                       dglobal=None, workspace=None, stream=None):
+    """Plain FP64 forward (image, float64 [n_y, n_x]) and, with I_target,
+    the FP64 loss and adjoint."""
+    import torch
+    L = _bind_plain64(lib())
+    a = datoms.struct()
+    need = fdx_plain64_workspace_size(problem, a.n_atoms, a.n_elem)
+    if workspace is None:
+        workspace = torch.empty(max(need, 256), dtype=torch.uint8, device=image.device)
+    g = Grads(dfrac.data_ptr() if dfrac is not None else None, dB.data_ptr() if dB is not None else None,
+              dglobal.data_ptr() if dglobal is not None else None, None)
+    _check(L.fdx_plain64_refine(C.byref(problem), C.byref(a), _ptr(I_target), _ptr(mask), _ptr(image), _ptr(loss),
+                                C.byref(g), _ptr(workspace), int(workspace.numel()), _stream(stream)),
+           "fdx_plain64_refine")
+    return image, loss
