@@ -251,6 +251,29 @@ int fdx_plain64_refine(const fdx_problem *prob, const fdx_atoms *atoms, const do
                        double *image, double *loss, const fdx_grads *grads, void *workspace, size_t ws_bytes,
                        void *stream);
 
+/* Bytes of workspace fdx_batch_refine needs for these models. */
+size_t fdx_batch_workspace_size(int32_t n_models, const fdx_problem *const *probs, const fdx_atoms *const *atoms);
+
+/*
+ * fdx_batch_refine -- one refinement step for many models at once (batched
+ * refinement of candidate models): per model the structure factors (into
+ * F[m], M[m]; probs[m]->M is ignored), the pattern (images[m]), and, when
+ * targets is not NULL, the loss of fdx_loss (losses[m], masks optional) and
+ * the adjoint of fdx_pattern_backward (grads[m]).  The pattern of all models
+ * runs in one persistent launch and the adjoint of all models in another;
+ * both take (model, tile) or (model, reflection, band) items from an atomic
+ * counter in the workspace, and each item is computed by one CTA or warp from
+ * start to finish, so results do not depend on the order items are taken.
+ * Every operation is a kernel launch or an asynchronous memset on `stream`,
+ * so the step can be captured in a CUDA graph and replayed while the
+ * problems' host parameters stay the same (atom coordinates and B, being
+ * device arrays, may change between replays).  Hosemann lineshape only.
+ */
+int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fdx_atoms *const *atoms,
+                     float *const *F, float *const *M, float *const *images, const float *const *targets,
+                     const float *const *masks, double *losses, const fdx_grads *const *grads, void *workspace,
+                     size_t ws_bytes, void *stream);
+
 /* Human-readable text for a return code (static storage). */
 const char *fdx_error_string(int code);
 

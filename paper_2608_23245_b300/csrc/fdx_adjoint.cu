@@ -76,21 +76,13 @@ __global__ void band_bounds_kernel(AdjParams A) {
     if (threadIdx.x == 0) A.band_bounds[b] = red[0];
 }
 
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
-    __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];
-    __shared__ float2 s_dn[PAIR_WARPS][ADJ_NODE_BUF];
-    __shared__ float4 s_sc[PAIR_WARPS][ADJ_NODE_BUF];
-    __shared__ float2 s_sc2[PAIR_WARPS][ADJ_NODE_BUF];
-    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
-    const long long n_items = (long long)A.P.n_refl * A.n_bands;
-    if (item >= n_items) return;
+// One (reflection, band) item of the adjoint for one warp.
+__device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item, float4 *buf, float2 *dn, float4 *sc,
+                                             float2 *sc2, float *rec, int lane) {
     const int r = (int)(item / A.n_bands), b = (int)(item % A.n_bands);
     double acc[ADJ_ITEM_VALS] = {0, 0, 0, 0, 0, 0};
     const float4 q = A.P.reach[r];
     if (reach_overlap(q, A.band_bounds[b])) {
-        float *rec = s_rec[warp];
         load_record(A.P.recs, r, rec, lane);
         const int pj0 = b * A.rows_per_band, pj1 = min(A.npy, pj0 + A.rows_per_band);
         const int np = (pj1 - pj0) * A.npx;
@@ -113,8 +105,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
                 if (__ballot_sync(FDX_FULL_MASK, c != 0.0f) == 0) continue;
                 PairAcc pa[1];
                 clear(pa[0]);
-                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, 1>(A.P, g, rec, s_nodes[warp], s_dn[warp],
-                                                                             s_sc[warp], s_sc2[warp], lane, pa))
+                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, 1>(A.P, g, rec, buf, dn, sc, sc2, lane, pa))
                     continue;
                 const double cd = (double)c;
                 const PairAcc &a = pa[0];
@@ -133,6 +124,47 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
         for (int k = 1; k < ADJ_ITEM_VALS; ++k)
             if (lane == k) o = acc[k];
         A.item_out[item * ADJ_ITEM_VALS + lane] = o;
+    }
+}
+
+#define FDX_ADJ_SMEM                                        \
+    __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];    \
+    __shared__ float2 s_dn[PAIR_WARPS][ADJ_NODE_BUF];       \
+    __shared__ float4 s_sc[PAIR_WARPS][ADJ_NODE_BUF];       \
+    __shared__ float2 s_sc2[PAIR_WARPS][ADJ_NODE_BUF];      \
+    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
+    FDX_ADJ_SMEM
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
+    if (item >= (long long)A.P.n_refl * A.n_bands) return;
+    adjoint_item(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+}
+
+__device__ __forceinline__ int batch_model(const long long *prefix, int n_models, long long item) {
+    int lo = 0, hi = n_models - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent adjoint over many models: each warp takes (model, reflection,
+// band) items from an atomic counter; items are independent, so the order in
+// which they are taken does not change any result.
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(BatchAdjParams B) {
+    FDX_ADJ_SMEM
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(B.counter, 1u);
+        const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
+        if (item >= B.total_items) break;
+        const int m = batch_model(B.item_prefix, B.n_models, item);
+        adjoint_item(B.models[m], item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
+                     s_rec[warp], lane);
     }
 }
 
@@ -356,6 +388,17 @@ cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
         adjoint_kernel<<<(unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS), PAIR_WARPS * 32, 0, s>>>(A);
         adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
     }
+    adjoint_globals_kernel<<<1, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_sm, cudaStream_t s) {
+    adjoint_batch_kernel<<<n_sm * 3, PAIR_WARPS * 32, 0, s>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s) {
+    if (A.P.n_refl > 0) adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
     adjoint_globals_kernel<<<1, 256, 0, s>>>(A);
     return cudaGetLastError();
 }

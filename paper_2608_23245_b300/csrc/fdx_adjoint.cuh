@@ -25,6 +25,14 @@ struct AdjParams {
     double alen[3], L[3], g[3], Bax[3];
 };
 
+struct BatchAdjParams {
+    const AdjParams *models;       // [n_models] device
+    const long long *item_prefix;  // [n_models] exclusive prefix of (reflection, band) items
+    long long total_items;
+    int n_models;
+    unsigned *counter;             // zeroed before the launch
+};
+
 struct SFAdjParams {
     int n_atoms, n_elem, n_refl, n_split, refl_per_split;
     const uint4 *atoms_q;
@@ -66,6 +74,8 @@ struct Plain64Params {
 
 cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s);
 cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s);
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_sm, cudaStream_t s);
+cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s);
 cudaError_t launch_globals_only(AdjParams &A, cudaStream_t s);
 cudaError_t launch_plain64_forward(Plain64Params &p, cudaStream_t s);
 cudaError_t launch_plain64_loss(Plain64Params &p, cudaStream_t s);

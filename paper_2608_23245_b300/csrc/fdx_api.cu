@@ -237,9 +237,217 @@ BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
     return B;
 }
 
+// Writes one model's parameter blocks and item prefixes into the batch tables
+// (a kernel, so that the whole batch step can be captured in a CUDA graph).
+__global__ void batch_write_params(PatternParams *fdst, const PatternParams P, AdjParams *adst, const AdjParams A,
+                                   long long *fpre, long long fp, long long *apre, long long ap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *fdst = P;
+        *adst = A;
+        *fpre = fp;
+        *apre = ap;
+    }
+}
+
+struct BatchLayout {
+    size_t fwd_tab, adj_tab, fpre, apre, counters, head;
+    std::vector<size_t> region, back, sf, gI, loss;
+    size_t total;
+};
+
+BatchLayout batch_layout(int n, const fdx_problem *const *probs, const fdx_atoms *const *atoms) {
+    BatchLayout L;
+    size_t off = 0;
+    L.fwd_tab = off, off += align_up(sizeof(PatternParams) * n);
+    L.adj_tab = off, off += align_up(sizeof(AdjParams) * n);
+    L.fpre = off, off += align_up(sizeof(long long) * n);
+    L.apre = off, off += align_up(sizeof(long long) * n);
+    L.counters = off, off += align_up(sizeof(unsigned) * 2);
+    L.head = off;
+    for (int m = 0; m < n; ++m) {
+        const fdx_problem *p = probs[m];
+        const size_t npx = (size_t)p->geom.n_x * p->geom.n_y;
+        L.region.push_back(off);
+        L.back.push_back(off), off += back_layout(p, atoms[m]->n_atoms, atoms[m]->n_elem).total;
+        L.sf.push_back(off), off += align_up(fdx_sf_workspace_size(atoms[m]->n_atoms, p->n_refl > 0 ? p->n_refl : 1));
+        L.gI.push_back(off), off += align_up(sizeof(float) * npx);
+        L.loss.push_back(off), off += align_up(sizeof(double) * ((npx + 255) / 256));
+    }
+    L.total = off;
+    return L;
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t fdx_batch_workspace_size(int32_t n_models, const fdx_problem *const *probs, const fdx_atoms *const *atoms) {
+    if (n_models < 1 || !probs || !atoms) return 0;
+    for (int m = 0; m < n_models; ++m)
+        if (!probs[m] || !atoms[m] || atoms[m]->n_atoms < 1 || atoms[m]->n_elem < 1) return 0;
+    return batch_layout(n_models, probs, atoms).total;
+}
+
+int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fdx_atoms *const *atoms,
+                     float *const *F, float *const *M, float *const *images, const float *const *targets,
+                     const float *const *masks, double *losses, const fdx_grads *const *grads, void *workspace,
+                     size_t ws_bytes, void *stream) {
+    if (n_models < 1 || !probs || !atoms || !F || !M || !images) return FDX_ERR_ARG;
+    if (targets && (!losses || !grads)) return FDX_ERR_ARG;
+    for (int m = 0; m < n_models; ++m) {
+        if (!probs[m] || !atoms[m] || !images[m]) return FDX_ERR_ARG;
+        fdx_problem pr = *probs[m];
+        pr.M = M[m];
+        int rc = validate_problem(&pr);
+        if (rc) return rc;
+        if (pr.br.lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
+        const fdx_atoms *a = atoms[m];
+        if (a->n_atoms < 1 || a->n_elem < 1 || a->n_elem > 64 || !a->frac || !a->B || !a->elem || !a->ff)
+            return FDX_ERR_ARG;
+        if (pr.n_refl > 0 && (!F[m] || !M[m])) return FDX_ERR_ARG;
+        if (targets && (!targets[m] || !grads[m])) return FDX_ERR_ARG;
+    }
+    const BatchLayout L = batch_layout(n_models, probs, atoms);
+    if (!workspace || ws_bytes < L.total || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    int dev = 0, n_sm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDX_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    unsigned *counters = reinterpret_cast<unsigned *>(ws + L.counters);
+    if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    std::vector<AdjParams> adj(n_models);
+    long long fsum = 0, asum = 0;
+    for (int m = 0; m < n_models; ++m) {
+        fdx_problem pr = *probs[m];
+        pr.M = M[m];
+        const fdx_atoms *a = atoms[m];
+        char *reg = ws + L.back[m];
+        // structure factors -> F, M
+        if (pr.n_refl > 0) {
+            SFParams sp;
+            memset(&sp, 0, sizeof sp);
+            double Am[9], As[9];
+            cell_basis(pr.cell, Am, As);
+            memcpy(sp.As, As, sizeof As);
+            sp.n_atoms = a->n_atoms, sp.n_elem = a->n_elem, sp.n_refl = pr.n_refl;
+            const int refl_blocks = (pr.n_refl + 127) / 128;
+            int n_split = (600 + refl_blocks - 1) / refl_blocks;
+            n_split = n_split < 1 ? 1 : (n_split > 64 ? 64 : n_split);
+            const int by_atoms = (a->n_atoms + 511) / 512;
+            if (n_split > by_atoms) n_split = by_atoms;
+            if (n_split < 1) n_split = 1;
+            int per = (a->n_atoms + n_split - 1) / n_split;
+            per = (per + 255) / 256 * 256;
+            sp.n_split = (a->n_atoms + per - 1) / per, sp.atoms_per_split = per;
+            sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
+            char *sw = ws + L.sf[m];
+            size_t o2 = 0;
+            sp.atoms_q = reinterpret_cast<uint4 *>(sw + o2), o2 += align_up(sizeof(uint4) * (size_t)a->n_atoms);
+            sp.atoms_w = reinterpret_cast<float2 *>(sw + o2), o2 += align_up(sizeof(float2) * (size_t)a->n_atoms);
+            sp.partial = reinterpret_cast<float4 *>(sw + o2);
+            sp.hkl = pr.hkl, sp.F_out = F[m], sp.M_out = M[m];
+            sp.has_br = 1, sp.intensity_model = pr.br.intensity_model;
+            for (int i = 0; i < 3; ++i) {
+                sp.g[i] = pr.br.g[i], sp.Bax[i] = pr.br.B_axis[i];
+                sp.alen[i] = sqrt(Am[3 * i] * Am[3 * i] + Am[3 * i + 1] * Am[3 * i + 1] + Am[3 * i + 2] * Am[3 * i + 2]);
+            }
+            if (launch_structure_factors(sp, st) != cudaSuccess) return FDX_ERR_CUDA;
+        }
+        // set-up kernels and parameter blocks
+        PatternParams P;
+        int rc = setup_pattern(&pr, reg, st, P, targets != nullptr);
+        if (rc) return rc;
+        P.image = images[m];
+        P.counts = nullptr;
+        const BackLayout B = back_layout(&pr, a->n_atoms, a->n_elem);
+        AdjParams &A = adj[m];
+        memset(&A, 0, sizeof A);
+        A.P = P;
+        double Am[9], As[9];
+        cell_basis(pr.cell, Am, As);
+        memcpy(A.As, As, sizeof As);
+        for (int i = 0; i < 3; ++i) {
+            A.alen[i] = sqrt(Am[3 * i] * Am[3 * i] + Am[3 * i + 1] * Am[3 * i + 1] + Am[3 * i + 2] * Am[3 * i + 2]);
+            A.L[i] = pr.br.L[i], A.g[i] = pr.br.g[i], A.Bax[i] = pr.br.B_axis[i];
+        }
+        A.patch_bounds = reinterpret_cast<float4 *>(reg + B.patch_bounds);
+        A.band_bounds = reinterpret_cast<float4 *>(reg + B.band_bounds);
+        A.npx = B.npx, A.npy = B.npy, A.n_bands = B.n_bands, A.rows_per_band = B.rows_per_band;
+        A.gI = reinterpret_cast<float *>(ws + L.gI[m]);
+        A.item_out = reinterpret_cast<double *>(reg + B.item_out);
+        A.refl_out = reinterpret_cast<double *>(reg + B.refl_out);
+        A.cF = reinterpret_cast<float4 *>(reg + B.cF);
+        A.fe = reinterpret_cast<float *>(reg + B.fe);
+        A.dM = targets ? grads[m]->dM : nullptr;
+        A.dglobal = targets ? grads[m]->dglobal : nullptr;
+        A.hkl = pr.hkl, A.F = F[m], A.ff = a->ff, A.n_elem = a->n_elem, A.intensity_model = pr.br.intensity_model;
+        const int ppl = P.ppl;
+        const long long ftiles = (long long)((pr.geom.n_x + 15) / 16) * ((pr.geom.n_y + 8 * ppl - 1) / (8 * ppl));
+        const long long aitems = (long long)pr.n_refl * B.n_bands;
+        batch_write_params<<<1, 32, 0, st>>>(reinterpret_cast<PatternParams *>(ws + L.fwd_tab) + m, P,
+                                             reinterpret_cast<AdjParams *>(ws + L.adj_tab) + m, A,
+                                             reinterpret_cast<long long *>(ws + L.fpre) + m, fsum,
+                                             reinterpret_cast<long long *>(ws + L.apre) + m, asum);
+        if (cudaGetLastError() != cudaSuccess) return FDX_ERR_CUDA;
+        fsum += ftiles;
+        asum += aitems;
+    }
+    // one persistent forward launch over all models
+    BatchFwdParams BF;
+    BF.models = reinterpret_cast<const PatternParams *>(ws + L.fwd_tab);
+    BF.item_prefix = reinterpret_cast<const long long *>(ws + L.fpre);
+    BF.total_items = fsum, BF.n_models = n_models, BF.counter = counters;
+    if (launch_pattern_batch(BF, n_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (!targets) return FDX_OK;
+
+    for (int m = 0; m < n_models; ++m) {
+        const fdx_problem *pr = probs[m];
+        LossParams lp;
+        lp.n = (long long)pr->geom.n_x * pr->geom.n_y, lp.I = images[m], lp.It = targets[m];
+        lp.mask = masks ? masks[m] : nullptr, lp.gI = adj[m].gI == nullptr ? nullptr : const_cast<float *>(adj[m].gI);
+        lp.partial = reinterpret_cast<double *>(ws + L.loss[m]);
+        lp.loss = losses + m;
+        if (launch_loss(lp, st) != cudaSuccess) return FDX_ERR_CUDA;
+        if (launch_bounds_only(adj[m], st) != cudaSuccess) return FDX_ERR_CUDA;
+    }
+    // one persistent adjoint launch over all models
+    BatchAdjParams BA;
+    BA.models = reinterpret_cast<const AdjParams *>(ws + L.adj_tab);
+    BA.item_prefix = reinterpret_cast<const long long *>(ws + L.apre);
+    BA.total_items = asum, BA.n_models = n_models, BA.counter = counters + 1;
+    if (asum > 0 && launch_adjoint_batch(BA, n_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    for (int m = 0; m < n_models; ++m) {
+        const fdx_problem *pr = probs[m];
+        const fdx_atoms *a = atoms[m];
+        if (launch_adjoint_post(adj[m], st) != cudaSuccess) return FDX_ERR_CUDA;
+        if (pr->n_refl > 0 && (grads[m]->dfrac || grads[m]->dB)) {
+            const BackLayout B = back_layout(pr, a->n_atoms, a->n_elem);
+            char *reg = ws + L.back[m];
+            SFParams sp;
+            memset(&sp, 0, sizeof sp);
+            sp.n_atoms = a->n_atoms, sp.n_elem = a->n_elem;
+            sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
+            sp.atoms_q = reinterpret_cast<uint4 *>(reg + B.atoms_q);
+            sp.atoms_w = reinterpret_cast<float2 *>(reg + B.atoms_w);
+            if (launch_sf_pack(sp, st) != cudaSuccess) return FDX_ERR_CUDA;
+            SFAdjParams q;
+            memset(&q, 0, sizeof q);
+            q.n_atoms = a->n_atoms, q.n_elem = a->n_elem, q.n_refl = pr->n_refl;
+            q.n_split = B.sf_split, q.refl_per_split = B.refl_per_split;
+            q.atoms_q = sp.atoms_q, q.atoms_w = sp.atoms_w;
+            q.hkl = pr->hkl, q.cF = adj[m].cF, q.fe = adj[m].fe;
+            q.partial = reinterpret_cast<double *>(reg + B.sf_partial);
+            q.dfrac = grads[m]->dfrac, q.dB = grads[m]->dB;
+            if (launch_sf_adjoint(q, st) != cudaSuccess) return FDX_ERR_CUDA;
+        } else if (pr->n_refl == 0) {
+            if (grads[m]->dfrac && cudaMemsetAsync(grads[m]->dfrac, 0, sizeof(double) * 3 * a->n_atoms, st)) return FDX_ERR_CUDA;
+            if (grads[m]->dB && cudaMemsetAsync(grads[m]->dB, 0, sizeof(double) * a->n_atoms, st)) return FDX_ERR_CUDA;
+        }
+    }
+    return FDX_OK;
+}
 
 int fdx_version(void) { return 100; }
 

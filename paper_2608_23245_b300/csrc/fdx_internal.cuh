@@ -136,6 +136,16 @@ struct PatternParams {
     int32_t *counts;      // [ny][nx] (count mode)
 };
 
+// Forward over many models (pattern_batch_kernel): per-model parameters in
+// device memory, item prefix (CTA tiles per model), atomic item counter.
+struct BatchFwdParams {
+    const PatternParams *models;  // [n_models] device
+    const long long *item_prefix; // [n_models] exclusive prefix of items
+    long long total_items;
+    int n_models;
+    unsigned *counter;            // zeroed before the launch
+};
+
 struct ReflSetupParams {
     double A[9], As[9];   // real basis rows a, b, c and reciprocal rows a*, b*, c*
     double nh[3], bh[3];  // unit fiber and beam axes
@@ -182,6 +192,7 @@ cudaError_t launch_pixel_geometry(const PixelParams &p, cudaStream_t s);
 cudaError_t launch_nodes(const NodeParams &p, const WeidemanCoeffs &wc, cudaStream_t s);
 cudaError_t launch_refl_setup(const ReflSetupParams &p, cudaStream_t s);
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s);
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_sm, cudaStream_t s);
 
 struct SFParams {
     int n_atoms, n_elem, n_refl, n_split, atoms_per_split;

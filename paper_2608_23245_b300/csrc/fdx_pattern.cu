@@ -18,16 +18,11 @@ static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp; 4 warps x 28
 // the patch spans a small fraction of a lattice period, else 1 (8 x 4, 16 x 8);
 // chosen on the host from the pixel pitch and the cell.
 
+// One warp's 8 x (4 PPL) patch with top-left pixel (px0, py0): scan the
+// reflections, evaluate the surviving pairs, write the pixels.
 template <int LS, int MODE, int PPL>
-__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternParams P) {
-    __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];
-    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1];
-    __shared__ float2 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1];
-    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * (8 * PPL) + (warp >> 1) * (4 * PPL);
-    if (px0 >= P.nx || py0 >= P.ny) return;  // the whole patch is outside; lane 0's first pixel is valid otherwise
+__device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, int py0, float4 *buf, float4 *bsc,
+                                             float2 *bsc2, float *rec, int lane) {
     const PatchPix<PPL> g = load_patch<PPL>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
 
     float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
@@ -39,8 +34,6 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
     }
     rmin = warp_min(rmin), rmax = warp_max(rmax), pmin = warp_min(pmin), pmax = warp_max(pmax);
 
-    float *rec = s_rec[warp];
-    float4 *buf = s_nodes[warp];
     ff acc[PPL];
     int32_t cnt[PPL];
 #pragma unroll
@@ -61,8 +54,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
             PairAcc pa[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) clear(pa[p]);
-            if (!eval_pair<LS, MODE, FWD_NODE_BUF, PPL>(P, g, rec, buf, nullptr, s_sc[warp], s_sc2[warp], lane, pa))
-                continue;
+            if (!eval_pair<LS, MODE, FWD_NODE_BUF, PPL>(P, g, rec, buf, nullptr, bsc, bsc2, lane, pa)) continue;
 #pragma unroll
             for (int p = 0; p < PPL; ++p) {
                 if (MODE == MODE_CNT)
@@ -85,6 +77,66 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
             P.image[out] = (float)(L * ((double)acc[p].hi + (double)acc[p].lo));
         }
     }
+}
+
+#define FDX_PATTERN_SMEM(LS, MODE)                                                                  \
+    __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];                                            \
+    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1]; \
+    __shared__ float2 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1]; \
+    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+
+template <int LS, int MODE, int PPL>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternParams P) {
+    FDX_PATTERN_SMEM(LS, MODE)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * (8 * PPL) + (warp >> 1) * (4 * PPL);
+    if (px0 >= P.nx || py0 >= P.ny) return;  // the whole patch is outside; its first pixel is valid otherwise
+    pattern_warp<LS, MODE, PPL>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+}
+
+// Model of a flattened item index: the last m with prefix[m] <= item.
+__device__ __forceinline__ int item_model(const long long *prefix, int n_models, long long item) {
+    int lo = 0, hi = n_models - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent forward over many models: CTAs take (model, tile) items from an
+// atomic counter until the items of all models are done.  Every item is
+// computed by one CTA start to finish, so the result does not depend on the
+// order in which items are taken.
+template <int LS>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(BatchFwdParams B) {
+    FDX_PATTERN_SMEM(LS, MODE_FWD)
+    __shared__ long long s_item;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        if (item >= B.total_items) break;
+        const int m = item_model(B.item_prefix, B.n_models, item);
+        const PatternParams &P = B.models[m];
+        const int t = (int)(item - B.item_prefix[m]);
+        const int ppl = P.ppl;
+        const int tiles_x = (P.nx + 15) / 16;
+        const int bx = t % tiles_x, by = t / tiles_x;
+        const int px0 = bx * 16 + (warp & 1) * 8, py0 = by * (8 * ppl) + (warp >> 1) * (4 * ppl);
+        if (px0 >= P.nx || py0 >= P.ny) continue;
+        if (ppl == 2)
+            pattern_warp<LS, MODE_FWD, 2>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+        else
+            pattern_warp<LS, MODE_FWD, 1>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    }
+}
+
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_sm, cudaStream_t s) {
+    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_sm * 4, PAIR_WARPS * 32, 0, s>>>(B);
+    return cudaGetLastError();
 }
 
 template <int PPL>

@@ -407,3 +407,71 @@ def fdx_plain64_refine(problem, datoms, image, I_target=None, mask=None, loss=No
                                 C.byref(g), _ptr(workspace), int(workspace.numel()), _stream(stream)),
            "fdx_plain64_refine")
     return image, loss
+
+
+# ---------------------------------------------------------------------------
+# batched refinement of many models
+# ---------------------------------------------------------------------------
+
+def _bind_batch(L):
+    if getattr(L, "_batch_bound", False):
+        return L
+    P = C.POINTER(C.POINTER(Problem))
+    A = C.POINTER(C.POINTER(Atoms))
+    V = C.POINTER(C.c_void_p)
+    L.fdx_batch_workspace_size.restype = C.c_size_t
+    L.fdx_batch_workspace_size.argtypes = [C.c_int32, P, A]
+    L.fdx_batch_refine.argtypes = [C.c_int32, P, A, V, V, V, V, V, C.c_void_p, C.POINTER(C.POINTER(Grads)),
+                                   C.c_void_p, C.c_size_t, C.c_void_p]
+    L._batch_bound = True
+    return L
+
+
+def _atoms_array(atoms_structs):
+    return (C.POINTER(Atoms) * len(atoms_structs))(*[C.pointer(a) for a in atoms_structs])
+
+
+def _vptrs(tensors):
+    return (C.c_void_p * len(tensors))(*[(t.data_ptr() if t is not None else None) for t in tensors])
+
+
+def fdx_batch_workspace_size(problems, atoms_structs) -> int:
+    L = _bind_batch(lib())
+    return int(L.fdx_batch_workspace_size(len(problems), _problem_array(problems), _atoms_array(atoms_structs)))
+
+
+class BatchStep:
+    """Device buffers and argument arrays for fdx_batch_refine over fixed
+    problems; call() issues the whole step on the current stream (capturable
+    in a CUDA graph: every argument is a device pointer fixed at construction)."""
+
+    def __init__(self, problems, datoms, targets=None, masks=None, device="cuda"):
+        import torch
+        self.problems = problems
+        self.datoms = datoms
+        self.astructs = [d.struct() for d in datoms]
+        n = len(problems)
+        self.F = [torch.empty((p.n_refl, 2), dtype=torch.float32, device=device) for p in problems]
+        self.M = [torch.empty((max(p.n_refl, 1),), dtype=torch.float32, device=device) for p in problems]
+        self.images = [torch.empty((p.geom.n_y, p.geom.n_x), dtype=torch.float32, device=device) for p in problems]
+        self.targets = targets
+        self.masks = masks
+        self.losses = torch.zeros(n, dtype=torch.float64, device=device)
+        self.dfrac = [torch.empty((a.n_atoms, 3), dtype=torch.float64, device=device) for a in self.astructs]
+        self.dB = [torch.empty((a.n_atoms,), dtype=torch.float64, device=device) for a in self.astructs]
+        self.dglobal = [torch.empty(8, dtype=torch.float64, device=device) for _ in problems]
+        self.dM = [torch.empty((max(p.n_refl, 1),), dtype=torch.float32, device=device) for p in problems]
+        self.gstructs = [Grads(self.dfrac[m].data_ptr(), self.dB[m].data_ptr(), self.dglobal[m].data_ptr(),
+                               self.dM[m].data_ptr()) for m in range(n)]
+        self.ws = torch.empty(max(fdx_batch_workspace_size(problems, self.astructs), 256), dtype=torch.uint8,
+                              device=device)
+        self._args = (n, _problem_array(problems), _atoms_array(self.astructs), _vptrs(self.F), _vptrs(self.M),
+                      _vptrs(self.images), _vptrs(targets) if targets is not None else None,
+                      _vptrs(masks) if masks is not None else None,
+                      C.c_void_p(self.losses.data_ptr()) if targets is not None else None,
+                      (C.POINTER(Grads) * n)(*[C.pointer(g) for g in self.gstructs]) if targets is not None else None,
+                      C.c_void_p(self.ws.data_ptr()), int(self.ws.numel()))
+
+    def __call__(self, stream=None):
+        L = _bind_batch(lib())
+        _check(L.fdx_batch_refine(*self._args, _stream(stream)), "fdx_batch_refine")

@@ -259,6 +259,41 @@ def config4(n_models: int = 256) -> List[Problem]:
     return [config4_model(m) for m in range(n_models)]
 
 
+def config4_target(model: Problem, m: int) -> Problem:
+    """Seeded perturbation of batched model m (as for the helix refinement):
+    Cartesian coordinates +-0.2 A (orthorhombic cell: fractional +-0.2/edge),
+    B +-5 A^2, sizes x (1 +- 20 %), sigma +-1 deg (gamma unchanged), g +-1 %
+    (kept >= 0)."""
+    rng = np.random.Generator(np.random.PCG64((SEED_BASE + 4) * 1000 + 500 + m))
+    edges = np.array(model.cell[:3])
+    frac = model.atoms.frac + rng.uniform(-0.2, 0.2, size=model.atoms.frac.shape) / edges[None, :]
+    B = model.atoms.B + rng.uniform(-5.0, 5.0, size=model.atoms.n)
+    fL = 1.0 + rng.uniform(-0.2, 0.2)
+    dsig = math.radians(rng.uniform(-1.0, 1.0))
+    dg = rng.uniform(-0.01, 0.01)
+    br = replace(model.br, L=tuple(fL * x for x in model.br.L), sigma=max(model.br.sigma + dsig, math.radians(0.5)),
+                 g=tuple(max(0.0, x + dg) for x in model.br.g))
+    return replace(model, name=model.name + "_target", atoms=replace(model.atoms, frac=frac, B=B), br=br)
+
+
+def small_batch(n_models: int = 5) -> List[Problem]:
+    """Reduced batched-refinement models for tests: the config-4 recipe with
+    the detector cut to a seeded 40-72 px ROI of the same angular coverage and
+    at most 600 atoms."""
+    out = []
+    for m in range(n_models):
+        p = config4_model(m)
+        rng = np.random.Generator(np.random.PCG64(SEED_BASE + 40 + m))
+        side = int(rng.integers(40, 73))
+        k = min(p.atoms.n, 600)
+        atoms = Atoms(frac=p.atoms.frac[:k].copy(), B=p.atoms.B[:k].copy(), occ=p.atoms.occ[:k].copy(),
+                      elem=p.atoms.elem[:k].copy(), ff=p.atoms.ff)
+        geom = replace(p.geom, n_x=side, n_y=side + int(rng.integers(0, 9)), pixel=p.geom.pixel * p.geom.n_x / side)
+        br = replace(p.br, n_nodes=20)
+        out.append(replace(p, name="small_batch%d" % m, atoms=atoms, geom=geom, br=br, d_min=3.0))
+    return out
+
+
 # ---------------------------------------------------------------------------
 # Reduced variants: same recipes, sized so the FP64 oracle finishes a whole
 # detector in seconds.  Each spans several 16x8-pixel tiles and leaves ragged
