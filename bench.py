@@ -200,6 +200,75 @@ def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
             "fp32_over_plain_fp64_roi": roi64 / roi32}
 
 
+def batch_measurements(n_models=256, tune_models=8):
+    """Batched refinement (config-4 recipe): n_models seeded candidate models of
+    uneven size, each against its own perturbed target.  One step = structure
+    factors + pattern + loss + adjoint for every model.  The batched step
+    (fdx_batch_refine: one persistent forward and one persistent adjoint launch
+    over all models) runs as a captured CUDA graph with launch shapes from the
+    autotuner (tuned on the first tune_models models); the comparison is a loop
+    over models calling the per-model entry points."""
+    import torch
+    from paper_2608_23245_b300 import fdx, tune, workloads as W
+    models = W.config4(n_models)
+    sims = [fdx.Simulation(p) for p in models]
+    tims = []
+    for m, p in enumerate(models):
+        s = fdx.Simulation(W.config4_target(p, m))
+        tims.append(s.forward().clone())
+        del s
+    probs = [s.prob for s in sims]
+    datoms = [s.atoms for s in sims]
+    grid = {"ppl_max": (2, 1), "fwd_ctas_per_sm": (4, 3), "adj_ctas_per_sm": (3, 2), "adj_bands": (16,)}
+    best, _ = tune.autotune_batch(probs[:tune_models], datoms[:tune_models], tims[:tune_models], grid=grid)
+    E = 0
+    for s in sims:
+        s.forward()
+        E += int(s.evals().to(torch.int64).sum().item())
+
+    def loop():
+        for s, It in zip(sims, tims):
+            s.forward()
+            gI = torch.empty_like(s.image)
+            fdx.fdx_loss(s.image, It, None, dL_dI=gI)
+            na = s.atoms.frac.shape[0]
+            dfrac = torch.empty((na, 3), dtype=torch.float64, device="cuda")
+            dB = torch.empty(na, dtype=torch.float64, device="cuda")
+            dg = torch.empty(8, dtype=torch.float64, device="cuda")
+            fdx.fdx_pattern_backward(s.prob, s.atoms, s.F, gI, dfrac, dB, dg, None)
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    loop()
+    e1.record()
+    torch.cuda.synchronize()
+    t_loop = e0.elapsed_time(e1) / 1e3
+    step = fdx.BatchStep(probs, datoms, targets=tims)
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        step(st)
+        torch.cuda.current_stream().synchronize()
+        with torch.cuda.graph(g, stream=st):
+            step(st)
+    torch.cuda.current_stream().wait_stream(st)
+    g.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    return {"workload": "%d seeded models (config-4 recipe: 500-8,000 atoms, 10-40 A edges, d >= 2 A, "
+                        "256^2-960^2 detectors, Gaussian/Voigt, 64^2 nodes), each vs its perturbed target" % n_models,
+            "n_models": n_models, "forward_evals_per_step": E,
+            "batched_graph_models_per_s": n_models / t_batch, "batched_graph_s_per_step": t_batch,
+            "per_model_loop_models_per_s": n_models / t_loop, "per_model_loop_s_per_step": t_loop,
+            "batched_over_loop": t_loop / t_batch, "tuning": best}
+
+
 def cpu_baseline(problem, budget_s=12.0, n_pix=None, seed=5):
     """Time the FP64 oracle (as it stands) on a bounded pixel sample."""
     import oracle
@@ -264,6 +333,8 @@ def main():
     ap.add_argument("--impl", default="fdx", choices=["fdx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-models", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -367,6 +438,8 @@ def main():
     }
     if not args.no_refine:
         line["refine"] = refine_measurements()
+    if not args.no_batch:
+        line["batch"] = batch_measurements(args.batch_models)
     if not args.no_cpu_baseline:
         cb, _ = cpu_baseline(p)
         line["cpu_baseline"] = cb

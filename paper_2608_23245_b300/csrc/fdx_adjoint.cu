@@ -392,8 +392,8 @@ cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_sm, cudaStream_t s) {
-    adjoint_batch_kernel<<<n_sm * 3, PAIR_WARPS * 32, 0, s>>>(B);
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s) {
+    adjoint_batch_kernel<<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,7 @@ struct Plain64Params {
 
 cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s);
 cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s);
-cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_sm, cudaStream_t s);
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s);
 cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s);
 cudaError_t launch_globals_only(AdjParams &A, cudaStream_t s);
 cudaError_t launch_plain64_forward(Plain64Params &p, cudaStream_t s);

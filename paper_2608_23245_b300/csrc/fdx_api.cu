@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "fdx_adjoint.cuh"
@@ -13,6 +14,14 @@ using namespace fdx;
 namespace {
 
 constexpr size_t kAlign = 256;
+
+std::mutex g_tune_mu;
+fdx_tuning g_tune = {2, 4, 3, 16};
+
+fdx_tuning tuning() {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return g_tune;
+}
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -167,7 +176,7 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
         const double pitch = p->geom.pixel / (p->geom.wavelength * p->geom.distance);
         double amax = 0.0;
         for (int q = 0; q < 3; ++q) amax = fmax(amax, rp.alen[q]);
-        P.ppl = pitch * 8.0 * sqrt(2.0) * amax <= 0.5 ? 2 : 1;
+        P.ppl = (pitch * 8.0 * sqrt(2.0) * amax <= 0.5 && tuning().ppl_max >= 2) ? 2 : 1;
     }
     P.pixgeo = pp.pixgeo;
     P.reach = rp.reach;
@@ -200,7 +209,8 @@ BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
     BackLayout B;
     const size_t nr = (size_t)(p->n_refl > 0 ? p->n_refl : 1);
     B.npx = (p->geom.n_x + 7) / 8, B.npy = (p->geom.n_y + 3) / 4;
-    B.n_bands = B.npy < 16 ? B.npy : 16;
+    const int want_bands = tuning().adj_bands;
+    B.n_bands = B.npy < want_bands ? B.npy : want_bands;
     B.rows_per_band = (B.npy + B.n_bands - 1) / B.n_bands;
     B.n_bands = (B.npy + B.rows_per_band - 1) / B.rows_per_band;
     const int atom_blocks = (n_atoms + 127) / 128;
@@ -399,7 +409,8 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
     BF.models = reinterpret_cast<const PatternParams *>(ws + L.fwd_tab);
     BF.item_prefix = reinterpret_cast<const long long *>(ws + L.fpre);
     BF.total_items = fsum, BF.n_models = n_models, BF.counter = counters;
-    if (launch_pattern_batch(BF, n_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    const fdx_tuning tu = tuning();
+    if (launch_pattern_batch(BF, n_sm * tu.fwd_ctas_per_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
     if (!targets) return FDX_OK;
 
     for (int m = 0; m < n_models; ++m) {
@@ -417,7 +428,7 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
     BA.models = reinterpret_cast<const AdjParams *>(ws + L.adj_tab);
     BA.item_prefix = reinterpret_cast<const long long *>(ws + L.apre);
     BA.total_items = asum, BA.n_models = n_models, BA.counter = counters + 1;
-    if (asum > 0 && launch_adjoint_batch(BA, n_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (asum > 0 && launch_adjoint_batch(BA, n_sm * tu.adj_ctas_per_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
     for (int m = 0; m < n_models; ++m) {
         const fdx_problem *pr = probs[m];
         const fdx_atoms *a = atoms[m];
@@ -450,6 +461,25 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
 }
 
 int fdx_version(void) { return 100; }
+
+int fdx_set_tuning(const fdx_tuning *t) {
+    fdx_tuning v = {2, 4, 3, 16};
+    if (t) {
+        if (t->ppl_max < 1 || t->ppl_max > 2 || t->fwd_ctas_per_sm < 1 || t->fwd_ctas_per_sm > 8 ||
+            t->adj_ctas_per_sm < 1 || t->adj_ctas_per_sm > 8 || t->adj_bands < 1 || t->adj_bands > 64)
+            return FDX_ERR_ARG;
+        v = *t;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune = v;
+    return FDX_OK;
+}
+
+int fdx_get_tuning(fdx_tuning *t) {
+    if (!t) return FDX_ERR_ARG;
+    *t = tuning();
+    return FDX_OK;
+}
 
 const char *fdx_error_string(int code) {
     switch (code) {

@@ -192,7 +192,7 @@ cudaError_t launch_pixel_geometry(const PixelParams &p, cudaStream_t s);
 cudaError_t launch_nodes(const NodeParams &p, const WeidemanCoeffs &wc, cudaStream_t s);
 cudaError_t launch_refl_setup(const ReflSetupParams &p, cudaStream_t s);
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s);
-cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_sm, cudaStream_t s);
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s);
 
 struct SFParams {
     int n_atoms, n_elem, n_refl, n_split, atoms_per_split;

@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(Batch
     }
 }
 
-cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_sm, cudaStream_t s) {
-    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_sm * 4, PAIR_WARPS * 32, 0, s>>>(B);
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s) {
+    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
     return cudaGetLastError();
 }
 

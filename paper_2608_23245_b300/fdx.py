@@ -475,3 +475,22 @@ class BatchStep:
     def __call__(self, stream=None):
         L = _bind_batch(lib())
         _check(L.fdx_batch_refine(*self._args, _stream(stream)), "fdx_batch_refine")
+
+
+class Tuning(C.Structure):
+    _fields_ = [("ppl_max", C.c_int32), ("fwd_ctas_per_sm", C.c_int32), ("adj_ctas_per_sm", C.c_int32),
+                ("adj_bands", C.c_int32)]
+
+
+def fdx_set_tuning(t=None):
+    L = lib()
+    L.fdx_set_tuning.argtypes = [C.POINTER(Tuning)]
+    _check(L.fdx_set_tuning(C.byref(t) if t is not None else None), "fdx_set_tuning")
+
+
+def fdx_get_tuning() -> Tuning:
+    L = lib()
+    L.fdx_get_tuning.argtypes = [C.POINTER(Tuning)]
+    t = Tuning()
+    _check(L.fdx_get_tuning(C.byref(t)), "fdx_get_tuning")
+    return t
