@@ -76,48 +76,78 @@ __global__ void band_bounds_kernel(AdjParams A) {
     if (threadIdx.x == 0) A.band_bounds[b] = red[0];
 }
 
-// One (reflection, band) item of the adjoint for one warp.
-__device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item, float4 *buf, float2 *dn, float4 *sc,
-                                             float2 *sc2, float *rec, int lane) {
+// One (reflection, band) item of the adjoint for one warp.  With PPL = 2 the
+// warp's patch is 8 x 8 pixels (two rows of 8 x 4 bound patches; bands hold
+// an even number of patch rows).  Per lane, the pair sums times the pixel's
+// c = dL/dI L are accumulated in float-float over the item's patches; the
+// warp adds its lanes in FP64 once at the end.
+template <int PPL>
+__device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item, float4 *buf, float4 *dn, float4 *sc,
+                                             float4 *sc2, float *rec, int lane) {
     const int r = (int)(item / A.n_bands), b = (int)(item % A.n_bands);
-    double acc[ADJ_ITEM_VALS] = {0, 0, 0, 0, 0, 0};
+    ff ia[ADJ_ITEM_VALS];
+#pragma unroll
+    for (int k = 0; k < ADJ_ITEM_VALS; ++k) ia[k] = ff{0.0f, 0.0f};
     const float4 q = A.P.reach[r];
     if (reach_overlap(q, A.band_bounds[b])) {
         load_record(A.P.recs, r, rec, lane);
         const int pj0 = b * A.rows_per_band, pj1 = min(A.npy, pj0 + A.rows_per_band);
-        const int np = (pj1 - pj0) * A.npx;
+        const int nrow = (pj1 - pj0 + PPL - 1) / PPL;  // patch rows of this band, PPL bound rows each
+        const int np = nrow * A.npx;
+        const float dl = (float)A.P.delta_L;
         for (int base = 0; base < np; base += 32) {
             const int idx = base + lane;
-            const bool cand = idx < np && reach_overlap(q, A.patch_bounds[(size_t)pj0 * A.npx + idx]);
+            bool cand = false;
+            if (idx < np) {
+                const int pj = pj0 + PPL * (idx / A.npx), pi = idx % A.npx;
+                float4 bb = A.patch_bounds[(size_t)pj * A.npx + pi];
+                if (PPL == 2 && pj + 1 < A.npy) {
+                    const float4 b2 = A.patch_bounds[(size_t)(pj + 1) * A.npx + pi];
+                    bb = make_float4(fminf(bb.x, b2.x), fmaxf(bb.y, b2.y), fminf(bb.z, b2.z), fmaxf(bb.w, b2.w));
+                }
+                cand = reach_overlap(q, bb);
+            }
             unsigned mask = __ballot_sync(FDX_FULL_MASK, cand);
             while (mask) {
                 const int bit = __ffs(mask) - 1;
                 mask &= mask - 1;
-                const int pidx = pj0 * A.npx + base + bit;
-                const int px0 = 8 * (pidx % A.npx), py0 = 4 * (pidx / A.npx);
-                const PatchPix<1> g = load_patch<1>(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
-                float c = 0.0f;
-                if (g.valid[0]) {
-                    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
-                    const double R = (double)g.Rh[0] + (double)g.Rl[0];
-                    c = (float)((double)A.gI[(size_t)py * A.P.nx + px] * A.P.delta_L / (R + A.P.delta_L));
+                const int k = base + bit;
+                const int px0 = 8 * (k % A.npx), py0 = 4 * (pj0 + PPL * (k / A.npx));
+                const PatchPix<PPL> g = load_patch<PPL>(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
+                float c[PPL];
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) {
+                    c[p] = 0.0f;
+                    if (g.valid[p]) {
+                        const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
+                        c[p] = A.gI[(size_t)py * A.P.nx + px] * (dl / ((g.Rh[p] + g.Rl[p]) + dl));
+                    }
+                    any |= c[p] != 0.0f;
                 }
-                if (__ballot_sync(FDX_FULL_MASK, c != 0.0f) == 0) continue;
-                PairAcc pa[1];
-                clear(pa[0]);
-                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, 1>(A.P, g, rec, buf, dn, sc, sc2, lane, pa))
+                if (__ballot_sync(FDX_FULL_MASK, any) == 0) continue;
+                PairAcc pa[PPL];
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) clear(pa[p]);
+                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, PPL>(A.P, g, rec, buf, dn, sc, sc2, lane,
+                                                                                    pa))
                     continue;
-                const double cd = (double)c;
-                const PairAcc &a = pa[0];
-                acc[0] += warp_sum_d(cd * ((double)a.s0.hi + (double)a.s0.lo));
-                acc[1] += warp_sum_d(cd * ((double)a.sb[0].hi + (double)a.sb[0].lo));
-                acc[2] += warp_sum_d(cd * ((double)a.sb[1].hi + (double)a.sb[1].lo));
-                acc[3] += warp_sum_d(cd * ((double)a.sb[2].hi + (double)a.sb[2].lo));
-                acc[4] += warp_sum_d(cd * ((double)a.ss.hi + (double)a.ss.lo));
-                acc[5] += warp_sum_d(cd * ((double)a.sg.hi + (double)a.sg.lo));
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) {
+                    const PairAcc &a = pa[p];
+                    ia[0] = ff_add(ia[0], ff_mul_f(a.s0, c[p]));
+                    ia[1] = ff_add(ia[1], ff_mul_f(a.sb[0], c[p]));
+                    ia[2] = ff_add(ia[2], ff_mul_f(a.sb[1], c[p]));
+                    ia[3] = ff_add(ia[3], ff_mul_f(a.sb[2], c[p]));
+                    ia[4] = ff_add(ia[4], ff_mul_f(a.ss, c[p]));
+                    ia[5] = ff_add(ia[5], ff_mul_f(a.sg, c[p]));
+                }
             }
         }
     }
+    double acc[ADJ_ITEM_VALS];
+#pragma unroll
+    for (int k = 0; k < ADJ_ITEM_VALS; ++k) acc[k] = warp_sum_d((double)ia[k].hi + (double)ia[k].lo);
     if (lane < ADJ_ITEM_VALS) {
         double o = acc[0];
 #pragma unroll
@@ -129,17 +159,18 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
 
 #define FDX_ADJ_SMEM                                        \
     __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];    \
-    __shared__ float2 s_dn[PAIR_WARPS][ADJ_NODE_BUF];       \
+    __shared__ float4 s_dn[PAIR_WARPS][ADJ_NODE_BUF / 2];   \
     __shared__ float4 s_sc[PAIR_WARPS][ADJ_NODE_BUF];       \
-    __shared__ float2 s_sc2[PAIR_WARPS][ADJ_NODE_BUF];      \
+    __shared__ float4 s_sc2[PAIR_WARPS][ADJ_NODE_BUF / 2];  \
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
 
+template <int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
     FDX_ADJ_SMEM
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
     if (item >= (long long)A.P.n_refl * A.n_bands) return;
-    adjoint_item(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    adjoint_item<PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
 }
 
 __device__ __forceinline__ int batch_model(const long long *prefix, int n_models, long long item) {
@@ -163,8 +194,13 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(Batch
         const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
         if (item >= B.total_items) break;
         const int m = batch_model(B.item_prefix, B.n_models, item);
-        adjoint_item(B.models[m], item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
-                     s_rec[warp], lane);
+        const AdjParams &A = B.models[m];
+        if (A.P.ppl == 2)
+            adjoint_item<2>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
+                            s_rec[warp], lane);
+        else
+            adjoint_item<1>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
+                            s_rec[warp], lane);
     }
 }
 
@@ -385,7 +421,11 @@ cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
     band_bounds_kernel<<<A.n_bands, 256, 0, s>>>(A);
     if (A.P.n_refl > 0) {
         const long long items = (long long)A.P.n_refl * A.n_bands;
-        adjoint_kernel<<<(unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS), PAIR_WARPS * 32, 0, s>>>(A);
+        const unsigned grid = (unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS);
+        if (A.P.ppl == 2)
+            adjoint_kernel<2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+        else
+            adjoint_kernel<1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
         adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
     }
     adjoint_globals_kernel<<<1, 256, 0, s>>>(A);

@@ -212,6 +212,7 @@ BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
     const int want_bands = tuning().adj_bands;
     B.n_bands = B.npy < want_bands ? B.npy : want_bands;
     B.rows_per_band = (B.npy + B.n_bands - 1) / B.n_bands;
+    B.rows_per_band += B.rows_per_band & 1;  // even: 8 x 8 adjoint patches (two bound rows) never straddle bands
     B.n_bands = (B.npy + B.rows_per_band - 1) / B.rows_per_band;
     const int atom_blocks = (n_atoms + 127) / 128;
     int split = (600 + atom_blocks - 1) / atom_blocks;

@@ -13,6 +13,11 @@
 //   3. every lane walks the buffer: t_i = tau_i - sigma_i with
 //      tau_i = a_i . (p - p_ref), support test, lineshape product, weight.
 // Partial sums of 32 nodes are folded into float-float accumulators.
+//
+// For the Hosemann lineshape the node walk runs on packed FP32 pairs
+// (__fadd2_rn/__fmul2_rn/__ffma2_rn: one instruction, two lanes of work):
+// the staged nodes are stored pairwise (even node, odd node) and every
+// arithmetic step of the walk handles two nodes of one pixel at once.
 #pragma once
 
 #include "fdx_internal.cuh"
@@ -92,6 +97,8 @@ __device__ __forceinline__ void sincospi_f(float x, float &s, float &c) {
     c = (qi & 2) ? -c1 : c1;
 }
 
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
 // A warp's pixels: PPL pixels per lane at (px0 + lane % 8, py0 + lane / 8 + 4 p),
 // p < PPL, so the warp covers an 8 x 4 PPL patch.  The reference pixel is the
 // patch's central pixel (column 4, row 2 PPL) when it lies on the detector,
@@ -145,10 +152,16 @@ __device__ __forceinline__ void clear(PairAcc &a) {
 }
 
 // Evaluate the pair for all PPL pixels of every lane; `rec` is the reflection
-// record in shared memory; `buf` (sigma_a, sigma_b, sigma_c, w), `buf2`
-// (adjoint: dw/dsigma, dw/dgamma) and, for the Hosemann lineshape,
-// `bsc`/`bsc2` (cos, sin of pi sigma_i) are the warp's node buffers of NB
-// entries.  Returns false when no node can be in any pixel's support.
+// record in shared memory.  Node buffers of the warp (NB nodes each): `buf`
+// (sigma_a, sigma_b, sigma_c, w), `buf2` (adjoint: dw/dsigma, dw/dgamma, as
+// float2 per node), and for the Hosemann lineshape `bsc` (NB float4) and
+// `bsc2` (NB/2 float4) for the scaled cos, sin of pi sigma_i.  Before the
+// Hosemann walk the buffers are rearranged in place into node pairs u:
+//   buf[2u]  = (-sigma_a, -sigma_a', -sigma_b, -sigma_b'),  buf[2u+1] = (-sigma_c, -sigma_c', w, w'),
+//   bsc[2u]  = (C_a, C_a', S_a, S_a'),  bsc[2u+1] = (C_b, C_b', S_b, S_b'),  bsc2[u] = (C_c, C_c', S_c, S_c'),
+//   buf2[u]  = (dw_s, dw_s', dw_g, dw_g')   (primes: the odd node of the pair),
+// with C_i = sqrt(1 - beta_i^2) cos(pi sigma_i), S_i likewise with sin.  Returns
+// false when no node can be in any pixel's support.
 //
 // Hosemann denominators by angle addition: with t = tau - sigma,
 //   sin(pi t) = sin(pi tau) cos(pi sigma) - cos(pi tau) sin(pi sigma),
@@ -158,8 +171,9 @@ __device__ __forceinline__ void clear(PairAcc &a) {
 // the two products.
 template <int LS, int MODE, int NB, int PPL>
 __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix<PPL> &g, const float *rec,
-                                          float4 *buf, float2 *buf2, float4 *bsc, float2 *bsc2, int lane,
+                                          float4 *buf, float4 *buf2, float4 *bsc, float4 *bsc2, int lane,
                                           PairAcc (&acc)[PPL]) {
+    constexpr bool PACKED = (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT);
     const int n = P.n_nodes;
     // node rows/columns that can be in each pixel's support: gnomonic
     // projection of the support box's corners around (p - D)/r0 (FP32, bounds only)
@@ -265,79 +279,152 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     int nlive = 0;
 
     // Walk the compacted nodes (warp-uniform bounds) and empty the buffer.
-    auto flush = [&]() {
+    auto flush_scalar = [&]() {
         __syncwarp();
-        if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
-            for (int q = lane; q < nlive; q += 32) {
-                const float4 nq = buf[q];
-                float sa, ca, sb, cb, sc, cc;
-                sincospi_f(nq.x, sa, ca);
-                sincospi_f(nq.y, sb, cb);
-                sincospi_f(nq.z, sc, cc);
-                // scaled by sqrt(1 - beta_i^2): den_i = beta_i^2 + (scaled sin(pi t_i))^2
-                bsc[q] = make_float4(slb[0] * ca, slb[0] * sa, slb[1] * cb, slb[1] * sb);
-                bsc2[q] = make_float2(slb[2] * cc, slb[2] * sc);
-            }
-            __syncwarp();
-        }
         for (int q0 = 0; q0 < nlive; q0 += 32) {
             const int qe = min(q0 + 32, nlive);
-            float r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
+            float r0[PPL];
 #pragma unroll
-            for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = 0.0f;
+            for (int p = 0; p < PPL; ++p) r0[p] = 0.0f;
 #pragma unroll 2
             for (int q = q0; q < qe; ++q) {
                 const float4 nq = buf[q];
-                float4 sc4;
-                float2 sc2, dw;
-                if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) sc4 = bsc[q], sc2 = bsc2[q];
-                if (MODE == MODE_ADJ) dw = buf2[q];
 #pragma unroll
                 for (int p = 0; p < PPL; ++p) {
                     const float ta = tau[p][0] - nq.x, tb = tau[p][1] - nq.y, tcc = tau[p][2] - nq.z;
                     const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tcc) <= tm[2]);
                     if (MODE == MODE_CNT) {
                         acc[p].cnt += in ? 1 : 0;
-                    } else if (LS == FDX_LINESHAPE_HOSEMANN) {
-                        const float sa = fmaf(st[p][0], sc4.x, -ct[p][0] * sc4.y);
-                        const float sb = fmaf(st[p][1], sc4.z, -ct[p][1] * sc4.w);
-                        const float sc = fmaf(st[p][2], sc2.x, -ct[p][2] * sc2.y);
-                        const float da = fmaf(sa, sa, la[0]);
-                        const float db = fmaf(sb, sb, la[1]);
-                        const float dc = fmaf(sc, sc, la[2]);
-                        const float dab = da * db;
-                        const float rp = rcp_approx(dab * dc);
-                        const float kv = nq.w * rp;
-                        r0[p] += in ? kv : 0.0f;
-                        if (MODE == MODE_ADJ) {
-                            const float dbc = db * dc, dac = da * dc;
-                            // 1/den_i = (product of the other two) * rp
-                            rb0[p] += in ? kv * fmaf(dbc, rp, -1.0f) : 0.0f;
-                            rb1[p] += in ? kv * fmaf(dac, rp, -1.0f) : 0.0f;
-                            rb2[p] += in ? kv * fmaf(dab, rp, -1.0f) : 0.0f;
-                            rss[p] += in ? dw.x * rp : 0.0f;
-                            rsg[p] += in ? dw.y * rp : 0.0f;
-                        }
                     } else {
                         const float kv = nq.w * sinc_term(ta, tb, tcc, la);
                         r0[p] += in ? kv : 0.0f;
                     }
                 }
             }
+            if (MODE != MODE_CNT) {
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) acc[p].s0 = ff_add_f(acc[p].s0, r0[p]);
+            }
+        }
+        nlive = 0;
+        __syncwarp();
+    };
+
+    // Hosemann walk on node pairs.  Per pixel and pair: t = tau - sigma (support
+    // test), scaled sin(pi t) = sin(pi tau) C - cos(pi tau) S, den_i = beta_i^2 +
+    // (scaled sin)^2, 1/prod den by one SFU reciprocal; a node outside the
+    // pixel's support gets the reciprocal of +inf, i.e. weight 0.
+    float2 tau2[PPL][3], st2[PPL][3], ctn2[PPL][3], la2[3];
+    if (PACKED) {
+#pragma unroll
+        for (int p = 0; p < PPL; ++p)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) tau2[p][i] = f2(tau[p][i]), st2[p][i] = f2(st[p][i]), ctn2[p][i] = f2(-ct[p][i]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) la2[i] = f2(la[i]);
+    }
+    auto flush_packed = [&]() {
+        __syncwarp();
+        const int npair = (nlive + 1) >> 1;
+        float *bf = reinterpret_cast<float *>(buf);
+        float *bs = reinterpret_cast<float *>(bsc);
+        float *be = reinterpret_cast<float *>(bsc2);
+        float *bd = reinterpret_cast<float *>(buf2);
+        // rearrange into pairs, 32 nodes (16 pairs) at a time; a pair never
+        // straddles two such groups, so reading the group before writing it is enough
+        for (int q0 = 0; q0 < 2 * npair; q0 += 32) {
+            const int q = q0 + lane;
+            // padding node (odd count): far outside every support, weight 0
+            float4 nq = make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f);
+            float2 dw = make_float2(0.0f, 0.0f);
+            if (q < nlive) {
+                nq = buf[q];
+                if (MODE == MODE_ADJ) dw = reinterpret_cast<const float2 *>(buf2)[q];
+            }
+            __syncwarp();
+            if (q < 2 * npair) {
+                float sa, ca, sb, cb, sc, cc;
+                sincospi_f(nq.x, sa, ca);
+                sincospi_f(nq.y, sb, cb);
+                sincospi_f(nq.z, sc, cc);
+                const int u = q >> 1, o = q & 1;
+                bf[8 * u + o] = -nq.x, bf[8 * u + 2 + o] = -nq.y, bf[8 * u + 4 + o] = -nq.z, bf[8 * u + 6 + o] = nq.w;
+                bs[8 * u + o] = slb[0] * ca, bs[8 * u + 2 + o] = slb[0] * sa;
+                bs[8 * u + 4 + o] = slb[1] * cb, bs[8 * u + 6 + o] = slb[1] * sb;
+                be[4 * u + o] = slb[2] * cc, be[4 * u + 2 + o] = slb[2] * sc;
+                if (MODE == MODE_ADJ) bd[4 * u + o] = dw.x, bd[4 * u + 2 + o] = dw.y;
+            }
+            __syncwarp();
+        }
+        const float inf = __int_as_float(0x7f800000);
+        const float2 m1 = f2(-1.0f);
+        for (int u0 = 0; u0 < npair; u0 += 16) {
+            const int ue = min(u0 + 16, npair);
+            float2 r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = f2(0.0f);
+#pragma unroll 2
+            for (int u = u0; u < ue; ++u) {
+                const float4 A4 = buf[2 * u], B4 = buf[2 * u + 1];
+                const float4 C4 = bsc[2 * u], D4 = bsc[2 * u + 1], E4 = bsc2[u];
+                float4 W4;
+                if (MODE == MODE_ADJ) W4 = buf2[u];
+                const float2 nsa = make_float2(A4.x, A4.y), nsb = make_float2(A4.z, A4.w);
+                const float2 nsc = make_float2(B4.x, B4.y), w = make_float2(B4.z, B4.w);
+                const float2 Ca = make_float2(C4.x, C4.y), Sa = make_float2(C4.z, C4.w);
+                const float2 Cb = make_float2(D4.x, D4.y), Sb = make_float2(D4.z, D4.w);
+                const float2 Cc = make_float2(E4.x, E4.y), Sc = make_float2(E4.z, E4.w);
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) {
+                    const float2 ta = __fadd2_rn(tau2[p][0], nsa);
+                    const float2 tb = __fadd2_rn(tau2[p][1], nsb);
+                    const float2 tc2 = __fadd2_rn(tau2[p][2], nsc);
+                    const bool in0 = (fabsf(ta.x) <= tm[0]) & (fabsf(tb.x) <= tm[1]) & (fabsf(tc2.x) <= tm[2]);
+                    const bool in1 = (fabsf(ta.y) <= tm[0]) & (fabsf(tb.y) <= tm[1]) & (fabsf(tc2.y) <= tm[2]);
+                    const float2 xa = __ffma2_rn(st2[p][0], Ca, __fmul2_rn(ctn2[p][0], Sa));
+                    const float2 xb = __ffma2_rn(st2[p][1], Cb, __fmul2_rn(ctn2[p][1], Sb));
+                    const float2 xc = __ffma2_rn(st2[p][2], Cc, __fmul2_rn(ctn2[p][2], Sc));
+                    const float2 da = __ffma2_rn(xa, xa, la2[0]);
+                    const float2 db = __ffma2_rn(xb, xb, la2[1]);
+                    const float2 dc = __ffma2_rn(xc, xc, la2[2]);
+                    const float2 dab = __fmul2_rn(da, db);
+                    const float2 d = __fmul2_rn(dab, dc);
+                    const float2 rp = make_float2(rcp_approx(in0 ? d.x : inf), rcp_approx(in1 ? d.y : inf));
+                    if (MODE == MODE_FWD) {
+                        r0[p] = __ffma2_rn(w, rp, r0[p]);
+                    } else {
+                        const float2 kv = __fmul2_rn(w, rp);
+                        r0[p] = __fadd2_rn(r0[p], kv);
+                        // 1/den_i = (product of the other two) * rp
+                        const float2 dbc = __fmul2_rn(db, dc), dac = __fmul2_rn(da, dc);
+                        rb0[p] = __ffma2_rn(kv, __ffma2_rn(dbc, rp, m1), rb0[p]);
+                        rb1[p] = __ffma2_rn(kv, __ffma2_rn(dac, rp, m1), rb1[p]);
+                        rb2[p] = __ffma2_rn(kv, __ffma2_rn(dab, rp, m1), rb2[p]);
+                        rss[p] = __ffma2_rn(make_float2(W4.x, W4.y), rp, rss[p]);
+                        rsg[p] = __ffma2_rn(make_float2(W4.z, W4.w), rp, rsg[p]);
+                    }
+                }
+            }
 #pragma unroll
             for (int p = 0; p < PPL; ++p) {
-                if (MODE != MODE_CNT) acc[p].s0 = ff_add_f(acc[p].s0, r0[p]);
+                acc[p].s0 = ff_add_f(acc[p].s0, r0[p].x + r0[p].y);
                 if (MODE == MODE_ADJ) {
-                    acc[p].sb[0] = ff_add_f(acc[p].sb[0], rb0[p]);
-                    acc[p].sb[1] = ff_add_f(acc[p].sb[1], rb1[p]);
-                    acc[p].sb[2] = ff_add_f(acc[p].sb[2], rb2[p]);
-                    acc[p].ss = ff_add_f(acc[p].ss, rss[p]);
-                    acc[p].sg = ff_add_f(acc[p].sg, rsg[p]);
+                    acc[p].sb[0] = ff_add_f(acc[p].sb[0], rb0[p].x + rb0[p].y);
+                    acc[p].sb[1] = ff_add_f(acc[p].sb[1], rb1[p].x + rb1[p].y);
+                    acc[p].sb[2] = ff_add_f(acc[p].sb[2], rb2[p].x + rb2[p].y);
+                    acc[p].ss = ff_add_f(acc[p].ss, rss[p].x + rss[p].y);
+                    acc[p].sg = ff_add_f(acc[p].sg, rsg[p].x + rsg[p].y);
                 }
             }
         }
         nlive = 0;
         __syncwarp();
+    };
+    auto flush = [&]() {
+        if constexpr (PACKED)
+            flush_packed();
+        else
+            flush_scalar();
     };
 
     for (int blk0 = 0; blk0 < nblk; blk0 += 32) {
@@ -389,7 +476,7 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
             if (live) {
                 const int pos = nlive + __popc(bal & lt_mask);
                 buf[pos] = val;
-                if (MODE == MODE_ADJ) buf2[pos] = val2;
+                if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = val2;
             }
             nlive += __popc(bal);
             if (nlive > NB - 32) flush();

@@ -13,7 +13,7 @@
 
 namespace fdx {
 
-static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp; 4 warps x 288 x 40 B keeps static shared memory < 48 KB
+static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp (even); 4 warps x 288 x 40 B keeps static shared memory < 48 KB
 // Pixels per lane (PPL): 2 (a warp owns 8 x 8 pixels, a CTA 16 x 16) when
 // the patch spans a small fraction of a lattice period, else 1 (8 x 4, 16 x 8);
 // chosen on the host from the pixel pitch and the cell.
@@ -22,7 +22,7 @@ static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp; 4 warps x 28
 // reflections, evaluate the surviving pairs, write the pixels.
 template <int LS, int MODE, int PPL>
 __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, int py0, float4 *buf, float4 *bsc,
-                                             float2 *bsc2, float *rec, int lane) {
+                                             float4 *bsc2, float *rec, int lane) {
     const PatchPix<PPL> g = load_patch<PPL>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
 
     float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
@@ -82,7 +82,7 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
 #define FDX_PATTERN_SMEM(LS, MODE)                                                                  \
     __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];                                            \
     __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1]; \
-    __shared__ float2 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1]; \
+    __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF / 2 : 1]; \
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
 
 template <int LS, int MODE, int PPL>
