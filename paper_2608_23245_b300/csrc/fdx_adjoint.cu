@@ -164,13 +164,21 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
     __shared__ float4 s_sc2[PAIR_WARPS][ADJ_NODE_BUF / 2];  \
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
 
+// Single-model adjoint, persistent: each warp takes (reflection, band) items
+// from the model's queue until none is left, so warps whose items end early
+// (no overlap with the band) pick up more work instead of idling in their CTA.
 template <int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
     FDX_ADJ_SMEM
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
-    if (item >= (long long)A.P.n_refl * A.n_bands) return;
-    adjoint_item<PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    const long long total = (long long)A.P.n_refl * A.n_bands;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(A.counter, 1u);
+        const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
+        if (item >= total) break;
+        adjoint_item<PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    }
 }
 
 __device__ __forceinline__ int batch_model(const long long *prefix, int n_models, long long item) {
@@ -415,13 +423,15 @@ __global__ void loss_final_kernel(LossParams p, int nblocks) {
 }
 
 // ---------------------------------------------------------------------------
-cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s) {
+cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s) {
     const int n_patch = A.npx * A.npy;
     patch_bounds_kernel<<<(n_patch * 32 + 127) / 128, 128, 0, s>>>(A);
     band_bounds_kernel<<<A.n_bands, 256, 0, s>>>(A);
     if (A.P.n_refl > 0) {
         const long long items = (long long)A.P.n_refl * A.n_bands;
-        const unsigned grid = (unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS);
+        long long want = (items + PAIR_WARPS - 1) / PAIR_WARPS;
+        const unsigned grid = (unsigned)(want < n_ctas ? want : n_ctas);
+        if (cudaMemsetAsync(A.counter, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
         if (A.P.ppl == 2)
             adjoint_kernel<2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
         else

@@ -16,6 +16,7 @@ struct AdjParams {
     float4 *cF;                // [n_refl] (dL/dM P DW conj(F), s^2)
     float *fe;                 // [n_refl][n_elem] form factors at the reflection
     float *dM;                 // [n_refl] dL/dM (may be null)
+    unsigned *counter;         // item queue of the single-model adjoint launch (zeroed by launch_adjoint)
     double *dglobal;           // [8] (may be null)
     const int32_t *hkl;
     const float *F;            // [n_refl][2]
@@ -72,7 +73,7 @@ struct Plain64Params {
     double *dfrac, *dB;
 };
 
-cudaError_t launch_adjoint(AdjParams &A, cudaStream_t s);
+cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s);
 cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s);
 cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s);
 cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s);

@@ -201,7 +201,7 @@ int run_pattern(const fdx_problem *p, float *image, int32_t *counts, char *ws, c
 
 // Backward workspace: the forward layout followed by the adjoint buffers.
 struct BackLayout {
-    size_t fwd, patch_bounds, band_bounds, item_out, refl_out, cF, fe, atoms_q, atoms_w, sf_partial, total;
+    size_t fwd, patch_bounds, band_bounds, item_out, refl_out, cF, fe, atoms_q, atoms_w, sf_partial, counter, total;
     int npx, npy, n_bands, rows_per_band, sf_split, refl_per_split;
 };
 
@@ -244,6 +244,8 @@ BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
     off += align_up(sizeof(float2) * (size_t)n_atoms);
     B.sf_partial = off;
     off += align_up(sizeof(double) * 4 * (size_t)split * (size_t)n_atoms);
+    B.counter = off;
+    off += align_up(sizeof(unsigned));
     B.total = off;
     return B;
 }
@@ -678,7 +680,11 @@ int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const 
     A.ff = atoms->ff;
     A.n_elem = atoms->n_elem;
     A.intensity_model = prob->br.intensity_model;
-    if (launch_adjoint(A, st) != cudaSuccess) return FDX_ERR_CUDA;
+    A.counter = reinterpret_cast<unsigned *>(ws + B.counter);
+    int dev = 0, n_sm = 148;
+    if (cudaGetDevice(&dev) != cudaSuccess) return FDX_ERR_CUDA;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (launch_adjoint(A, n_sm * tuning().adj_ctas_per_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
 
     if (grads->dfrac || grads->dB) {
         SFParams sp;

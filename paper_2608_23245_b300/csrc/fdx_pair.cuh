@@ -20,6 +20,8 @@
 // arithmetic step of the walk handles two nodes of one pixel at once.
 #pragma once
 
+#include <type_traits>
+
 #include "fdx_internal.cuh"
 
 namespace fdx {
@@ -99,6 +101,19 @@ __device__ __forceinline__ void sincospi_f(float x, float &s, float &c) {
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// v if |a| <= ta and |b| <= tb and |c| <= tc, else o (one predicate chain).
+__device__ __forceinline__ float support_sel(float a, float b, float c, float ta, float tb, float tc, float v, float o) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.le.f32 p, %1, %4;\n\t"
+        "setp.le.and.f32 p, %2, %5, p;\n\t"
+        "setp.le.and.f32 p, %3, %6, p;\n\t"
+        "selp.f32 %0, %7, %8, p;\n\t}"
+        : "=f"(r)
+        : "f"(fabsf(a)), "f"(fabsf(b)), "f"(fabsf(c)), "f"(ta), "f"(tb), "f"(tc), "f"(v), "f"(o));
+    return r;
+}
+
 // A warp's pixels: PPL pixels per lane at (px0 + lane % 8, py0 + lane / 8 + 4 p),
 // p < PPL, so the warp covers an 8 x 4 PPL patch.  The reference pixel is the
 // patch's central pixel (column 4, row 2 PPL) when it lies on the detector,
@@ -160,8 +175,12 @@ __device__ __forceinline__ void clear(PairAcc &a) {
 //   buf[2u]  = (-sigma_a, -sigma_a', -sigma_b, -sigma_b'),  buf[2u+1] = (-sigma_c, -sigma_c', w, w'),
 //   bsc[2u]  = (C_a, C_a', S_a, S_a'),  bsc[2u+1] = (C_b, C_b', S_b, S_b'),  bsc2[u] = (C_c, C_c', S_c, S_c'),
 //   buf2[u]  = (dw_s, dw_s', dw_g, dw_g')   (primes: the odd node of the pair),
-// with C_i = sqrt(1 - beta_i^2) cos(pi sigma_i), S_i likewise with sin.  Returns
-// false when no node can be in any pixel's support.
+// with C_i = sqrt(1 - beta_i^2) cos(pi sigma_i), S_i likewise with sin.
+// In the Hosemann forward, nodes are staged in two lists: "core" nodes (slots
+// [0, NB/2)) lie inside the support of every valid pixel of the warp, by a
+// margin far above FP32 rounding, so their walk needs no support test; the
+// others ("rim", slots [NB/2, NB)) are tested per pixel.  Returns false when no node can be
+// in any pixel's support.
 //
 // Hosemann denominators by angle addition: with t = tau - sigma,
 //   sin(pi t) = sin(pi tau) cos(pi sigma) - cos(pi tau) sin(pi sigma),
@@ -276,13 +295,25 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     for (int i = 0; i < 3; ++i) bw[i] = th[i] + rec[REC_AR0 + i] * rho_b + 1e-4f;
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bj_lane = lane / BC, bm_lane = lane % BC;  // this lane's node inside a block
-    int nlive = 0;
+    // staged counts: nr = rim nodes (all nodes when not PACKED), nc = core nodes
+    int nr = 0, nc = 0;
+    constexpr int NBH = NB / 2;                  // slots per list (PACKED)
+    // core/rim split in the forward only (the adjoint's longer per-chunk fold
+    // makes the extra list cost more than the tests it saves)
+    constexpr bool SPLIT = PACKED && MODE == MODE_FWD;
+    constexpr int RIM0 = SPLIT ? NBH : 0;        // first rim slot
+    constexpr int RIM_CAP = SPLIT ? NBH : NB;
+    static_assert(NB % 4 == 0, "node buffer must hold an even number of pairs per list");
+    // core half-widths: |sigma_i - tc_i| <= ch_i puts the node inside every valid pixel's support
+    float ch[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) ch[i] = tm[i] - (th[i] - tm[i]) - 4e-5f;
 
     // Walk the compacted nodes (warp-uniform bounds) and empty the buffer.
     auto flush_scalar = [&]() {
         __syncwarp();
-        for (int q0 = 0; q0 < nlive; q0 += 32) {
-            const int qe = min(q0 + 32, nlive);
+        for (int q0 = 0; q0 < nr; q0 += 32) {
+            const int qe = min(q0 + 32, nr);
             float r0[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) r0[p] = 0.0f;
@@ -306,7 +337,7 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                 for (int p = 0; p < PPL; ++p) acc[p].s0 = ff_add_f(acc[p].s0, r0[p]);
             }
         }
-        nlive = 0;
+        nr = 0;
         __syncwarp();
     };
 
@@ -323,31 +354,33 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
 #pragma unroll
         for (int i = 0; i < 3; ++i) la2[i] = f2(la[i]);
     }
-    auto flush_packed = [&]() {
-        __syncwarp();
-        const int npair = (nlive + 1) >> 1;
+    const float inf = __int_as_float(0x7f800000);
+    const float2 neg1 = f2(-1.0f);
+    // rearrange n staged nodes at slots [base, base + n) into pairs, 32 nodes
+    // (16 pairs) at a time; a pair never straddles two such groups, so reading
+    // the group before writing it is enough.  Padding node (odd n): weight 0,
+    // and for the rim list far outside every support.
+    auto pack = [&](int base, int n, bool rim) {
         float *bf = reinterpret_cast<float *>(buf);
         float *bs = reinterpret_cast<float *>(bsc);
         float *be = reinterpret_cast<float *>(bsc2);
         float *bd = reinterpret_cast<float *>(buf2);
-        // rearrange into pairs, 32 nodes (16 pairs) at a time; a pair never
-        // straddles two such groups, so reading the group before writing it is enough
-        for (int q0 = 0; q0 < 2 * npair; q0 += 32) {
+        const int npad = (n + 1) & ~1;
+        for (int q0 = 0; q0 < npad; q0 += 32) {
             const int q = q0 + lane;
-            // padding node (odd count): far outside every support, weight 0
-            float4 nq = make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f);
+            float4 nq = rim ? make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float2 dw = make_float2(0.0f, 0.0f);
-            if (q < nlive) {
-                nq = buf[q];
-                if (MODE == MODE_ADJ) dw = reinterpret_cast<const float2 *>(buf2)[q];
+            if (q < n) {
+                nq = buf[base + q];
+                if (MODE == MODE_ADJ) dw = reinterpret_cast<const float2 *>(buf2)[base + q];
             }
             __syncwarp();
-            if (q < 2 * npair) {
+            if (q < npad) {
                 float sa, ca, sb, cb, sc, cc;
                 sincospi_f(nq.x, sa, ca);
                 sincospi_f(nq.y, sb, cb);
                 sincospi_f(nq.z, sc, cc);
-                const int u = q >> 1, o = q & 1;
+                const int u = (base >> 1) + (q >> 1), o = q & 1;
                 bf[8 * u + o] = -nq.x, bf[8 * u + 2 + o] = -nq.y, bf[8 * u + 4 + o] = -nq.z, bf[8 * u + 6 + o] = nq.w;
                 bs[8 * u + o] = slb[0] * ca, bs[8 * u + 2 + o] = slb[0] * sa;
                 bs[8 * u + 4 + o] = slb[1] * cb, bs[8 * u + 6 + o] = slb[1] * sb;
@@ -356,15 +389,17 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
             }
             __syncwarp();
         }
-        const float inf = __int_as_float(0x7f800000);
-        const float2 m1 = f2(-1.0f);
+    };
+    // walk npair pairs from pair slot ub; TEST: per-pixel support test (rim list)
+    auto walk = [&](int ub, int npair, auto test_tag) {
+        constexpr bool TEST = decltype(test_tag)::value;
         for (int u0 = 0; u0 < npair; u0 += 16) {
-            const int ue = min(u0 + 16, npair);
+            const int ue = ub + min(u0 + 16, npair);
             float2 r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = f2(0.0f);
 #pragma unroll 2
-            for (int u = u0; u < ue; ++u) {
+            for (int u = ub + u0; u < ue; ++u) {
                 const float4 A4 = buf[2 * u], B4 = buf[2 * u + 1];
                 const float4 C4 = bsc[2 * u], D4 = bsc[2 * u + 1], E4 = bsc2[u];
                 float4 W4;
@@ -376,11 +411,6 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                 const float2 Cc = make_float2(E4.x, E4.y), Sc = make_float2(E4.z, E4.w);
 #pragma unroll
                 for (int p = 0; p < PPL; ++p) {
-                    const float2 ta = __fadd2_rn(tau2[p][0], nsa);
-                    const float2 tb = __fadd2_rn(tau2[p][1], nsb);
-                    const float2 tc2 = __fadd2_rn(tau2[p][2], nsc);
-                    const bool in0 = (fabsf(ta.x) <= tm[0]) & (fabsf(tb.x) <= tm[1]) & (fabsf(tc2.x) <= tm[2]);
-                    const bool in1 = (fabsf(ta.y) <= tm[0]) & (fabsf(tb.y) <= tm[1]) & (fabsf(tc2.y) <= tm[2]);
                     const float2 xa = __ffma2_rn(st2[p][0], Ca, __fmul2_rn(ctn2[p][0], Sa));
                     const float2 xb = __ffma2_rn(st2[p][1], Cb, __fmul2_rn(ctn2[p][1], Sb));
                     const float2 xc = __ffma2_rn(st2[p][2], Cc, __fmul2_rn(ctn2[p][2], Sc));
@@ -389,7 +419,16 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                     const float2 dc = __ffma2_rn(xc, xc, la2[2]);
                     const float2 dab = __fmul2_rn(da, db);
                     const float2 d = __fmul2_rn(dab, dc);
-                    const float2 rp = make_float2(rcp_approx(in0 ? d.x : inf), rcp_approx(in1 ? d.y : inf));
+                    float2 rp;
+                    if constexpr (TEST) {
+                        const float2 ta = __fadd2_rn(tau2[p][0], nsa);
+                        const float2 tb = __fadd2_rn(tau2[p][1], nsb);
+                        const float2 tc2 = __fadd2_rn(tau2[p][2], nsc);
+                        rp = make_float2(rcp_approx(support_sel(ta.x, tb.x, tc2.x, tm[0], tm[1], tm[2], d.x, inf)),
+                                         rcp_approx(support_sel(ta.y, tb.y, tc2.y, tm[0], tm[1], tm[2], d.y, inf)));
+                    } else {
+                        rp = make_float2(rcp_approx(d.x), rcp_approx(d.y));
+                    }
                     if (MODE == MODE_FWD) {
                         r0[p] = __ffma2_rn(w, rp, r0[p]);
                     } else {
@@ -397,9 +436,9 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                         r0[p] = __fadd2_rn(r0[p], kv);
                         // 1/den_i = (product of the other two) * rp
                         const float2 dbc = __fmul2_rn(db, dc), dac = __fmul2_rn(da, dc);
-                        rb0[p] = __ffma2_rn(kv, __ffma2_rn(dbc, rp, m1), rb0[p]);
-                        rb1[p] = __ffma2_rn(kv, __ffma2_rn(dac, rp, m1), rb1[p]);
-                        rb2[p] = __ffma2_rn(kv, __ffma2_rn(dab, rp, m1), rb2[p]);
+                        rb0[p] = __ffma2_rn(kv, __ffma2_rn(dbc, rp, neg1), rb0[p]);
+                        rb1[p] = __ffma2_rn(kv, __ffma2_rn(dac, rp, neg1), rb1[p]);
+                        rb2[p] = __ffma2_rn(kv, __ffma2_rn(dab, rp, neg1), rb2[p]);
                         rss[p] = __ffma2_rn(make_float2(W4.x, W4.y), rp, rss[p]);
                         rsg[p] = __ffma2_rn(make_float2(W4.z, W4.w), rp, rsg[p]);
                     }
@@ -417,7 +456,16 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                 }
             }
         }
-        nlive = 0;
+    };
+    auto flush_packed = [&]() {
+        __syncwarp();
+        if (SPLIT) {
+            pack(0, nc, false);
+            walk(0, (nc + 1) >> 1, std::integral_constant<bool, false>{});
+        }
+        pack(RIM0, nr, true);
+        walk(RIM0 / 2, (nr + 1) >> 1, std::integral_constant<bool, true>{});
+        nc = nr = 0;
         __syncwarp();
     };
     auto flush = [&]() {
@@ -472,17 +520,23 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                 val = make_float4(sg[0], sg[1], sg[2], nb.z);
                 if (MODE == MODE_ADJ) val2 = P.dnodes[k];
             }
-            const unsigned bal = __ballot_sync(FDX_FULL_MASK, live);
+            bool core = false;
+            if (SPLIT)
+                core = live & (fabsf(val.x - tc[0]) <= ch[0]) & (fabsf(val.y - tc[1]) <= ch[1]) &
+                       (fabsf(val.z - tc[2]) <= ch[2]);
+            const unsigned bal = __ballot_sync(FDX_FULL_MASK, live & !core);
+            const unsigned balc = SPLIT ? __ballot_sync(FDX_FULL_MASK, core) : 0u;
             if (live) {
-                const int pos = nlive + __popc(bal & lt_mask);
+                const int pos = core ? nc + __popc(balc & lt_mask) : RIM0 + nr + __popc(bal & lt_mask);
                 buf[pos] = val;
                 if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = val2;
             }
-            nlive += __popc(bal);
-            if (nlive > NB - 32) flush();
+            nr += __popc(bal);
+            nc += __popc(balc);
+            if (nr > RIM_CAP - 32 || nc > NBH - 32) flush();
         }
     }
-    if (nlive > 0) flush();
+    if (nr > 0 || nc > 0) flush();
     return true;
 }
 
