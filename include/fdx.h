@@ -281,11 +281,11 @@ typedef struct fdx_tuning {
     int32_t ppl_max;         /* 1 or 2: pixels per lane of the pattern kernels (2 is used only where the
                                 8 x 8 patch spans <= 0.5 lattice periods, which keeps FP32 t accurate) */
     int32_t fwd_ctas_per_sm; /* persistent forward CTAs per SM in fdx_batch_refine, 1..8 */
-    int32_t adj_ctas_per_sm; /* persistent adjoint CTAs per SM in fdx_batch_refine, 1..8 */
-    int32_t adj_bands;       /* detector bands per reflection in the adjoint work items, 1..64 */
+    int32_t adj_ctas_per_sm; /* persistent adjoint CTAs per SM in fdx_batch_refine and fdx_pattern_backward, 1..8 */
+    int32_t adj_bands;       /* detector bands per reflection in the adjoint work items, 1..256 */
 } fdx_tuning;
 
-/* Set the tuning (NULL restores the defaults 2, 4, 3, 16).  Workspace sizes
+/* Set the tuning (NULL restores the defaults 2, 4, 3, 64).  Workspace sizes
  * depend on adj_bands: query them after setting. */
 int fdx_set_tuning(const fdx_tuning *t);
 int fdx_get_tuning(fdx_tuning *t);

@@ -21,7 +21,7 @@ DEFAULT_GRID = {
     "ppl_max": (2, 1),
     "fwd_ctas_per_sm": (4, 3),
     "adj_ctas_per_sm": (3, 2),
-    "adj_bands": (16, 8, 32),
+    "adj_bands": (64, 32, 128),
 }
 
 
