@@ -43,6 +43,10 @@ WORKLOAD = "helix_2000atoms_hex20x20x28_dmin2.0_voigt3-2deg_g2pct_nodes64_det102
 # polynomial in t^2 (3 x 14); Hosemann denominators (3 x 2); their product (2);
 # reciprocal (1); weight (1); accumulation (1).
 FLOPS_PER_EVAL = 55
+# Structure factors, per atom-reflection term: exact integer phase (not
+# counted); remainder to float (5); r^2 (1); sin and cos polynomials (14);
+# sin = r * poly (1); amplitude exponent (2) and exp2 (1); form factor (1);
+# two accumulating FMAs (4); quadrant rotation is selects.  29 -> 30.
 SF_FLOPS_PER_TERM = 30
 
 
@@ -200,6 +204,63 @@ def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
             "fp32_over_plain_fp64_roi": roi64 / roi32}
 
 
+def large_measurements(g=0.01, reps=2, roi=128):
+    """Large forward (config-2 recipe: 20,000 atoms, 217,252 reflections,
+    128^2 nodes, 2048^2 detector): the structure-factor kernel at full size
+    (atom x reflection terms/s and its FP32 roofline fraction), the FP32
+    forward pattern at full size (evals/s), and the FP32 forward against the
+    plain FP64 GPU form on a central roi x roi detector (same pixel size)."""
+    import torch
+    from dataclasses import replace
+    from paper_2608_23245_b300 import fdx, workloads as W
+    p = W.config2(g)
+    sim = fdx.Simulation(p)
+    n_refl, n_atoms = int(sim.hkl.shape[0]), p.atoms.n
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / k
+
+    t_sf = timed(sim.structure_factors, 3)
+    terms = n_refl * n_atoms
+    peaks = _peaks()
+    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    sf_tflops = SF_FLOPS_PER_TERM * terms / t_sf / 1e12
+    sim.forward()
+    E = int(sim.evals().to(torch.int64).sum().item())
+    t_fwd = timed(sim.pattern, reps)
+    pr = replace(p, geom=replace(p.geom, n_x=roi, n_y=roi))
+    rs = fdx.Simulation(pr)
+    rs.forward()
+    E_roi = int(rs.evals().to(torch.int64).sum().item())
+    t_roi32 = timed(rs.pattern, reps)
+    img = torch.empty((roi, roi), dtype=torch.float64, device="cuda")
+    ws = torch.empty(fdx.fdx_plain64_workspace_size(rs.prob, n_atoms, rs.atoms.ff.shape[0]), dtype=torch.uint8,
+                     device="cuda")
+    t_roi64 = timed(lambda: fdx.fdx_plain64_refine(rs.prob, rs.atoms, img, None, None, None, None, None, None, ws), 1)
+    rel = float((rs.image.to(torch.float64) - img).abs().max() / img.abs().max())
+    return {"workload": "config-2 recipe: 20,000 atoms, 50x50x70 A, d >= 1.5 A, Lorentzian 4 deg, L = 300 A, "
+                        "g = %g, 128^2 nodes, 2048^2 detector (0.075 mm, 200 mm)" % g,
+            "n_refl": n_refl, "n_atoms": n_atoms,
+            "sf_terms_per_s": terms / t_sf, "sf_ms": 1e3 * t_sf,
+            "sf_roofline": {"bound": "alu", "achieved": sf_tflops, "peak": peak, "unit": "TFLOP/s",
+                            "frac": sf_tflops / peak,
+                            "basis": "%d algorithmic FP32 flops per atom-reflection term (exp2 counted as one)"
+                                     % SF_FLOPS_PER_TERM},
+            "pattern_evals": E, "pattern_ms": 1e3 * t_fwd, "pattern_evals_per_s": E / t_fwd,
+            "pattern_frac_of_fp32_peak": FLOPS_PER_EVAL * E / t_fwd / 1e12 / peak,
+            "roi": "central %dx%d pixels" % (roi, roi), "roi_evals": E_roi,
+            "fp32_roi_forward_ms": 1e3 * t_roi32, "plain_fp64_roi_forward_ms": 1e3 * t_roi64,
+            "fp32_over_plain_fp64_roi": t_roi64 / t_roi32, "roi_max_rel_diff_fp32_vs_fp64": rel}
+
+
 def batch_measurements(n_models=256, tune_models=8):
     """Batched refinement (config-4 recipe): n_models seeded candidate models of
     uneven size, each against its own perturbed target.  One step = structure
@@ -334,6 +395,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--batch-models", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -438,6 +500,8 @@ def main():
     }
     if not args.no_refine:
         line["refine"] = refine_measurements()
+    if not args.no_large:
+        line["large"] = large_measurements()
     if not args.no_batch:
         line["batch"] = batch_measurements(args.batch_models)
     if not args.no_cpu_baseline:

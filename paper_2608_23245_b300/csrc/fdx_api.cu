@@ -345,15 +345,9 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
             cell_basis(pr.cell, Am, As);
             memcpy(sp.As, As, sizeof As);
             sp.n_atoms = a->n_atoms, sp.n_elem = a->n_elem, sp.n_refl = pr.n_refl;
-            const int refl_blocks = (pr.n_refl + 127) / 128;
-            int n_split = (600 + refl_blocks - 1) / refl_blocks;
-            n_split = n_split < 1 ? 1 : (n_split > 64 ? 64 : n_split);
-            const int by_atoms = (a->n_atoms + 511) / 512;
-            if (n_split > by_atoms) n_split = by_atoms;
-            if (n_split < 1) n_split = 1;
-            int per = (a->n_atoms + n_split - 1) / n_split;
-            per = (per + 255) / 256 * 256;
-            sp.n_split = (a->n_atoms + per - 1) / per, sp.atoms_per_split = per;
+            int n_split = 1, per = 1;
+            sf_plan(a->n_atoms, pr.n_refl, 64, n_split, per);
+            sp.n_split = n_split, sp.atoms_per_split = per;
             sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
             char *sw = ws + L.sf[m];
             size_t o2 = 0;
@@ -570,16 +564,8 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
     cell_basis(*cell, A, As);
     memcpy(p.As, As, sizeof As);
     p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
-    // Split the atom list so that the grid has >= ~4 CTAs per SM, keeping >= 512 atoms per split.
-    const int refl_blocks = (n_refl + 127) / 128;
-    int n_split = (600 + refl_blocks - 1) / refl_blocks;
-    n_split = n_split < 1 ? 1 : (n_split > 64 ? 64 : n_split);
-    const int max_by_atoms = (atoms->n_atoms + 511) / 512;
-    if (n_split > max_by_atoms) n_split = max_by_atoms;
-    if (n_split < 1) n_split = 1;
-    int per = (atoms->n_atoms + n_split - 1) / n_split;
-    per = (per + 255) / 256 * 256;
-    n_split = (atoms->n_atoms + per - 1) / per;
+    int n_split = 1, per = 1;
+    sf_plan(atoms->n_atoms, n_refl, 64, n_split, per);
     p.n_split = n_split, p.atoms_per_split = per;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
     char *ws = static_cast<char *>(workspace);

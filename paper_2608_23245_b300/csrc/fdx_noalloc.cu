@@ -90,15 +90,8 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     if (atoms_bytes + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
     int max_split = (int)((kScratchBytes - atoms_bytes) / per_split);
     if (max_split > 64) max_split = 64;
-    const int refl_blocks = (n_refl + 127) / 128;
-    int n_split = (600 + refl_blocks - 1) / refl_blocks;
-    const int by_atoms = (atoms->n_atoms + 511) / 512;
-    if (n_split > by_atoms) n_split = by_atoms;
-    if (n_split > max_split) n_split = max_split;
-    if (n_split < 1) n_split = 1;
-    int per = (atoms->n_atoms + n_split - 1) / n_split;
-    per = (per + 255) / 256 * 256;
-    n_split = (atoms->n_atoms + per - 1) / per;
+    int n_split = 1, per = 1;
+    sf_plan(atoms->n_atoms, n_refl, max_split, n_split, per);
     if (atoms_bytes + align_up(per_split * (size_t)n_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
 
     void *base = nullptr;

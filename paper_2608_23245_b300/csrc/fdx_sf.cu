@@ -19,8 +19,7 @@
 namespace fdx {
 
 static constexpr int SF_THREADS = 128;
-static constexpr int SF_TILE = 256;  // atoms per shared-memory tile (multiple of 8)
-static constexpr int SF_MAX_ELEM = 64;
+static constexpr int SF_TILE = 256;  // atoms per shared-memory tile (multiple of 16)
 
 // Pack atoms: fixed-point coordinates, element, and the exponent terms
 // Bq = -B log2(e) / 4 (so that exp(-B s^2/4) = exp2(Bq s^2)) and log2(occ).
@@ -42,83 +41,141 @@ __global__ void sf_pack_atoms_kernel(SFParams p) {
     p.atoms_w[j] = make_float2((float)(-(double)p.B[j] * 1.4426950408889634 / 4.0), lo);
 }
 
-__device__ __forceinline__ void sincos_turns(unsigned u, float &s, float &c) {
-    // quadrant and remainder in [-2^29, 2^29)
-    const unsigned qd = (u + 0x20000000u) >> 30;
-    const int rem = (int)(u - (qd << 30));
-    // exact int -> float of the 30-bit remainder via two 'magic number' conversions
-    const int rh = rem >> 8, rl = rem & 255;
-    const float fh = __int_as_float(0x4B400000 + rh) - 12582912.0f;
-    const float fl = __int_as_float(0x4B000000 + rl) - 8388608.0f;
-    const float r = fmaf(fh, 5.9604644775390625e-08f /* 2^-24 */, fl * 2.3283064365386963e-10f /* 2^-32 */);
-    const float Sc[4] = FDX_SIN2PI_C;
-    const float Cc[5] = FDX_COS2PI_C;
-    const float r2 = r * r;
-    const float sn = r * horner(Sc, r2);
-    const float cs = horner(Cc, r2);
-    // rotate by qd quarter turns
-    const float s1 = (qd & 1) ? cs : sn;
-    const float c1 = (qd & 1) ? -sn : cs;
-    s = (qd & 2) ? -s1 : s1;
-    c = (qd & 2) ? -c1 : c1;
+// ex2.approx with flush-to-zero: one SFU op (amplitudes below 2^-126 are 0).
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
 }
+
+// Exact float of the half-turn remainder of v = phase + 2^30 (uint32 turns):
+// rem = (v & 0x7fffffff) - 2^30 in [-2^30, 2^30), split as 2^8 hi + lo and
+// converted by 'magic number' ORs (hi < 2^23, lo < 2^8), returned as
+// (float bits of 2^23 + hi, float bits of 2^23 + lo); the caller subtracts
+// 2^23 + 2^22 and 2^23 and scales by 2^-24 and 2^-32.
+__device__ __forceinline__ float2 rem_parts(unsigned v) {
+    return make_float2(__uint_as_float(((v >> 8) & 0x7fffffu) | 0x4b000000u), __uint_as_float((v & 0xffu) | 0x4b000000u));
+}
+
+// Phase -> (sin, cos) for two reflections at once, on the half turn:
+// v = h . X + 2^30 (wrapping); bit 31 of v is the half turn (it flips the
+// sign of both sin and cos, applied to the amplitude by the caller) and the
+// remainder r = rem 2^-32 in [-1/4, 1/4) turn feeds the half-turn polynomials.
+__device__ __forceinline__ void sincos_half2(unsigned v0, unsigned v1, float2 &sn, float2 &cs) {
+    const float2 a = rem_parts(v0), b = rem_parts(v1);
+    const float2 fh = __fadd2_rn(make_float2(a.x, b.x), make_float2(-12582912.0f, -12582912.0f));
+    const float2 fl = __fadd2_rn(make_float2(a.y, b.y), make_float2(-8388608.0f, -8388608.0f));
+    const float2 r = __ffma2_rn(fh, make_float2(5.9604644775390625e-08f, 5.9604644775390625e-08f),
+                                __fmul2_rn(fl, make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f)));
+    const float2 r2 = __fmul2_rn(r, r);
+    const float Sc[5] = FDX_SIN2PI_H_C;
+    const float Cc[6] = FDX_COS2PI_H_C;
+    float2 S = make_float2(Sc[4], Sc[4]);
+#pragma unroll
+    for (int k = 3; k >= 0; --k) S = __ffma2_rn(S, r2, make_float2(Sc[k], Sc[k]));
+    float2 C = make_float2(Cc[5], Cc[5]);
+#pragma unroll
+    for (int k = 4; k >= 0; --k) C = __ffma2_rn(C, r2, make_float2(Cc[k], Cc[k]));
+    sn = __fmul2_rn(r, S);
+    cs = C;
+}
+
+// One thread per SF_RPT = 4 consecutive reflections (two packed pairs), atoms
+// staged through shared memory; per atom and reflection: exact phase (3 IMAD),
+// half-turn sin/cos, amplitude occ f_e(s) exp(-B s^2/4) = f_e(s) 2^(Bq s^2 +
+// log2 occ) with one SFU exp2, half-turn sign folded into the amplitude.
+// 16 atoms are summed in FP32, then folded into float-float.
+static constexpr int SF_RPT = 4;
+static constexpr int SF_FOLD = 16;  // atoms per FP32 partial sum (SF_TILE is a multiple)
 
 __global__ void __launch_bounds__(SF_THREADS) sf_main_kernel(SFParams p) {
     __shared__ uint4 s_q[SF_TILE];
-    __shared__ float2 s_w[SF_TILE];
-    __shared__ float s_fe[SF_MAX_ELEM][SF_THREADS];
+    __shared__ float4 s_w[SF_TILE];  // (Bq, Bq, log2 occ, log2 occ)
+    extern __shared__ float4 s_fe[];  // [n_elem][SF_THREADS]: f_e(s) of this thread's 4 reflections
 
-    const int r = blockIdx.x * SF_THREADS + threadIdx.x;
-    const bool active = r < p.n_refl;
-    int h = 0, k = 0, l = 0;
-    if (active) h = p.hkl[3 * r], k = p.hkl[3 * r + 1], l = p.hkl[3 * r + 2];
-    double D[3];
-    for (int q = 0; q < 3; ++q) D[q] = h * p.As[q] + k * p.As[3 + q] + l * p.As[6 + q];
-    const double s2d = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
-    const float s2 = (float)s2d;
+    const int r0 = (blockIdx.x * SF_THREADS + threadIdx.x) * SF_RPT;
+    unsigned h[SF_RPT], k[SF_RPT], l[SF_RPT];
+    float s2[SF_RPT];
+#pragma unroll
+    for (int j = 0; j < SF_RPT; ++j) {
+        const int r = r0 + j;
+        int hh = 0, kk = 0, ll = 0;
+        if (r < p.n_refl) hh = p.hkl[3 * r], kk = p.hkl[3 * r + 1], ll = p.hkl[3 * r + 2];
+        h[j] = (unsigned)hh, k[j] = (unsigned)kk, l[j] = (unsigned)ll;
+        double D[3];
+        for (int q = 0; q < 3; ++q) D[q] = hh * p.As[q] + kk * p.As[3 + q] + ll * p.As[6 + q];
+        s2[j] = (float)(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    }
     for (int e = 0; e < p.n_elem; ++e) {
         const float *f = p.ff + 9 * e;
-        double v = f[8];
-        for (int i = 0; i < 4; ++i) v += (double)f[i] * exp(-(double)f[4 + i] * s2d * 0.25);
-        s_fe[e][threadIdx.x] = (float)v;
+        float fe[SF_RPT];
+#pragma unroll
+        for (int j = 0; j < SF_RPT; ++j) {  // FP32 (expf, a few ulp): FP64 here would cost more than the sum
+            float v = f[8];
+            for (int i = 0; i < 4; ++i) v = fmaf(f[i], expf(-0.25f * f[4 + i] * s2[j]), v);
+            fe[j] = v;
+        }
+        s_fe[e * SF_THREADS + threadIdx.x] = make_float4(fe[0], fe[1], fe[2], fe[3]);
     }
-    const unsigned uh = (unsigned)h, uk = (unsigned)k, ul = (unsigned)l;
+    const float2 s2a = make_float2(s2[0], s2[1]), s2b = make_float2(s2[2], s2[3]);
 
     const int a_begin = blockIdx.y * p.atoms_per_split;
     const int a_end = min(p.n_atoms, a_begin + p.atoms_per_split);
-    ff re = {0.0f, 0.0f}, im = {0.0f, 0.0f};
+    ff re[SF_RPT], im[SF_RPT];
+#pragma unroll
+    for (int j = 0; j < SF_RPT; ++j) re[j] = im[j] = ff{0.0f, 0.0f};
     for (int t0 = a_begin; t0 < a_end; t0 += SF_TILE) {
         const int cnt = min(SF_TILE, a_end - t0);
         __syncthreads();
         for (int i = threadIdx.x; i < SF_TILE; i += SF_THREADS) {
             if (i < cnt) {
                 s_q[i] = p.atoms_q[t0 + i];
-                s_w[i] = p.atoms_w[t0 + i];
+                const float2 w = p.atoms_w[t0 + i];
+                s_w[i] = make_float4(w.x, w.x, w.y, w.y);
             } else {
                 s_q[i] = make_uint4(0u, 0u, 0u, 0u);
-                s_w[i] = make_float2(0.0f, -INFINITY);  // zero amplitude padding
+                s_w[i] = make_float4(0.0f, 0.0f, -INFINITY, -INFINITY);  // zero amplitude padding
             }
         }
         __syncthreads();
-        const int cnt8 = (cnt + 7) & ~7;
-        for (int i0 = 0; i0 < cnt8; i0 += 8) {
-            float bre = 0.0f, bim = 0.0f;
-#pragma unroll
-            for (int i = i0; i < i0 + 8; ++i) {
+        const int cntf = (cnt + SF_FOLD - 1) / SF_FOLD * SF_FOLD;
+        for (int i0 = 0; i0 < cntf; i0 += SF_FOLD) {
+            float2 ra = make_float2(0.0f, 0.0f), ia = ra, rb = ra, ib = ra;
+#pragma unroll 4
+            for (int i = i0; i < i0 + SF_FOLD; ++i) {
                 const uint4 q = s_q[i];
-                const float2 w = s_w[i];
-                const unsigned ph = uh * q.x + uk * q.y + ul * q.z;
-                float sn, cs;
-                sincos_turns(ph, sn, cs);
-                const float amp = s_fe[q.w][threadIdx.x] * exp2f(fmaf(w.x, s2, w.y));
-                bre = fmaf(amp, cs, bre);
-                bim = fmaf(amp, sn, bim);
+                const float4 w = s_w[i];
+                const float4 fe = s_fe[q.w * SF_THREADS + threadIdx.x];
+                unsigned v[SF_RPT];
+#pragma unroll
+                for (int j = 0; j < SF_RPT; ++j) v[j] = h[j] * q.x + k[j] * q.y + l[j] * q.z + 0x40000000u;
+                float2 sa, ca, sb, cb;
+                sincos_half2(v[0], v[1], sa, ca);
+                sincos_half2(v[2], v[3], sb, cb);
+                const float2 xa = __ffma2_rn(make_float2(w.x, w.y), s2a, make_float2(w.z, w.w));
+                const float2 xb = __ffma2_rn(make_float2(w.x, w.y), s2b, make_float2(w.z, w.w));
+                float2 aa = __fmul2_rn(make_float2(fe.x, fe.y), make_float2(ex2_ftz(xa.x), ex2_ftz(xa.y)));
+                float2 ab = __fmul2_rn(make_float2(fe.z, fe.w), make_float2(ex2_ftz(xb.x), ex2_ftz(xb.y)));
+                // half-turn sign of (sin, cos) onto the amplitude
+                aa.x = __uint_as_float(__float_as_uint(aa.x) ^ (v[0] & 0x80000000u));
+                aa.y = __uint_as_float(__float_as_uint(aa.y) ^ (v[1] & 0x80000000u));
+                ab.x = __uint_as_float(__float_as_uint(ab.x) ^ (v[2] & 0x80000000u));
+                ab.y = __uint_as_float(__float_as_uint(ab.y) ^ (v[3] & 0x80000000u));
+                ra = __ffma2_rn(aa, ca, ra);
+                ia = __ffma2_rn(aa, sa, ia);
+                rb = __ffma2_rn(ab, cb, rb);
+                ib = __ffma2_rn(ab, sb, ib);
             }
-            re = ff_add_f(re, bre);
-            im = ff_add_f(im, bim);
+            re[0] = ff_add_f(re[0], ra.x), re[1] = ff_add_f(re[1], ra.y);
+            re[2] = ff_add_f(re[2], rb.x), re[3] = ff_add_f(re[3], rb.y);
+            im[0] = ff_add_f(im[0], ia.x), im[1] = ff_add_f(im[1], ia.y);
+            im[2] = ff_add_f(im[2], ib.x), im[3] = ff_add_f(im[3], ib.y);
         }
     }
-    if (active) p.partial[(size_t)blockIdx.y * p.n_refl + r] = make_float4(re.hi, re.lo, im.hi, im.lo);
+#pragma unroll
+    for (int j = 0; j < SF_RPT; ++j)
+        if (r0 + j < p.n_refl)
+            p.partial[(size_t)blockIdx.y * p.n_refl + r0 + j] = make_float4(re[j].hi, re[j].lo, im[j].hi, im[j].lo);
 }
 
 // Sum the splits in order; F = (re, im); M = |F|^2 P DW (FP64 scalars).
@@ -148,6 +205,21 @@ __global__ void sf_reduce_kernel(SFParams p) {
     }
 }
 
+// Split of the atom list across blockIdx.y: enough CTAs for ~6 per SM on 148
+// SMs, at least 256 atoms per split (a multiple of the tile), at most
+// max_split splits.
+void sf_plan(int n_atoms, int n_refl, int max_split, int &n_split, int &per) {
+    const int refl_blocks = (n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT);
+    n_split = (888 + refl_blocks - 1) / refl_blocks;
+    const int by_atoms = (n_atoms + SF_TILE - 1) / SF_TILE;
+    if (n_split > by_atoms) n_split = by_atoms;
+    if (n_split > max_split) n_split = max_split;
+    if (n_split < 1) n_split = 1;
+    per = (n_atoms + n_split - 1) / n_split;
+    per = (per + SF_TILE - 1) / SF_TILE * SF_TILE;
+    n_split = (n_atoms + per - 1) / per;
+}
+
 cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
     sf_pack_atoms_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);
     return cudaGetLastError();
@@ -156,8 +228,17 @@ cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s) {
     if (p.n_refl <= 0) return cudaSuccess;
     sf_pack_atoms_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);
-    dim3 grid((p.n_refl + SF_THREADS - 1) / SF_THREADS, p.n_split);
-    sf_main_kernel<<<grid, SF_THREADS, 0, s>>>(p);
+    dim3 grid((p.n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT), p.n_split);
+    const size_t shm = sizeof(float4) * SF_THREADS * (size_t)p.n_elem;
+    if (shm > 48 * 1024) {
+        static size_t s_opted = 0;  // largest opt-in so far (the attribute is per function, process-wide)
+        if (shm > s_opted) {
+            if (cudaFuncSetAttribute(sf_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+                return cudaGetLastError();
+            s_opted = shm;
+        }
+    }
+    sf_main_kernel<<<grid, SF_THREADS, shm, s>>>(p);
     sf_reduce_kernel<<<(p.n_refl + 127) / 128, 128, 0, s>>>(p);
     return cudaGetLastError();
 }
