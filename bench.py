@@ -111,30 +111,18 @@ class ClockSampler:
 
 
 def dist_init(n_gpus):
-    import torch
-    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
-    if world > 1:
-        import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
-        dist.init_process_group(backend)
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    return rank, world
+    from paper_2608_23245_b300 import replicas
+    return replicas.dist_init()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2608_23245_b300 import replicas
+    replicas.barrier(world)
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2608_23245_b300 import replicas
+    return replicas.max_over_ranks(x, world, "cuda")
 
 
 def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):

@@ -346,7 +346,7 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
             memcpy(sp.As, As, sizeof As);
             sp.n_atoms = a->n_atoms, sp.n_elem = a->n_elem, sp.n_refl = pr.n_refl;
             int n_split = 1, per = 1;
-            sf_plan(a->n_atoms, pr.n_refl, 64, n_split, per);
+            sf_plan(a->n_atoms, pr.n_refl, a->n_elem, 64, n_split, per);
             sp.n_split = n_split, sp.atoms_per_split = per;
             sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
             char *sw = ws + L.sf[m];
@@ -565,7 +565,7 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
     memcpy(p.As, As, sizeof As);
     p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
     int n_split = 1, per = 1;
-    sf_plan(atoms->n_atoms, n_refl, 64, n_split, per);
+    sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, 64, n_split, per);
     p.n_split = n_split, p.atoms_per_split = per;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
     char *ws = static_cast<char *>(workspace);

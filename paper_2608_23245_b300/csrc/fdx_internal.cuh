@@ -210,6 +210,6 @@ struct SFParams {
 };
 
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);
-void sf_plan(int n_atoms, int n_refl, int max_split, int &n_split, int &per);
+void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);
 
 }  // namespace fdx

@@ -91,7 +91,7 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     int max_split = (int)((kScratchBytes - atoms_bytes) / per_split);
     if (max_split > 64) max_split = 64;
     int n_split = 1, per = 1;
-    sf_plan(atoms->n_atoms, n_refl, max_split, n_split, per);
+    sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, max_split, n_split, per);
     if (atoms_bytes + align_up(per_split * (size_t)n_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
 
     void *base = nullptr;

@@ -4,16 +4,18 @@
 // Phase reduction is exact: fractional coordinates are stored as 32-bit
 // fixed-point turns X = round(x 2^32) mod 2^32, so h X + k Y + l Z computed in
 // wrapping uint32 arithmetic is the phase modulo one turn with no rounding
-// beyond the 2^-32 quantisation of x.  The top two bits pick the quadrant;
-// the remainder (|r| <= 1/8 turn) is converted to float exactly and fed to
-// polynomials for sin(2 pi r), cos(2 pi r) fitted by fit_poly.py.
+// beyond the 2^-32 quantisation of x.  The phase is split into a half turn
+// (a sign on the amplitude) and a remainder |r| <= 1/4 turn, converted to
+// float once and fed to polynomials for sin(2 pi r), cos(2 pi r) fitted by
+// fit_poly.py.
 //
-// Work decomposition: one thread per reflection, atoms staged through shared
-// memory in tiles; the atom list is split across blockIdx.y so that small
-// reflection counts still fill the GPU.  Each split writes a float-float
-// partial (re, im) to the workspace; a second kernel adds the splits in a
-// fixed order (deterministic, no atomics) and forms M = |F|^2 P DW.
-// Sums: 8 terms in plain FP32, then folded into a float-float accumulator.
+// Work decomposition: one thread per 4 consecutive reflections, evaluated as
+// two packed FP32 pairs; atoms staged through shared memory in tiles; the
+// atom list is split across blockIdx.y (sf_plan: whole waves of resident
+// CTAs).  Each split writes a float-float partial (re, im) to the workspace; a
+// second kernel adds the splits in a fixed order (deterministic, no atomics)
+// and forms M = |F|^2 P DW.  Sums: 16 terms in plain FP32, then folded into a
+// float-float accumulator.
 #include "fdx_internal.cuh"
 
 namespace fdx {
@@ -48,25 +50,19 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-// Exact float of the half-turn remainder of v = phase + 2^30 (uint32 turns):
-// rem = (v & 0x7fffffff) - 2^30 in [-2^30, 2^30), split as 2^8 hi + lo and
-// converted by 'magic number' ORs (hi < 2^23, lo < 2^8), returned as
-// (float bits of 2^23 + hi, float bits of 2^23 + lo); the caller subtracts
-// 2^23 + 2^22 and 2^23 and scales by 2^-24 and 2^-32.
-__device__ __forceinline__ float2 rem_parts(unsigned v) {
-    return make_float2(__uint_as_float(((v >> 8) & 0x7fffffu) | 0x4b000000u), __uint_as_float((v & 0xffu) | 0x4b000000u));
-}
+// Phase -> (sin, cos) for two reflections at once, on the half turn.  With
+// the phase u (uint32 turns), rem = u sign-extended from its low 31 bits is
+// u mod 1/2 turn in [-2^30, 2^30), and bit 31 of u - rem is the half turn (it
+// flips the sign of both sin and cos; half_sign() returns it for the caller
+// to apply to the amplitude).  r = rem 2^-32 in [-1/4, 1/4) turn (one
+// rounding to 24 bits in the int -> float conversion: <= 2^-26 turn) feeds the
+// half-turn polynomials.
+__device__ __forceinline__ int half_rem(unsigned u) { return ((int)(u << 1)) >> 1; }
+__device__ __forceinline__ unsigned half_sign(unsigned u, int rem) { return (u - (unsigned)rem) & 0x80000000u; }
 
-// Phase -> (sin, cos) for two reflections at once, on the half turn:
-// v = h . X + 2^30 (wrapping); bit 31 of v is the half turn (it flips the
-// sign of both sin and cos, applied to the amplitude by the caller) and the
-// remainder r = rem 2^-32 in [-1/4, 1/4) turn feeds the half-turn polynomials.
-__device__ __forceinline__ void sincos_half2(unsigned v0, unsigned v1, float2 &sn, float2 &cs) {
-    const float2 a = rem_parts(v0), b = rem_parts(v1);
-    const float2 fh = __fadd2_rn(make_float2(a.x, b.x), make_float2(-12582912.0f, -12582912.0f));
-    const float2 fl = __fadd2_rn(make_float2(a.y, b.y), make_float2(-8388608.0f, -8388608.0f));
-    const float2 r = __ffma2_rn(fh, make_float2(5.9604644775390625e-08f, 5.9604644775390625e-08f),
-                                __fmul2_rn(fl, make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f)));
+__device__ __forceinline__ void sincos_half2(int rem0, int rem1, float2 &sn, float2 &cs) {
+    const float2 r = __fmul2_rn(make_float2(__int2float_rn(rem0), __int2float_rn(rem1)),
+                                make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f));
     const float2 r2 = __fmul2_rn(r, r);
     const float Sc[5] = FDX_SIN2PI_H_C;
     const float Cc[6] = FDX_COS2PI_H_C;
@@ -81,7 +77,8 @@ __device__ __forceinline__ void sincos_half2(unsigned v0, unsigned v1, float2 &s
 }
 
 // One thread per SF_RPT = 4 consecutive reflections (two packed pairs), atoms
-// staged through shared memory; per atom and reflection: exact phase (3 IMAD),
+// staged through shared memory; per atom and reflection: exact phase (3 IMAD
+// in wrapping uint32),
 // half-turn sin/cos, amplitude occ f_e(s) exp(-B s^2/4) = f_e(s) 2^(Bq s^2 +
 // log2 occ) with one SFU exp2, half-turn sign folded into the amplitude.
 // 16 atoms are summed in FP32, then folded into float-float.
@@ -146,21 +143,26 @@ __global__ void __launch_bounds__(SF_THREADS) sf_main_kernel(SFParams p) {
                 const uint4 q = s_q[i];
                 const float4 w = s_w[i];
                 const float4 fe = s_fe[q.w * SF_THREADS + threadIdx.x];
-                unsigned v[SF_RPT];
+                unsigned v[SF_RPT], sg[SF_RPT];
+                int rm[SF_RPT];
 #pragma unroll
-                for (int j = 0; j < SF_RPT; ++j) v[j] = h[j] * q.x + k[j] * q.y + l[j] * q.z + 0x40000000u;
+                for (int j = 0; j < SF_RPT; ++j) {
+                    v[j] = h[j] * q.x + k[j] * q.y + l[j] * q.z;
+                    rm[j] = half_rem(v[j]);
+                    sg[j] = half_sign(v[j], rm[j]);
+                }
                 float2 sa, ca, sb, cb;
-                sincos_half2(v[0], v[1], sa, ca);
-                sincos_half2(v[2], v[3], sb, cb);
+                sincos_half2(rm[0], rm[1], sa, ca);
+                sincos_half2(rm[2], rm[3], sb, cb);
                 const float2 xa = __ffma2_rn(make_float2(w.x, w.y), s2a, make_float2(w.z, w.w));
                 const float2 xb = __ffma2_rn(make_float2(w.x, w.y), s2b, make_float2(w.z, w.w));
                 float2 aa = __fmul2_rn(make_float2(fe.x, fe.y), make_float2(ex2_ftz(xa.x), ex2_ftz(xa.y)));
                 float2 ab = __fmul2_rn(make_float2(fe.z, fe.w), make_float2(ex2_ftz(xb.x), ex2_ftz(xb.y)));
                 // half-turn sign of (sin, cos) onto the amplitude
-                aa.x = __uint_as_float(__float_as_uint(aa.x) ^ (v[0] & 0x80000000u));
-                aa.y = __uint_as_float(__float_as_uint(aa.y) ^ (v[1] & 0x80000000u));
-                ab.x = __uint_as_float(__float_as_uint(ab.x) ^ (v[2] & 0x80000000u));
-                ab.y = __uint_as_float(__float_as_uint(ab.y) ^ (v[3] & 0x80000000u));
+                aa.x = __uint_as_float(__float_as_uint(aa.x) ^ sg[0]);
+                aa.y = __uint_as_float(__float_as_uint(aa.y) ^ sg[1]);
+                ab.x = __uint_as_float(__float_as_uint(ab.x) ^ sg[2]);
+                ab.y = __uint_as_float(__float_as_uint(ab.y) ^ sg[3]);
                 ra = __ffma2_rn(aa, ca, ra);
                 ia = __ffma2_rn(aa, sa, ia);
                 rb = __ffma2_rn(ab, cb, rb);
@@ -205,19 +207,46 @@ __global__ void sf_reduce_kernel(SFParams p) {
     }
 }
 
-// Split of the atom list across blockIdx.y: enough CTAs for ~6 per SM on 148
-// SMs, at least 256 atoms per split (a multiple of the tile), at most
-// max_split splits.
-void sf_plan(int n_atoms, int n_refl, int max_split, int &n_split, int &per) {
-    const int refl_blocks = (n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT);
-    n_split = (888 + refl_blocks - 1) / refl_blocks;
-    const int by_atoms = (n_atoms + SF_TILE - 1) / SF_TILE;
-    if (n_split > by_atoms) n_split = by_atoms;
-    if (n_split > max_split) n_split = max_split;
-    if (n_split < 1) n_split = 1;
-    per = (n_atoms + n_split - 1) / n_split;
-    per = (per + SF_TILE - 1) / SF_TILE * SF_TILE;
-    n_split = (n_atoms + per - 1) / per;
+// Split of the atom list across blockIdx.y.  A CTA's time is proportional to
+// its atoms (plus a fixed set-up of about SF_TILE / 4 atoms), and CTAs run in
+// waves of `slots` (resident CTAs on the whole GPU), so the split count n
+// minimises waves(n) x (atoms per split + set-up); splits hold a multiple of
+// SF_TILE atoms, and there are at most max_split of them.
+void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per) {
+    static int s_sm = 0;
+    if (s_sm == 0) {
+        int dev = 0, v = 148;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            s_sm = v;
+        else
+            s_sm = 148;
+    }
+    static size_t s_shm = (size_t)-1;
+    static int s_per_sm = 1;
+    const size_t shm = sizeof(float4) * SF_THREADS * (size_t)(n_elem > 0 ? n_elem : 1);
+    if (shm != s_shm) {
+        int v = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sf_main_kernel, SF_THREADS, shm) != cudaSuccess || v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        s_shm = shm, s_per_sm = v;
+    }
+    const int per_sm = s_per_sm;
+    const long long slots = (long long)s_sm * per_sm;
+    const long long refl_blocks = (n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT);
+    const int tiles = (n_atoms + SF_TILE - 1) / SF_TILE;
+    int best_n = 1, best_per = tiles * SF_TILE;
+    double best_t = -1.0;
+    for (int want = 1; want <= max_split && want <= tiles; ++want) {
+        const int pt = (tiles + want - 1) / want;  // tiles per split
+        const int n = (tiles + pt - 1) / pt;
+        const long long ctas = (long long)n * refl_blocks;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double t = (double)waves * (pt * SF_TILE + SF_TILE / 4);
+        if (best_t < 0.0 || t < 0.98 * best_t) best_t = t, best_n = n, best_per = pt * SF_TILE;
+    }
+    n_split = best_n, per = best_per;
 }
 
 cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
