@@ -158,9 +158,10 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
  *   - No workspace argument: the kernels' scratch is a fixed array of
  *     FDX_NOALLOC_SF_SCRATCH_BYTES (8 MiB) in device memory that every GPU
  *     loading libfdx holds until the process exits.  It must fit 24 bytes per
- *     atom plus 16 bytes per reflection (per atom split; the call uses as many
- *     splits as fit, at most 64); larger sizes return FDX_ERR_WORKSPACE before
- *     any work is queued.  The call allocates nothing.
+ *     atom, 4 bytes per reflection, and 16 bytes per reflection per row of
+ *     partial sums (the call uses as many rows as fit, at most 64); larger
+ *     sizes return FDX_ERR_WORKSPACE before any work is queued.  The call
+ *     allocates nothing.
  *   - The first call on a device looks up the array's address on that device
  *     and caches it; make that first call before any stream capture.
  *   - All calls share the array.  Calls whose work overlaps on the GPU race on

@@ -349,11 +349,7 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
             sf_plan(a->n_atoms, pr.n_refl, a->n_elem, 64, n_split, per);
             sp.n_split = n_split, sp.atoms_per_split = per;
             sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
-            char *sw = ws + L.sf[m];
-            size_t o2 = 0;
-            sp.atoms_q = reinterpret_cast<uint4 *>(sw + o2), o2 += align_up(sizeof(uint4) * (size_t)a->n_atoms);
-            sp.atoms_w = reinterpret_cast<float2 *>(sw + o2), o2 += align_up(sizeof(float2) * (size_t)a->n_atoms);
-            sp.partial = reinterpret_cast<float4 *>(sw + o2);
+            sf_bind(&sp, ws + L.sf[m], a->n_atoms, pr.n_refl, 64);
             sp.hkl = pr.hkl, sp.F_out = F[m], sp.M_out = M[m];
             sp.has_br = 1, sp.intensity_model = pr.br.intensity_model;
             for (int i = 0; i < 3; ++i) {
@@ -536,12 +532,7 @@ int fdx_reflections(const fdx_cell *cell, double d_min, double d_max, int32_t ca
 
 size_t fdx_sf_workspace_size(int32_t n_atoms, int32_t n_refl) {
     if (n_atoms < 1 || n_refl < 0) return 0;
-    size_t off = 0;
-    off += align_up(sizeof(uint4) * (size_t)n_atoms);
-    off += align_up(sizeof(float2) * (size_t)n_atoms);
-    // at most 64 splits of the atom list
-    off += align_up(sizeof(float4) * (size_t)64 * (size_t)(n_refl > 0 ? n_refl : 1));
-    return off;
+    return sf_bind(nullptr, nullptr, n_atoms, n_refl, 64);  // at most 64 rows of partials
 }
 
 int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fdx_broadening *br, int32_t n_refl,
@@ -568,13 +559,7 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
     sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, 64, n_split, per);
     p.n_split = n_split, p.atoms_per_split = per;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
-    char *ws = static_cast<char *>(workspace);
-    size_t off = 0;
-    p.atoms_q = reinterpret_cast<uint4 *>(ws + off);
-    off += align_up(sizeof(uint4) * (size_t)atoms->n_atoms);
-    p.atoms_w = reinterpret_cast<float2 *>(ws + off);
-    off += align_up(sizeof(float2) * (size_t)atoms->n_atoms);
-    p.partial = reinterpret_cast<float4 *>(ws + off);
+    sf_bind(&p, static_cast<char *>(workspace), atoms->n_atoms, n_refl, 64);
     p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;
     p.has_br = br ? 1 : 0;
     if (br) {

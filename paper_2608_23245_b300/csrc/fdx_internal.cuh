@@ -203,13 +203,18 @@ struct SFParams {
     uint4 *atoms_q;        // packed: X, Y, Z (fixed point), elem
     float2 *atoms_w;       // packed: Bq = -B log2(e)/4, log2(occ)
     const int32_t *hkl;
-    float4 *partial;       // [n_split][n_refl] (re hi, re lo, im hi, im lo)
+    int *groups;           // [<= n_refl] first reflection of each group (consecutive l, equal h, k)
+    int *gblk;             // [n_refl / 1024 + 1] per-block group offsets
+    int *n_groups;         // group count (device)
+    float4 *partial;       // [rows][n_refl] (re hi, re lo, im hi, im lo)
     float *F_out, *M_out;
     int has_br, intensity_model;
+    int e_lo, n_fe, split_base, n_rows;  // element pass and partial rows (set by the launcher)
     double g[3], Bax[3], alen[3];
 };
 
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);
+size_t sf_bind(SFParams *p, char *ws, int n_atoms, int n_refl, int max_split);
 
 }  // namespace fdx

@@ -82,17 +82,17 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     }
     if (n_refl == 0) return FDX_OK;
 
-    // Scratch: packed atoms (uint4 + float2 each) and one float4 partial per
-    // (atom split, reflection).  Use as many splits as fit, at most 64.
-    const size_t atoms_bytes = align_up(sizeof(uint4) * (size_t)atoms->n_atoms) +
-                               align_up(sizeof(float2) * (size_t)atoms->n_atoms);
+    // Scratch: packed atoms (uint4 + float2 each), the group list of the
+    // reflections (one int each) and one float4 partial per (partial row,
+    // reflection).  Use as many rows as fit, at most 64.
+    const size_t fixed = sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, 0);
     const size_t per_split = sizeof(float4) * (size_t)n_refl;
-    if (atoms_bytes + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
-    int max_split = (int)((kScratchBytes - atoms_bytes) / per_split);
+    if (fixed + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
+    int max_split = (int)((kScratchBytes - fixed) / per_split);
     if (max_split > 64) max_split = 64;
     int n_split = 1, per = 1;
     sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, max_split, n_split, per);
-    if (atoms_bytes + align_up(per_split * (size_t)n_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
+    if (sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, max_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
 
     void *base = nullptr;
     int rc = scratch_address(&base);
@@ -106,13 +106,7 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
     p.n_split = n_split, p.atoms_per_split = per;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
-    char *ws = static_cast<char *>(base);
-    size_t off = 0;
-    p.atoms_q = reinterpret_cast<uint4 *>(ws + off);
-    off += align_up(sizeof(uint4) * (size_t)atoms->n_atoms);
-    p.atoms_w = reinterpret_cast<float2 *>(ws + off);
-    off += align_up(sizeof(float2) * (size_t)atoms->n_atoms);
-    p.partial = reinterpret_cast<float4 *>(ws + off);
+    sf_bind(&p, static_cast<char *>(base), atoms->n_atoms, n_refl, max_split);
     p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;
     p.has_br = br ? 1 : 0;
     if (br) {

@@ -4,24 +4,41 @@
 // Phase reduction is exact: fractional coordinates are stored as 32-bit
 // fixed-point turns X = round(x 2^32) mod 2^32, so h X + k Y + l Z computed in
 // wrapping uint32 arithmetic is the phase modulo one turn with no rounding
-// beyond the 2^-32 quantisation of x.  The phase is split into a half turn
-// (a sign on the amplitude) and a remainder |r| <= 1/4 turn, converted to
-// float once and fed to polynomials for sin(2 pi r), cos(2 pi r) fitted by
-// fit_poly.py.
+// beyond the 2^-32 quantisation of x.  A phase is split into a half turn (a
+// sign) and a remainder |r| <= 1/4 turn, converted to float once and fed to
+// polynomials for sin(2 pi r), cos(2 pi r) fitted by fit_poly.py.
 //
-// Work decomposition: one thread per 4 consecutive reflections, evaluated as
-// two packed FP32 pairs; atoms staged through shared memory in tiles; the
-// atom list is split across blockIdx.y (sf_plan: whole waves of resident
-// CTAs).  Each split writes a float-float partial (re, im) to the workspace; a
-// second kernel adds the splits in a fixed order (deterministic, no atomics)
-// and forms M = |F|^2 P DW.  Sums: 16 terms in plain FP32, then folded into a
-// float-float accumulator.
+// Runs of l.  Reflections are processed in groups of up to four with equal
+// (h, k) and consecutive l (l = l0 .. l0 + 3), so that per atom
+//   exp(2 pi i (h.x + (l0 + j) z)) = exp(2 pi i (h.x + l0 z)) exp(2 pi i j z):
+// one exact phase and one polynomial sin/cos per group and atom, the other
+// three terms by a complex rotation with exp(2 pi i j z), j = 1, 2, 3, which
+// depends on the atom only and is tabulated (each from its own exact phase
+// j Z) when the atom tile is staged.  A group starts at every run start of
+// the reflection list and wherever l is a multiple of 4; three small kernels
+// (flags and counts, a scan, a scatter) list the group starts, so any
+// reflection order is valid and the lexicographic order of fdx_reflections
+// gives runs of tens of reflections.
+//
+// Work decomposition: one thread per two groups (8 reflections, evaluated as
+// packed FP32 pairs across the two groups); atoms staged through shared
+// memory in tiles; the atom list is cut into n_split splits; CTAs loop over
+// (256-group block, split) items.  Each item writes float-float partials
+// (re, im) per reflection; a second kernel adds the splits in a fixed order
+// (deterministic, no atomics) and forms M = |F|^2 P DW.  Sums: 16 atoms in
+// plain FP32, then folded into a float-float accumulator.
 #include "fdx_internal.cuh"
 
 namespace fdx {
 
 static constexpr int SF_THREADS = 128;
-static constexpr int SF_TILE = 256;  // atoms per shared-memory tile (multiple of 16)
+static constexpr int SF_TILE = 256;   // atoms per shared-memory tile (multiple of SF_FOLD)
+static constexpr int SF_FOLD = 16;    // atoms per FP32 partial sum
+static constexpr int SF_GROUP = 4;    // reflections per group (consecutive l)
+static constexpr int SF_GPT = 2;      // groups per thread
+static constexpr int SF_GPB = SF_THREADS * SF_GPT;  // groups per work item
+static constexpr int SF_SCAN = 1024;  // reflections per block of the grouping kernels
+static constexpr int SF_FE_MAX = 40;  // element types per pass (form-factor table in shared memory)
 
 // Pack atoms: fixed-point coordinates, element, and the exponent terms
 // Bq = -B log2(e) / 4 (so that exp(-B s^2/4) = exp2(Bq s^2)) and log2(occ).
@@ -50,18 +67,32 @@ __device__ __forceinline__ float ex2_ftz(float x) {
     return y;
 }
 
-// Phase -> (sin, cos) for two reflections at once, on the half turn.  With
-// the phase u (uint32 turns), rem = u sign-extended from its low 31 bits is
-// u mod 1/2 turn in [-2^30, 2^30), and bit 31 of u - rem is the half turn (it
-// flips the sign of both sin and cos; half_sign() returns it for the caller
-// to apply to the amplitude).  r = rem 2^-32 in [-1/4, 1/4) turn (one
-// rounding to 24 bits in the int -> float conversion: <= 2^-26 turn) feeds the
-// half-turn polynomials.
+// With a phase u (uint32 turns), rem = u sign-extended from its low 31 bits
+// is u mod 1/2 turn in [-2^30, 2^30), and bit 31 of u - rem is the half turn,
+// which flips the sign of both sin and cos.  r = rem 2^-32 in [-1/4, 1/4)
+// turn has one rounding to 24 bits in the int -> float conversion (<= 2^-26
+// turn).
 __device__ __forceinline__ int half_rem(unsigned u) { return ((int)(u << 1)) >> 1; }
 __device__ __forceinline__ unsigned half_sign(unsigned u, int rem) { return (u - (unsigned)rem) & 0x80000000u; }
+__device__ __forceinline__ float flip(float x, unsigned sign) { return __uint_as_float(__float_as_uint(x) ^ sign); }
 
-__device__ __forceinline__ void sincos_half2(int rem0, int rem1, float2 &sn, float2 &cs) {
-    const float2 r = __fmul2_rn(make_float2(__int2float_rn(rem0), __int2float_rn(rem1)),
+// (sin, cos)(2 pi u) for one phase (scalar), sign of the half turn included.
+__device__ __forceinline__ void sincos_turn(unsigned u, float &sn, float &cs) {
+    const int rem = half_rem(u);
+    const unsigned sg = half_sign(u, rem);
+    const float r = __int2float_rn(rem) * 2.3283064365386963e-10f;
+    const float r2 = r * r;
+    const float Sc[5] = FDX_SIN2PI_H_C;
+    const float Cc[6] = FDX_COS2PI_H_C;
+    sn = flip(r * horner(Sc, r2), sg);
+    cs = flip(horner(Cc, r2), sg);
+}
+
+// The same for two phases at once on packed pairs; the signs are returned
+// for the caller to apply.
+__device__ __forceinline__ void sincos_turn2(unsigned u0, unsigned u1, float2 &sn, float2 &cs) {
+    const int m0 = half_rem(u0), m1 = half_rem(u1);
+    const float2 r = __fmul2_rn(make_float2(__int2float_rn(m0), __int2float_rn(m1)),
                                 make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f));
     const float2 r2 = __fmul2_rn(r, r);
     const float Sc[5] = FDX_SIN2PI_H_C;
@@ -72,120 +103,240 @@ __device__ __forceinline__ void sincos_half2(int rem0, int rem1, float2 &sn, flo
     float2 C = make_float2(Cc[5], Cc[5]);
 #pragma unroll
     for (int k = 4; k >= 0; --k) C = __ffma2_rn(C, r2, make_float2(Cc[k], Cc[k]));
-    sn = __fmul2_rn(r, S);
-    cs = C;
+    S = __fmul2_rn(r, S);
+    const unsigned g0 = half_sign(u0, m0), g1 = half_sign(u1, m1);
+    sn = make_float2(flip(S.x, g0), flip(S.y, g1));
+    cs = make_float2(flip(C.x, g0), flip(C.y, g1));
 }
 
-// One thread per SF_RPT = 4 consecutive reflections (two packed pairs), atoms
-// staged through shared memory; per atom and reflection: exact phase (3 IMAD
-// in wrapping uint32),
-// half-turn sin/cos, amplitude occ f_e(s) exp(-B s^2/4) = f_e(s) 2^(Bq s^2 +
-// log2 occ) with one SFU exp2, half-turn sign folded into the amplitude.
-// 16 atoms are summed in FP32, then folded into float-float.
-static constexpr int SF_RPT = 4;
-static constexpr int SF_FOLD = 16;  // atoms per FP32 partial sum (SF_TILE is a multiple)
+// ---------------------------------------------------------------------------
+// Grouping: group starts at run starts (first reflection, or (h, k) differ
+// from the previous reflection, or l is not the previous l + 1) and where
+// l = 0 mod 4.  A group holds the following reflections up to the next start.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool group_start(const int32_t *hkl, int r) {
+    const int l = hkl[3 * r + 2];
+    if (r == 0 || (l & 3) == 0) return true;
+    return hkl[3 * r] != hkl[3 * r - 3] || hkl[3 * r + 1] != hkl[3 * r - 2] || l != hkl[3 * r - 1] + 1;
+}
 
+// Per block of SF_SCAN reflections: number of group starts.
+__global__ void __launch_bounds__(SF_SCAN) sf_group_count_kernel(SFParams p) {
+    const int r = blockIdx.x * SF_SCAN + threadIdx.x;
+    const int f = r < p.n_refl ? (int)group_start(p.hkl, r) : 0;
+    const int cnt = __syncthreads_count(f);
+    if (threadIdx.x == 0) p.gblk[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the block counts (one CTA); the total is the group count.
+__global__ void __launch_bounds__(SF_SCAN) sf_group_scan_kernel(SFParams p, int nblk) {
+    __shared__ int s_warp[SF_SCAN / 32];
+    __shared__ int s_carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += SF_SCAN) {
+        const int b = b0 + threadIdx.x;
+        const int v = b < nblk ? p.gblk[b] : 0;
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FDX_FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FDX_FULL_MASK, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int excl = s_carry + (warp > 0 ? s_warp[warp - 1] : 0) + x - v;
+        if (b < nblk) p.gblk[b] = excl;
+        __syncthreads();
+        if (threadIdx.x == SF_SCAN - 1) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *p.n_groups = s_carry;
+}
+
+// Scatter: groups[g] = first reflection of group g, in list order.
+__global__ void __launch_bounds__(SF_SCAN) sf_group_write_kernel(SFParams p) {
+    __shared__ int s_warp[SF_SCAN / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r = blockIdx.x * SF_SCAN + threadIdx.x;
+    const bool f = r < p.n_refl && group_start(p.hkl, r);
+    const unsigned bal = __ballot_sync(FDX_FULL_MASK, f);
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+        const int v = s_warp[lane];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FDX_FULL_MASK, x, o);
+            if (lane >= o) x += y;
+        }
+        s_warp[lane] = x - v;
+    }
+    __syncthreads();
+    if (f) p.groups[p.gblk[blockIdx.x] + s_warp[warp] + __popc(bal & ((1u << lane) - 1u))] = r;
+}
+
+// Group g: first reflection r0 and count c (1..4; a group never crosses a
+// multiple of 4 in l, so the next start is at most 4 entries later).
+__device__ __forceinline__ void group_span(const SFParams &p, int G, int g, int &r0, int &c) {
+    if (g >= G) {
+        r0 = 0, c = 0;
+        return;
+    }
+    r0 = p.groups[g];
+    c = (g + 1 < G ? p.groups[g + 1] : p.n_refl) - r0;
+}
+
+// One CTA per (block of SF_GPB groups, atom split) item, looping over items.
+// Thread t owns groups t and t + SF_THREADS of the block; every quantity of
+// slot j (reflection l0 + j) is a packed pair over the two groups.  Element
+// types e_lo .. e_lo + n_fe - 1 of this pass contribute (atoms of other
+// types have amplitude 0 in this pass).
 __global__ void __launch_bounds__(SF_THREADS) sf_main_kernel(SFParams p) {
     __shared__ uint4 s_q[SF_TILE];
-    __shared__ float4 s_w[SF_TILE];  // (Bq, Bq, log2 occ, log2 occ)
-    extern __shared__ float4 s_fe[];  // [n_elem][SF_THREADS]: f_e(s) of this thread's 4 reflections
-
-    const int r0 = (blockIdx.x * SF_THREADS + threadIdx.x) * SF_RPT;
-    unsigned h[SF_RPT], k[SF_RPT], l[SF_RPT];
-    float s2[SF_RPT];
+    __shared__ float4 s_w[SF_TILE];          // (Bq, Bq, log2 occ, log2 occ); log2 occ = -inf: not in this pass
+    __shared__ float4 s_rot[3][SF_TILE];     // j = 1..3: (cos, cos, sin, sin)(2 pi j z)
+    extern __shared__ float4 s_fe[];         // [n_fe][2][SF_THREADS]: f_e(s) pairs (slot 0, 1) and (slot 2, 3)
+    const int tid = threadIdx.x;
+    const int G = *p.n_groups;
+    const int n_gblk = (G + SF_GPB - 1) / SF_GPB;
+    const long long n_items = (long long)n_gblk * p.n_split;
+    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int gb = (int)(item % n_gblk), split = (int)(item / n_gblk);
+        int r0[SF_GPT], cnt[SF_GPT];
+        unsigned h[SF_GPT], k[SF_GPT], l[SF_GPT];
+        float s2[SF_GPT][SF_GROUP];
 #pragma unroll
-    for (int j = 0; j < SF_RPT; ++j) {
-        const int r = r0 + j;
-        int hh = 0, kk = 0, ll = 0;
-        if (r < p.n_refl) hh = p.hkl[3 * r], kk = p.hkl[3 * r + 1], ll = p.hkl[3 * r + 2];
-        h[j] = (unsigned)hh, k[j] = (unsigned)kk, l[j] = (unsigned)ll;
-        double D[3];
-        for (int q = 0; q < 3; ++q) D[q] = hh * p.As[q] + kk * p.As[3 + q] + ll * p.As[6 + q];
-        s2[j] = (float)(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
-    }
-    for (int e = 0; e < p.n_elem; ++e) {
-        const float *f = p.ff + 9 * e;
-        float fe[SF_RPT];
+        for (int t = 0; t < SF_GPT; ++t) {
+            group_span(p, G, gb * SF_GPB + t * SF_THREADS + tid, r0[t], cnt[t]);
+            int hh = 0, kk = 0, ll = 0;
+            if (cnt[t] > 0) hh = p.hkl[3 * r0[t]], kk = p.hkl[3 * r0[t] + 1], ll = p.hkl[3 * r0[t] + 2];
+            h[t] = (unsigned)hh, k[t] = (unsigned)kk, l[t] = (unsigned)ll;
 #pragma unroll
-        for (int j = 0; j < SF_RPT; ++j) {  // FP32 (expf, a few ulp): FP64 here would cost more than the sum
-            float v = f[8];
-            for (int i = 0; i < 4; ++i) v = fmaf(f[i], expf(-0.25f * f[4 + i] * s2[j]), v);
-            fe[j] = v;
-        }
-        s_fe[e * SF_THREADS + threadIdx.x] = make_float4(fe[0], fe[1], fe[2], fe[3]);
-    }
-    const float2 s2a = make_float2(s2[0], s2[1]), s2b = make_float2(s2[2], s2[3]);
-
-    const int a_begin = blockIdx.y * p.atoms_per_split;
-    const int a_end = min(p.n_atoms, a_begin + p.atoms_per_split);
-    ff re[SF_RPT], im[SF_RPT];
-#pragma unroll
-    for (int j = 0; j < SF_RPT; ++j) re[j] = im[j] = ff{0.0f, 0.0f};
-    for (int t0 = a_begin; t0 < a_end; t0 += SF_TILE) {
-        const int cnt = min(SF_TILE, a_end - t0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < SF_TILE; i += SF_THREADS) {
-            if (i < cnt) {
-                s_q[i] = p.atoms_q[t0 + i];
-                const float2 w = p.atoms_w[t0 + i];
-                s_w[i] = make_float4(w.x, w.x, w.y, w.y);
-            } else {
-                s_q[i] = make_uint4(0u, 0u, 0u, 0u);
-                s_w[i] = make_float4(0.0f, 0.0f, -INFINITY, -INFINITY);  // zero amplitude padding
+            for (int j = 0; j < SF_GROUP; ++j) {
+                const double lj = (double)(ll + j);
+                double D[3];
+                for (int q = 0; q < 3; ++q) D[q] = hh * p.As[q] + kk * p.As[3 + q] + lj * p.As[6 + q];
+                s2[t][j] = (float)(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
             }
         }
-        __syncthreads();
-        const int cntf = (cnt + SF_FOLD - 1) / SF_FOLD * SF_FOLD;
-        for (int i0 = 0; i0 < cntf; i0 += SF_FOLD) {
-            float2 ra = make_float2(0.0f, 0.0f), ia = ra, rb = ra, ib = ra;
-#pragma unroll 4
-            for (int i = i0; i < i0 + SF_FOLD; ++i) {
-                const uint4 q = s_q[i];
-                const float4 w = s_w[i];
-                const float4 fe = s_fe[q.w * SF_THREADS + threadIdx.x];
-                unsigned v[SF_RPT], sg[SF_RPT];
-                int rm[SF_RPT];
+        // form factors of this thread's 8 reflections (0 for empty slots)
+        for (int e = 0; e < p.n_fe; ++e) {
+            const float *f = p.ff + 9 * (p.e_lo + e);
+            float fe[SF_GPT][SF_GROUP];
 #pragma unroll
-                for (int j = 0; j < SF_RPT; ++j) {
-                    v[j] = h[j] * q.x + k[j] * q.y + l[j] * q.z;
-                    rm[j] = half_rem(v[j]);
-                    sg[j] = half_sign(v[j], rm[j]);
+            for (int t = 0; t < SF_GPT; ++t)
+#pragma unroll
+                for (int j = 0; j < SF_GROUP; ++j) {
+                    float v = f[8];
+                    for (int i = 0; i < 4; ++i) v = fmaf(f[i], expf(-0.25f * f[4 + i] * s2[t][j]), v);
+                    fe[t][j] = j < cnt[t] ? v : 0.0f;
                 }
-                float2 sa, ca, sb, cb;
-                sincos_half2(rm[0], rm[1], sa, ca);
-                sincos_half2(rm[2], rm[3], sb, cb);
-                const float2 xa = __ffma2_rn(make_float2(w.x, w.y), s2a, make_float2(w.z, w.w));
-                const float2 xb = __ffma2_rn(make_float2(w.x, w.y), s2b, make_float2(w.z, w.w));
-                float2 aa = __fmul2_rn(make_float2(fe.x, fe.y), make_float2(ex2_ftz(xa.x), ex2_ftz(xa.y)));
-                float2 ab = __fmul2_rn(make_float2(fe.z, fe.w), make_float2(ex2_ftz(xb.x), ex2_ftz(xb.y)));
-                // half-turn sign of (sin, cos) onto the amplitude
-                aa.x = __uint_as_float(__float_as_uint(aa.x) ^ sg[0]);
-                aa.y = __uint_as_float(__float_as_uint(aa.y) ^ sg[1]);
-                ab.x = __uint_as_float(__float_as_uint(ab.x) ^ sg[2]);
-                ab.y = __uint_as_float(__float_as_uint(ab.y) ^ sg[3]);
-                ra = __ffma2_rn(aa, ca, ra);
-                ia = __ffma2_rn(aa, sa, ia);
-                rb = __ffma2_rn(ab, cb, rb);
-                ib = __ffma2_rn(ab, sb, ib);
-            }
-            re[0] = ff_add_f(re[0], ra.x), re[1] = ff_add_f(re[1], ra.y);
-            re[2] = ff_add_f(re[2], rb.x), re[3] = ff_add_f(re[3], rb.y);
-            im[0] = ff_add_f(im[0], ia.x), im[1] = ff_add_f(im[1], ia.y);
-            im[2] = ff_add_f(im[2], ib.x), im[3] = ff_add_f(im[3], ib.y);
+            s_fe[(2 * e) * SF_THREADS + tid] = make_float4(fe[0][0], fe[1][0], fe[0][1], fe[1][1]);
+            s_fe[(2 * e + 1) * SF_THREADS + tid] = make_float4(fe[0][2], fe[1][2], fe[0][3], fe[1][3]);
         }
-    }
+        float2 s2p[SF_GROUP];
 #pragma unroll
-    for (int j = 0; j < SF_RPT; ++j)
-        if (r0 + j < p.n_refl)
-            p.partial[(size_t)blockIdx.y * p.n_refl + r0 + j] = make_float4(re[j].hi, re[j].lo, im[j].hi, im[j].lo);
+        for (int j = 0; j < SF_GROUP; ++j) s2p[j] = make_float2(s2[0][j], s2[1][j]);
+
+        ff reF[SF_GPT][SF_GROUP], imF[SF_GPT][SF_GROUP];
+#pragma unroll
+        for (int t = 0; t < SF_GPT; ++t)
+#pragma unroll
+            for (int j = 0; j < SF_GROUP; ++j) reF[t][j] = imF[t][j] = ff{0.0f, 0.0f};
+        const int a_begin = split * p.atoms_per_split;
+        const int a_end = min(p.n_atoms, a_begin + p.atoms_per_split);
+        for (int t0 = a_begin; t0 < a_end; t0 += SF_TILE) {
+            const int na = min(SF_TILE, a_end - t0);
+            __syncthreads();
+            for (int i = tid; i < SF_TILE; i += SF_THREADS) {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
+                float2 w = make_float2(0.0f, -INFINITY);  // zero amplitude padding
+                if (i < na) {
+                    q = p.atoms_q[t0 + i];
+                    w = p.atoms_w[t0 + i];
+                    const int e = (int)q.w - p.e_lo;
+                    if ((e < 0 || e >= p.n_fe) && !isnan(w.y)) w.y = -INFINITY;  // another pass's element (NaN stays NaN)
+                    q.w = (unsigned)min(max(e, 0), p.n_fe - 1);
+                }
+                s_q[i] = q;
+                s_w[i] = make_float4(w.x, w.x, w.y, w.y);
+#pragma unroll
+                for (int j = 1; j <= 3; ++j) {
+                    float sn, cs;
+                    sincos_turn((unsigned)j * q.z, sn, cs);
+                    s_rot[j - 1][i] = make_float4(cs, cs, sn, sn);
+                }
+            }
+            __syncthreads();
+            const int naf = (na + SF_FOLD - 1) / SF_FOLD * SF_FOLD;
+            for (int i0 = 0; i0 < naf; i0 += SF_FOLD) {
+                float2 ra[SF_GROUP], ia[SF_GROUP];
+#pragma unroll
+                for (int j = 0; j < SF_GROUP; ++j) ra[j] = ia[j] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+                for (int i = i0; i < i0 + SF_FOLD; ++i) {
+                    const uint4 q = s_q[i];
+                    const float4 w = s_w[i];
+                    const float4 fa = s_fe[(2 * q.w) * SF_THREADS + tid];
+                    const float4 fb = s_fe[(2 * q.w + 1) * SF_THREADS + tid];
+                    const float2 wb = make_float2(w.x, w.y), wl = make_float2(w.z, w.w);
+                    float2 sn, cs;
+                    sincos_turn2(h[0] * q.x + k[0] * q.y + l[0] * q.z, h[1] * q.x + k[1] * q.y + l[1] * q.z, sn, cs);
+                    const float2 nsn = make_float2(-sn.x, -sn.y);
+                    float2 cr[SF_GROUP], ci[SF_GROUP];
+                    cr[0] = cs, ci[0] = sn;
+#pragma unroll
+                    for (int j = 1; j < SF_GROUP; ++j) {
+                        const float4 R = s_rot[j - 1][i];
+                        const float2 C = make_float2(R.x, R.y), S = make_float2(R.z, R.w);
+                        cr[j] = __ffma2_rn(cs, C, __fmul2_rn(nsn, S));
+                        ci[j] = __ffma2_rn(cs, S, __fmul2_rn(sn, C));
+                    }
+                    const float2 fe[SF_GROUP] = {make_float2(fa.x, fa.y), make_float2(fa.z, fa.w), make_float2(fb.x, fb.y),
+                                                 make_float2(fb.z, fb.w)};
+#pragma unroll
+                    for (int j = 0; j < SF_GROUP; ++j) {
+                        const float2 x = __ffma2_rn(wb, s2p[j], wl);
+                        const float2 a = __fmul2_rn(fe[j], make_float2(ex2_ftz(x.x), ex2_ftz(x.y)));
+                        ra[j] = __ffma2_rn(a, cr[j], ra[j]);
+                        ia[j] = __ffma2_rn(a, ci[j], ia[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < SF_GROUP; ++j) {
+                    reF[0][j] = ff_add_f(reF[0][j], ra[j].x), reF[1][j] = ff_add_f(reF[1][j], ra[j].y);
+                    imF[0][j] = ff_add_f(imF[0][j], ia[j].x), imF[1][j] = ff_add_f(imF[1][j], ia[j].y);
+                }
+            }
+        }
+        const size_t row = (size_t)(p.split_base + split) * p.n_refl;
+#pragma unroll
+        for (int t = 0; t < SF_GPT; ++t)
+#pragma unroll
+            for (int j = 0; j < SF_GROUP; ++j)
+                if (j < cnt[t]) p.partial[row + r0[t] + j] = make_float4(reF[t][j].hi, reF[t][j].lo, imF[t][j].hi, imF[t][j].lo);
+    }
 }
 
-// Sum the splits in order; F = (re, im); M = |F|^2 P DW (FP64 scalars).
+// Sum the partial rows in order; F = (re, im); M = |F|^2 P DW (FP64 scalars).
 __global__ void sf_reduce_kernel(SFParams p) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= p.n_refl) return;
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < p.n_split; ++s) {
+    for (int s = 0; s < p.n_rows; ++s) {
         const float4 v = p.partial[(size_t)s * p.n_refl + r];
         re += (double)v.x + (double)v.y;
         im += (double)v.z + (double)v.w;
@@ -207,12 +358,11 @@ __global__ void sf_reduce_kernel(SFParams p) {
     }
 }
 
-// Split of the atom list across blockIdx.y.  A CTA's time is proportional to
-// its atoms (plus a fixed set-up of about SF_TILE / 4 atoms), and CTAs run in
-// waves of `slots` (resident CTAs on the whole GPU), so the split count n
-// minimises waves(n) x (atoms per split + set-up); splits hold a multiple of
-// SF_TILE atoms, and there are at most max_split of them.
-void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per) {
+static size_t sf_align(size_t x) { return (x + 255) / 256 * 256; }
+
+static int sf_passes(int n_elem) { return (n_elem + SF_FE_MAX - 1) / SF_FE_MAX; }
+
+static int sm_count() {
     static int s_sm = 0;
     if (s_sm == 0) {
         int dev = 0, v = 148;
@@ -221,32 +371,76 @@ void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, i
         else
             s_sm = 148;
     }
+    return s_sm;
+}
+
+// Resident CTAs of sf_main_kernel on the whole GPU for a form-factor table of
+// n_fe element types (dynamic shared memory).
+static int sf_slots(int n_fe) {
     static size_t s_shm = (size_t)-1;
     static int s_per_sm = 1;
-    const size_t shm = sizeof(float4) * SF_THREADS * (size_t)(n_elem > 0 ? n_elem : 1);
+    const size_t shm = sizeof(float4) * 2 * SF_THREADS * (size_t)(n_fe > 0 ? n_fe : 1);
     if (shm != s_shm) {
         int v = 0;
+        if (shm > 48 * 1024 &&
+            cudaFuncSetAttribute(sf_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
+            cudaGetLastError();
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, sf_main_kernel, SF_THREADS, shm) != cudaSuccess || v < 1) {
             cudaGetLastError();
             v = 1;
         }
         s_shm = shm, s_per_sm = v;
     }
-    const int per_sm = s_per_sm;
-    const long long slots = (long long)s_sm * per_sm;
-    const long long refl_blocks = (n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT);
+    return sm_count() * s_per_sm;
+}
+
+// Split of the atom list: enough (group block, split) items for about four
+// waves of resident CTAs (so that the last, partial wave costs little), with
+// at least one tile of atoms per split and at most max_split rows of partials
+// over all element passes.  The group count is estimated as 0.3 n_refl + 16
+// (lexicographic lists give 0.26-0.35 groups per reflection); any other count
+// only changes the balance, never the result.
+void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per) {
+    const int passes = sf_passes(n_elem);
+    const long long slots = sf_slots(n_elem < SF_FE_MAX ? n_elem : SF_FE_MAX);
+    const long long gblk = ((long long)(0.3 * n_refl) + 16 + SF_GPB - 1) / SF_GPB;
     const int tiles = (n_atoms + SF_TILE - 1) / SF_TILE;
-    int best_n = 1, best_per = tiles * SF_TILE;
-    double best_t = -1.0;
-    for (int want = 1; want <= max_split && want <= tiles; ++want) {
-        const int pt = (tiles + want - 1) / want;  // tiles per split
-        const int n = (tiles + pt - 1) / pt;
-        const long long ctas = (long long)n * refl_blocks;
-        const long long waves = (ctas + slots - 1) / slots;
-        const double t = (double)waves * (pt * SF_TILE + SF_TILE / 4);
-        if (best_t < 0.0 || t < 0.98 * best_t) best_t = t, best_n = n, best_per = pt * SF_TILE;
+    long long want = (4 * slots + gblk - 1) / gblk;
+    const int cap = max_split / passes;
+    if (want > cap) want = cap;
+    if (want > tiles) want = tiles;
+    if (want < 1) want = 1;
+    const int pt = (tiles + (int)want - 1) / (int)want;  // tiles per split
+    per = pt * SF_TILE;
+    n_split = (tiles + pt - 1) / pt;
+}
+
+// Workspace of the structure factors: packed atoms, the group list and block
+// offsets, the group count, and max_split rows of partials.  With ws null only
+// the size is computed.
+size_t sf_bind(SFParams *p, char *ws, int n_atoms, int n_refl, int max_split) {
+    const int nr = n_refl > 0 ? n_refl : 1;
+    const int nblk = (nr + SF_SCAN - 1) / SF_SCAN;
+    size_t off = 0;
+    const size_t q = off;
+    off += sf_align(sizeof(uint4) * (size_t)n_atoms);
+    const size_t w = off;
+    off += sf_align(sizeof(float2) * (size_t)n_atoms);
+    const size_t g = off;
+    off += sf_align(sizeof(int) * (size_t)nr);
+    const size_t b = off;
+    off += sf_align(sizeof(int) * (size_t)(nblk + 1));
+    const size_t part = off;
+    off += sf_align(sizeof(float4) * (size_t)max_split * (size_t)nr);
+    if (p && ws) {
+        p->atoms_q = reinterpret_cast<uint4 *>(ws + q);
+        p->atoms_w = reinterpret_cast<float2 *>(ws + w);
+        p->groups = reinterpret_cast<int *>(ws + g);
+        p->gblk = reinterpret_cast<int *>(ws + b);
+        p->n_groups = p->gblk + nblk;
+        p->partial = reinterpret_cast<float4 *>(ws + part);
     }
-    n_split = best_n, per = best_per;
+    return off;
 }
 
 cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
@@ -257,17 +451,23 @@ cudaError_t launch_sf_pack(SFParams &p, cudaStream_t s) {
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s) {
     if (p.n_refl <= 0) return cudaSuccess;
     sf_pack_atoms_kernel<<<(p.n_atoms + 127) / 128, 128, 0, s>>>(p);
-    dim3 grid((p.n_refl + SF_THREADS * SF_RPT - 1) / (SF_THREADS * SF_RPT), p.n_split);
-    const size_t shm = sizeof(float4) * SF_THREADS * (size_t)p.n_elem;
-    if (shm > 48 * 1024) {
-        static size_t s_opted = 0;  // largest opt-in so far (the attribute is per function, process-wide)
-        if (shm > s_opted) {
-            if (cudaFuncSetAttribute(sf_main_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm) != cudaSuccess)
-                return cudaGetLastError();
-            s_opted = shm;
-        }
+    const int nblk = (p.n_refl + SF_SCAN - 1) / SF_SCAN;
+    sf_group_count_kernel<<<nblk, SF_SCAN, 0, s>>>(p);
+    sf_group_scan_kernel<<<1, SF_SCAN, 0, s>>>(p, nblk);
+    sf_group_write_kernel<<<nblk, SF_SCAN, 0, s>>>(p);
+    const int passes = sf_passes(p.n_elem);
+    // items: at most (n_refl groups) / SF_GPB blocks x n_split; CTAs loop over items
+    const long long items_ub = (long long)((p.n_refl + SF_GPB - 1) / SF_GPB) * p.n_split;
+    for (int pass = 0; pass < passes; ++pass) {
+        p.e_lo = pass * SF_FE_MAX;
+        p.n_fe = min(SF_FE_MAX, p.n_elem - p.e_lo);
+        p.split_base = pass * p.n_split;
+        const long long slots = sf_slots(p.n_fe);
+        const unsigned grid = (unsigned)(items_ub < slots ? items_ub : slots);
+        const size_t shm = sizeof(float4) * 2 * SF_THREADS * (size_t)p.n_fe;
+        sf_main_kernel<<<grid, SF_THREADS, shm, s>>>(p);
     }
-    sf_main_kernel<<<grid, SF_THREADS, shm, s>>>(p);
+    p.n_rows = passes * p.n_split;
     sf_reduce_kernel<<<(p.n_refl + 127) / 128, 128, 0, s>>>(p);
     return cudaGetLastError();
 }
