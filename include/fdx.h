@@ -51,7 +51,7 @@ extern "C" {
 /* Return codes. */
 #define FDX_OK 0
 #define FDX_ERR_ARG (-1)       /* null pointer, non-positive size, NaN, bad enum */
-#define FDX_ERR_GEOMETRY (-2)  /* |beam . fiber| > 1e-3 (Sect. Experimental geometry), d_min <= 0, bad cell */
+#define FDX_ERR_GEOMETRY (-2)  /* fiber axis (nearly) parallel to the beam, d_min <= 0, bad cell */
 #define FDX_ERR_WORKSPACE (-3) /* workspace too small or misaligned (256-byte alignment) */
 #define FDX_ERR_CUDA (-4)      /* a CUDA runtime call or kernel launch failed */
 #define FDX_ERR_CAPACITY (-5)  /* output capacity too small */
@@ -59,6 +59,8 @@ extern "C" {
 
 #define FDX_LINESHAPE_SINC 0     /* K = N sinc^2(N t), N = 1/beta, |t| <= min(K_z/N, 1/2) (Eq. I_shape) */
 #define FDX_LINESHAPE_HOSEMANN 1 /* K = beta/(beta^2 + (1-beta^2) sin^2(pi t)), |t| <= 1/2 (Eq. Z) */
+#define FDX_LINESHAPE_GAUSS 2    /* K = exp(-pi t^2/beta^2)/beta, |t| <= min(K_z beta, 1/2): the Gaussian of
+                                    the same integral breadth as Eq. Z (Eq. breadth); forward only */
 #define FDX_INTENSITY_NONE 0     /* P = 1 */
 #define FDX_INTENSITY_HOSEMANN 1 /* P = prod_i 2A_i/(1 + A_i^2), A_i = exp(-2 pi^2 g_i^2 h_i^2) (Eq. Ipara) */
 
@@ -102,7 +104,8 @@ typedef struct fdx_geometry {
     double distance;        /* sample-detector distance */
     double pixel;           /* pixel size, same unit as distance */
     int32_t n_x, n_y;       /* detector size in pixels, 1..16384 each */
-    double fiber_axis[3];   /* fiber (rotation) axis, need not be unit */
+    double fiber_axis[3];   /* fiber (rotation) axis, need not be unit; tilted towards the beam by the
+                               fiber tilt (Sect. Experimental geometry: tilt), not parallel to it */
     double beam_axis[3];    /* incident beam direction, need not be unit */
     double delta_L;         /* Lorentz regulariser delta of Eq. lorentz (1/A), > 0 */
 } fdx_geometry;

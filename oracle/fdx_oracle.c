@@ -20,9 +20,11 @@
  *   per-reflection disorder .......... Eqs. Ah, breadth, Neff, Ipara; the
  *                                      anisotropic axis damping of Sect.
  *                                      "Paracrystalline disorder"
- *   lineshapes ....................... Eq. I_shape (sinc^2 with N_eff) and
+ *   lineshapes ....................... Eq. I_shape (sinc^2 with N_eff),
  *                                      Eq. Z (Hosemann) with the combined
- *                                      breadth of Eq. Neff
+ *                                      breadth of Eq. Neff, and the Gaussian
+ *                                      of the same integral breadth (Eq.
+ *                                      breadth)
  *   angular shapes ................... Sect. "Angular peak shapes": Gaussian,
  *                                      Lorentzian, Voigt normalised to g(0)=1;
  *                                      the Voigt is the convolution integral
@@ -72,7 +74,7 @@ typedef struct {
     double L[3];             /* crystallite size along a, b, c (A) */
     double g[3];             /* Hosemann g along a, b, c */
     double B_axis[3];        /* axis damping B_a, B_b, B_c (A^2) */
-    int32_t lineshape;       /* 0 = sinc, 1 = Hosemann */
+    int32_t lineshape;       /* 0 = sinc, 1 = Hosemann, 2 = Gaussian of matched breadth */
     int32_t intensity_model; /* 0 = none, 1 = Hosemann */
     double sigma, gamma;     /* orientation widths (rad) */
     double sigma_r;          /* radial shell width (1/A) */
@@ -240,17 +242,25 @@ double or_lineshape(int32_t lineshape, double t, double beta, double *dK_dbeta) 
             *dK_dbeta = -N * N * dKdN;
         }
         return K;
-    } else {
+    } else if (lineshape == 1) {
         double s = sin(OR_PI * t);
         double s2 = s * s;
         double den = beta * beta + (1.0 - beta * beta) * s2;
         if (dK_dbeta) *dK_dbeta = (s2 * (1.0 + beta * beta) - beta * beta) / (den * den);
         return beta / den;
+    } else {
+        /* Gaussian of the same integral breadth beta (Sect. "Paracrystalline
+         * disorder", the alternative to Eq. Z; reading R20): peak 1/beta, unit
+         * integral, K = exp(-pi t^2 / beta^2) / beta. */
+        double q = t / beta;
+        double K = exp(-OR_PI * q * q) / beta;
+        if (dK_dbeta) *dK_dbeta = K * (2.0 * OR_PI * q * q - 1.0) / beta;
+        return K;
     }
 }
 
 double or_support(int32_t lineshape, double beta, double K_z) {
-    if (lineshape == 0) {
+    if (lineshape == 0 || lineshape == 2) {
         double t = K_z * beta;
         return t < 0.5 ? t : 0.5;
     }

@@ -48,7 +48,9 @@ int validate_broadening(const fdx_broadening *b) {
         if (!(b->g[i] >= 0) || !isfinite(b->g[i])) return FDX_ERR_ARG;
         if (!isfinite(b->B_axis[i])) return FDX_ERR_ARG;
     }
-    if (b->lineshape != FDX_LINESHAPE_SINC && b->lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
+    if (b->lineshape != FDX_LINESHAPE_SINC && b->lineshape != FDX_LINESHAPE_HOSEMANN &&
+        b->lineshape != FDX_LINESHAPE_GAUSS)
+        return FDX_ERR_ARG;
     if (b->intensity_model != FDX_INTENSITY_NONE && b->intensity_model != FDX_INTENSITY_HOSEMANN) return FDX_ERR_ARG;
     if (!(b->sigma >= 0) || !(b->gamma >= 0) || !isfinite(b->sigma) || !isfinite(b->gamma)) return FDX_ERR_ARG;
     if (b->gamma == 0 && !(b->sigma > 0)) return FDX_ERR_ARG;  // no angular shape
@@ -73,7 +75,9 @@ int validate_geometry(const fdx_geometry *g) {
     if (!(nf > 0) || !(nb > 0)) return FDX_ERR_ARG;
     const double c = (g->fiber_axis[0] * g->beam_axis[0] + g->fiber_axis[1] * g->beam_axis[1] +
                       g->fiber_axis[2] * g->beam_axis[2]) / (nf * nb);
-    if (fabs(c) > 1e-3) return FDX_ERR_GEOMETRY;  // Sect. Experimental geometry
+    // any fiber tilt towards the beam (Sect. Experimental geometry: tilt); the
+    // detector's vertical axis is the fiber axis projected onto it
+    if (fabs(c) > 1.0 - 1e-6) return FDX_ERR_GEOMETRY;
     return FDX_OK;
 }
 
@@ -478,7 +482,7 @@ const char *fdx_error_string(int code) {
     switch (code) {
         case FDX_OK: return "ok";
         case FDX_ERR_ARG: return "invalid argument";
-        case FDX_ERR_GEOMETRY: return "invalid geometry (cell, resolution, or beam not orthogonal to fiber)";
+        case FDX_ERR_GEOMETRY: return "invalid geometry (cell, resolution, or fiber axis parallel to the beam)";
         case FDX_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
         case FDX_ERR_CUDA: return "CUDA runtime error";
         case FDX_ERR_CAPACITY: return "output capacity too small";

@@ -81,6 +81,16 @@ __device__ __forceinline__ float sinc_term(float ta, float tb, float tc, const f
     return q * __fdividef(num, den);
 }
 
+// Gaussian lineshape product: prod_i exp(-pi t_i^2 / beta_i^2) = 2^-(sum LA_i t_i^2)
+// with LA_i = pi log2(e) / beta_i^2 (one SFU exp2); the factor prod 1/beta_i is
+// in the pair factor.
+__device__ __forceinline__ float gauss_term(float ta, float tb, float tc, const float *la) {
+    const float x = fmaf(la[0] * ta, ta, fmaf(la[1] * tb, tb, la[2] * tc * tc));
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-x));
+    return y;
+}
+
 // sin(pi x), cos(pi x) for |x| < 2^20: x = q/2 + f with q = rint(2x), |f| <= 1/4,
 // so pi x = q pi/2 + pi f; sin(pi f), cos(pi f) from the sin(2 pi r)/cos(2 pi r)
 // polynomials at r = f/2, then a rotation by q quarter turns.
@@ -327,7 +337,8 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                     if (MODE == MODE_CNT) {
                         acc[p].cnt += in ? 1 : 0;
                     } else {
-                        const float kv = nq.w * sinc_term(ta, tb, tcc, la);
+                        const float kv =
+                            nq.w * (LS == FDX_LINESHAPE_GAUSS ? gauss_term(ta, tb, tcc, la) : sinc_term(ta, tb, tcc, la));
                         r0[p] += in ? kv : 0.0f;
                     }
                 }

@@ -139,21 +139,24 @@ cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream
     return cudaGetLastError();
 }
 
-template <int PPL>
-static void launch_ppl(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+template <int LS, int PPL>
+static void launch_ls(const PatternParams &p, bool count_mode, cudaStream_t s) {
     dim3 grid((p.nx + 15) / 16, (p.ny + 8 * PPL - 1) / (8 * PPL));
     dim3 block(PAIR_WARPS * 32);
-    if (lineshape == FDX_LINESHAPE_HOSEMANN) {
-        if (count_mode)
-            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
-        else
-            pattern_kernel<FDX_LINESHAPE_HOSEMANN, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
-    } else {
-        if (count_mode)
-            pattern_kernel<FDX_LINESHAPE_SINC, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
-        else
-            pattern_kernel<FDX_LINESHAPE_SINC, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
-    }
+    if (count_mode)
+        pattern_kernel<LS, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
+    else
+        pattern_kernel<LS, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
+}
+
+template <int PPL>
+static void launch_ppl(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+    if (lineshape == FDX_LINESHAPE_HOSEMANN)
+        launch_ls<FDX_LINESHAPE_HOSEMANN, PPL>(p, count_mode, s);
+    else if (lineshape == FDX_LINESHAPE_GAUSS)
+        launch_ls<FDX_LINESHAPE_GAUSS, PPL>(p, count_mode, s);
+    else
+        launch_ls<FDX_LINESHAPE_SINC, PPL>(p, count_mode, s);
 }
 
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {

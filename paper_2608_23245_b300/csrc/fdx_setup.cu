@@ -248,6 +248,11 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
             tm[i] = 0.5;
             o[REC_LA + i] = (float)(beta[i] * beta[i]);
             o[REC_LB + i] = (float)(1.0 - beta[i] * beta[i]);
+        } else if (p.lineshape == FDX_LINESHAPE_GAUSS) {
+            // K = exp(-pi t^2 / beta^2) / beta = 2^(-LA t^2) / beta
+            tm[i] = fmin(p.K_z * beta[i], 0.5);
+            o[REC_LA + i] = (float)(FDX_PI * 1.4426950408889634 / (beta[i] * beta[i]));
+            o[REC_LB + i] = 0.0f;
         } else {
             tm[i] = fmin(p.K_z * beta[i], 0.5);
             o[REC_LA + i] = (float)(1.0 / beta[i]);
@@ -267,6 +272,8 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
     double fr = M * r0 * r0;
     if (p.lineshape == FDX_LINESHAPE_HOSEMANN) {
         fr *= beta[0] * beta[1] * beta[2];
+    } else if (p.lineshape == FDX_LINESHAPE_GAUSS) {
+        fr /= beta[0] * beta[1] * beta[2];
     } else {
         const double pi2 = FDX_PI * FDX_PI;
         fr *= (1.0 / beta[0]) * (1.0 / beta[1]) * (1.0 / beta[2]) / (pi2 * pi2 * pi2);

@@ -30,6 +30,7 @@ ELEMENT_P = (0.5, 0.2, 0.25, 0.05)
 
 LINESHAPE_SINC = 0
 LINESHAPE_HOSEMANN = 1
+LINESHAPE_GAUSS = 2
 INTENSITY_NONE = 0
 INTENSITY_HOSEMANN = 1
 
@@ -344,6 +345,30 @@ def small_lorentz() -> Problem:
     geom = Geometry(wavelength=1.0, distance=200.0, pixel=1.2, n_x=84, n_y=52)
     return Problem("small_lorentz", (50.0, 50.0, 70.0, math.pi / 2, math.pi / 2, math.pi / 2),
                    atoms, 4.5, 0.0, br, geom, seed)
+
+
+def small_gauss() -> Problem:
+    """The reduced helix (small_helix) with the Gaussian lineshape of matched
+    integral breadth instead of the Hosemann factor."""
+    p = small_helix()
+    return replace(p, name="small_gauss", br=replace(p.br, lineshape=LINESHAPE_GAUSS))
+
+
+def tilted(p: Problem, tilt_deg: float) -> Problem:
+    """The same problem with the fiber axis tilted by tilt_deg towards the
+    beam (rotation about the detector's horizontal axis n x b)."""
+    n = np.asarray(p.geom.fiber_axis, float)
+    b = np.asarray(p.geom.beam_axis, float)
+    n = n / np.linalg.norm(n)
+    b = b / np.linalg.norm(b)
+    t = math.radians(tilt_deg)
+    nt = math.cos(t) * n - math.sin(t) * b
+    return replace(p, name="%s_tilt%g" % (p.name, tilt_deg), geom=replace(p.geom, fiber_axis=tuple(float(x) for x in nt)))
+
+
+def small_tilted() -> Problem:
+    """The reduced helix with the fiber axis tilted by 20 deg towards the beam."""
+    return tilted(small_helix(), 20.0)
 
 
 def small_triclinic() -> Problem:

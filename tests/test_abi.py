@@ -55,15 +55,19 @@ def _problem(fdx, **geo):
     return prob
 
 
-def test_pattern_rejects_nonorthogonal_beam(fdx):
-    """Sect. Experimental geometry: beam and fiber must be orthogonal within 1e-3."""
+def test_pattern_geometry_tilt_and_parallel_axes(fdx):
+    """A fiber axis tilted towards the beam is accepted (fiber tilt, Sect.
+    Experimental geometry); a fiber axis parallel to the beam has no detector
+    frame and is rejected with FDX_ERR_GEOMETRY before any work is queued."""
     lib = fdx.lib()
-    prob = _problem(fdx, beam_axis=(1.0, 0.0, 0.01))
+    prob = _problem(fdx, beam_axis=(1.0, 0.0, 0.5))
+    assert lib.fdx_workspace_size(1, fdx._problem_array([prob])) > 0
+    prob = _problem(fdx, beam_axis=(0.0, 0.0, 1.0))
     arr = fdx._problem_array([prob])
     ims = (C.c_void_p * 1)(16)
     assert lib.fdx_pattern(1, arr, ims, C.c_void_p(256), 1 << 30, None) == -2
-    prob = _problem(fdx, beam_axis=(1.0, 0.0, 0.0009))
-    assert lib.fdx_workspace_size(1, fdx._problem_array([prob])) > 0
+    prob = _problem(fdx, beam_axis=(1e-7, 0.0, -1.0))
+    assert lib.fdx_pattern(1, fdx._problem_array([prob]), ims, C.c_void_p(256), 1 << 30, None) == -2
 
 
 def test_pattern_rejects_bad_arguments(fdx):

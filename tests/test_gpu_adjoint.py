@@ -78,7 +78,7 @@ def test_loss_kernel(gpu):
     assert np.allclose(gI.cpu().numpy(), 2 * w * d, rtol=1e-6, atol=1e-12)
 
 
-@pytest.mark.parametrize("make", [W.small_helix, W.small_lorentz, W.small_triclinic])
+@pytest.mark.parametrize("make", [W.small_helix, W.small_lorentz, W.small_triclinic, W.small_tilted])
 def test_backward_matches_oracle_adjoint(gpu, orc, make):
     """Common seeded upstream gradient dL/dI into both adjoints."""
     p = api_precision(make())
@@ -148,9 +148,10 @@ def test_refinement_gradient_helix_subset(gpu, orc):
     assert gam.grad.item() == pytest.approx(go["gamma"], rel=ADJ_TOL)
 
 
-def test_backward_rejects_sinc(gpu):
+@pytest.mark.parametrize("make", [W.small_sinc, W.small_gauss])
+def test_backward_rejects_other_lineshapes(gpu, make):
     import torch
-    p = api_precision(W.small_sinc())
+    p = api_precision(make())
     sim = gpu.Simulation(p)
     gI = torch.zeros((p.geom.n_y, p.geom.n_x), dtype=torch.float32, device="cuda")
     with pytest.raises(gpu.FdxError):

@@ -26,7 +26,7 @@ def gpu():
     return fdx
 
 
-SMALL = [W.small_sinc, W.small_helix, W.small_lorentz, W.small_triclinic]
+SMALL = [W.small_sinc, W.small_helix, W.small_lorentz, W.small_triclinic, W.small_gauss, W.small_tilted]
 
 
 def _sync():

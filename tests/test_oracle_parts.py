@@ -263,7 +263,28 @@ def test_sinc_lineshape_laue(orc, N):
     assert orc.support(0, beta, 3.0) == pytest.approx(min(3.0 / N, 0.5))
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("beta", [0.03, 0.1, 0.3])
+def test_gauss_lineshape_matched_breadth(orc, beta):
+    """The Gaussian alternative to Eq. Z has the same integral breadth: its
+    integral over the support divided by its peak equals that of the Hosemann
+    factor over one period (both beta, Eq. breadth); K = exp(-pi t^2/beta^2)/beta
+    against the textbook Gaussian integral erf(sqrt(pi) x / beta) beta;
+    support min(K_z beta, 1/2)."""
+    peak_g = orc.lineshape(2, 0.0, beta)
+    peak_h = orc.lineshape(1, 0.0, beta)
+    tm = orc.support(2, beta, 3.0)
+    assert tm == pytest.approx(min(3.0 * beta, 0.5))
+    int_g, _ = si.quad(lambda t: orc.lineshape(2, t, beta), -tm, tm, epsabs=1e-14, epsrel=1e-13, limit=400)
+    int_h, _ = si.quad(lambda t: orc.lineshape(1, t, beta), -0.5, 0.5, epsabs=1e-13, epsrel=1e-13, limit=400,
+                       points=[0.0])
+    assert int_g == pytest.approx(math.erf(math.sqrt(math.pi) * tm / beta), rel=1e-11)
+    assert int_g / peak_g == pytest.approx(int_h / peak_h, rel=1e-9 + math.erfc(math.sqrt(math.pi) * tm / beta))
+    assert peak_g == pytest.approx(peak_h, rel=1e-13)
+    for x in (0.5, 1.0, 2.0):
+        assert orc.lineshape(2, x * beta, beta) * beta == pytest.approx(math.exp(-math.pi * x * x), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_lineshape_beta_derivative(orc, kind):
     for beta in (0.05, 0.2, 0.6):
         for t in (0.0, 0.013, 0.07, 0.21, 0.44):
@@ -369,15 +390,17 @@ def test_node_weights_gaussian_cap(orc):
 # ------------------------------------------------------------- geometry ---
 
 def test_pixel_on_ewald_sphere(orc):
-    """Eq. laue: every pixel's S satisfies |k_in + S| = 1/lambda."""
-    for f in (W.small_sinc, W.small_helix, W.config2):
+    """Eq. laue: every pixel's S satisfies |k_in + S| = 1/lambda; (R, Z) are
+    the components of S across and along the fiber axis (tilted or not)."""
+    for f in (W.small_sinc, W.small_helix, W.config2, W.small_tilted):
         p = f()
         k_in = np.array(p.geom.beam_axis) / p.geom.wavelength
+        n = np.array(p.geom.fiber_axis) / np.linalg.norm(p.geom.fiber_axis)
         for (i, j) in ((0, 0), (p.geom.n_x - 1, 3), (p.geom.n_x // 2, p.geom.n_y // 2), (7, p.geom.n_y - 1)):
             S, R, Z = orc.pixel_S(p, i, j)
             assert np.linalg.norm(k_in + S) == pytest.approx(1.0 / p.geom.wavelength, rel=1e-14)
-            assert R == pytest.approx(math.hypot(S[0], S[1]), rel=1e-13)
-            assert Z == pytest.approx(S[2], rel=1e-13, abs=1e-16)
+            assert R == pytest.approx(np.linalg.norm(S - (S @ n) * n), rel=1e-12)
+            assert Z == pytest.approx(S @ n, rel=1e-12, abs=1e-16)
 
 
 def _paper_ewald_solutions(S, n, k_in, lam):
@@ -401,16 +424,20 @@ def _paper_ewald_solutions(S, n, k_in, lam):
     return out
 
 
-def test_pixel_roundtrip_paper_forward_solver(orc):
+@pytest.mark.parametrize("tilt", [0.0, 20.0])
+def test_pixel_roundtrip_paper_forward_solver(orc, tilt):
     """Take a pixel's S, rotate it about the fiber axis to a random azimuth,
     and bring it back into the diffraction condition with the paper's closed
     form (Eqs. harmonic, solutions); one of the two solutions must land on
-    the same detector pixel (tilt 0, flat detector)."""
-    p = W.small_helix()
+    the same detector pixel (flat detector; fiber axis tilted by `tilt`
+    degrees towards the beam)."""
+    p = W.tilted(W.small_helix(), tilt) if tilt else W.small_helix()
     n = np.array(p.geom.fiber_axis, dtype=float)
+    n /= np.linalg.norm(n)
     b = np.array(p.geom.beam_axis, dtype=float)
     lam = p.geom.wavelength
     u_hat = np.cross(n, b)
+    u_hat /= np.linalg.norm(u_hat)
     v_hat = np.cross(b, u_hat)
     rng = np.random.default_rng(11)
     for _ in range(12):

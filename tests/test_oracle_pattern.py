@@ -33,7 +33,7 @@ def _single(p, hkl, r):
     return M
 
 
-@pytest.mark.parametrize("make", [W.small_sinc, W.small_triclinic])
+@pytest.mark.parametrize("make", [W.small_sinc, W.small_triclinic, W.small_gauss])
 def test_cull_is_exact(orc, make):
     """Skipping reflections with | |p| - r0 | > rho_B changes nothing."""
     p = make()
@@ -46,7 +46,7 @@ def test_cull_is_exact(orc, make):
     assert np.array_equal(E1, E0)
 
 
-@pytest.mark.parametrize("make", [W.small_sinc, W.small_lorentz, W.small_triclinic])
+@pytest.mark.parametrize("make", [W.small_sinc, W.small_lorentz, W.small_triclinic, W.small_gauss])
 def test_mirror_symmetry(orc, make):
     """Fiber symmetry: a pixel and its mirror about the meridian (u -> -u)
     have the same (R, Z), hence the same value; with Friedel-symmetric
@@ -63,6 +63,21 @@ def test_mirror_symmetry(orc, make):
     assert np.max(np.abs(img - img[::-1, :])) <= 1e-12 * scale
     cnt = E[:, 0].reshape(ny, nx)
     assert np.array_equal(cnt, cnt[:, ::-1])
+
+
+def test_mirror_symmetry_tilted(orc):
+    """With the fiber axis tilted towards the beam the setup is still mirror
+    symmetric about the plane of beam and fiber axis (u -> -u), but not about
+    the equator."""
+    p = W.small_tilted()
+    hkl = orc.reflections(p.cell, p.d_min)
+    M = orc.intensities_M(p, hkl)
+    I, E = orc.pattern(p, hkl, M)
+    img = I.reshape(p.geom.n_y, p.geom.n_x)
+    scale = img.max()
+    assert scale > 0
+    assert np.max(np.abs(img - img[:, ::-1])) <= 1e-12 * scale
+    assert np.max(np.abs(img - img[::-1, :])) > 1e-3 * scale
 
 
 def test_delta_limit(orc):
