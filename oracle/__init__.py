@@ -92,6 +92,8 @@ def lib():
             L.or_chain_globals.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, _dp, _dp, _dp, _dp]
             L.or_sf_adjoint.argtypes = [_dp, C.c_int32, _dp, _dp, _dp, _ip, _dp, C.c_int32, _ip, _dp, _dp,
                                         _dp, _dp]
+            L.or_scatter.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _dp, _dp,
+                                     C.c_void_p, C.POINTER(C.c_int64)]
             L.or_num_threads.restype = C.c_int32
             L.or_set_threads.argtypes = [C.c_int32]
             _lib = L
@@ -250,6 +252,24 @@ def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, **over):
     lib().or_pattern(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(pix), pix.reshape(-1),
                      int(bool(cull)), float(eta), I, E)
     return I[:len(pix)], E[:3 * len(pix)].reshape(-1, 3)
+
+
+def scatter(problem, hkl, M, samples, with_samples=False, **over):
+    """Scatter form: image [n_y, n_x] accumulated over all reflections and
+    samples (samples [n_s, 4]: xi_r, xi_1, xi_2, q), the in-support count,
+    and optionally per (reflection, sample) rows (I, dV, L, x0, y0, x1, y1)."""
+    hkl = _i32(hkl).reshape(-1, 3)
+    xs = _f64(samples).reshape(-1, 4)
+    prm = params(problem, **over)
+    img = np.zeros(problem.geom.n_x * problem.geom.n_y)
+    E = C.c_int64(0)
+    samp = np.zeros(7 * max(1, len(hkl) * len(xs))) if with_samples else None
+    lib().or_scatter(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(xs), xs.reshape(-1), img,
+                     samp.ctypes.data_as(C.c_void_p) if samp is not None else None, C.byref(E))
+    img = img.reshape(problem.geom.n_y, problem.geom.n_x)
+    if with_samples:
+        return img, E.value, samp[:7 * len(hkl) * len(xs)].reshape(len(hkl), len(xs), 7)
+    return img, E.value
 
 
 def pattern_adjoint(problem, hkl, M, gI, pix=None, **over):

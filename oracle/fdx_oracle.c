@@ -32,6 +32,11 @@
  *                                      Gauss-Legendre quadrature
  *   shell nodes and weights .......... Eqs. gnomonic and node_weight on a
  *                                      midpoint grid
+ *   scatter form ..................... per-reflection samples of the shell
+ *                                      (Eq. gnomonic), Eq. direct_sum at each,
+ *                                      Eq. lorentz per sample, Ewald rotation
+ *                                      by Eqs. harmonic/solutions, splat into
+ *                                      the hit pixel
  *   pixel value ...................... Eq. direct_sum at the pixel's query
  *                                      point, Lorentz factor of Eq. lorentz,
  *                                      pixel -> scattering vector from the
@@ -571,6 +576,125 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
             E_out[3 * q + 2] = e2c;
         }
     }
+    free(d1); free(d2); free(w); free(beta); free(Pv); free(DWv); free(G);
+}
+
+/*
+ * Scatter form of the projection (the paper's own pipeline; Sects. "Numerical
+ * evaluation: per-reflection shell quadrature", "Lorentz correction on a
+ * sampled reciprocal lattice", "Analytical Solution of the Ewald Diffraction
+ * Condition"; reading R22).  For every reflection and every sample m with
+ * normalised coordinates (xr, x1, x2) in [-1, 1]^3 and quadrature weight q:
+ *   h_r = rho_B (support circumradius), d_i = x_i T, c = (1 + d^2)^(-1/2),
+ *   S = (r0 + xr h_r) c (Sh + d1 e1 + d2 e2)                    (Eq. gnomonic)
+ *   dV = q h_r T^2 (r0 + xr h_r)^2 c^3                         (r^2 dr dOmega)
+ *   I = M r0^2 sum_k w_k prod_i K_i(a_i . (S - s_k))           (Eq. direct_sum)
+ *   L = delta_L / (R + delta_L), R = |S - (S.n) n|             (Eq. lorentz)
+ * S is rotated about the fiber axis into the diffraction condition with the
+ * closed form of Eqs. harmonic and solutions (two solutions, none when
+ * |R/sqrt(P^2+Q^2)| > 1, Eq. valid); each k_out = k_in + S_phi with
+ * k_out . b > 0 is followed to the flat detector at distance SF, and the
+ * pixel containing the hit (spot size one pixel) receives dV L I.
+ * img[ny][nx] is accumulated (not cleared).  samp (nullable) receives per
+ * (reflection, sample) 7 values: I, dV, L, and the two hits' continuous pixel
+ * coordinates x = u/p + n_x/2, y = v/p + n_y/2 (NaN when there is no hit).
+ * E (nullable) receives the number of in-support (sample, node) terms.
+ */
+void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_s,
+                const double *xs, double *img, double *samp, int64_t *E) {
+    double A[9], As[9];
+    or_basis(p->cell, A, As);
+    double bh[3], nh[3], uh[3], vh[3];
+    detector_frame(p, bh, nh, uh, vh);
+    int nn = p->n_nodes * p->n_nodes;
+    double *d1 = malloc(sizeof(double) * nn), *d2 = malloc(sizeof(double) * nn), *w = malloc(sizeof(double) * nn);
+    or_nodes(p, d1, d2, w, NULL, NULL);
+    double *beta = malloc(sizeof(double) * 3 * (n_refl > 0 ? n_refl : 1));
+    double *Pv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    double *DWv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    or_refl_scalars(p, n_refl, hkl, beta, Pv, DWv);
+    refl_geo *G = malloc(sizeof(refl_geo) * (n_refl > 0 ? n_refl : 1));
+    build_refl_geo(p, A, As, nh, bh, n_refl, hkl, beta, G);
+    const double lam = p->wavelength, T = p->T;
+    double kin[3];
+    for (int q = 0; q < 3; q++) kin[q] = bh[q] / lam;
+    const int npx = p->n_x * p->n_y;
+    int64_t etot = 0;
+#pragma omp parallel
+    {
+        double *loc = calloc((size_t)npx, sizeof(double));
+        int64_t eloc = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t r = 0; r < n_refl; r++) {
+            const refl_geo *g = &G[r];
+            const double hr = g->rhoB;
+            for (int32_t m = 0; m < n_s; m++) {
+                const double *x = xs + 4 * (size_t)m;
+                const double rr = g->r0 + x[0] * hr, dd1 = x[1] * T, dd2 = x[2] * T;
+                const double c = 1.0 / sqrt(1.0 + dd1 * dd1 + dd2 * dd2);
+                double S[3];
+                for (int q = 0; q < 3; q++) S[q] = rr * c * (g->Sh[q] + dd1 * g->e1[q] + dd2 * g->e2[q]);
+                const double dV = x[3] * hr * T * T * rr * rr * c * c * c;
+                double sum = 0.0;
+                for (int k = 0; k < nn; k++) {
+                    double inv = 1.0 / sqrt(1.0 + d1[k] * d1[k] + d2[k] * d2[k]);
+                    double X[3];
+                    for (int q = 0; q < 3; q++)
+                        X[q] = S[q] - g->r0 * (g->Sh[q] + d1[k] * g->e1[q] + d2[k] * g->e2[q]) * inv;
+                    double t[3];
+                    int in = 1;
+                    for (int i = 0; i < 3; i++) {
+                        t[i] = dot3(A + 3 * i, X);
+                        if (fabs(t[i]) > g->tmax[i]) in = 0;
+                    }
+                    if (!in) continue;
+                    eloc++;
+                    double Kp = 1.0;
+                    for (int i = 0; i < 3; i++) Kp *= or_lineshape(p->lineshape, t[i], g->beta[i], NULL);
+                    sum += w[k] * Kp;
+                }
+                const double I = M[r] * g->r0 * g->r0 * sum;
+                const double Z = dot3(S, nh);
+                double perp[3];
+                for (int q = 0; q < 3; q++) perp[q] = S[q] - Z * nh[q];
+                const double R = norm3(perp);
+                const double L = p->delta_L / (R + p->delta_L);
+                double *o = samp ? samp + 7 * ((size_t)r * n_s + m) : NULL;
+                if (o) o[0] = I, o[1] = dV, o[2] = L, o[3] = o[4] = o[5] = o[6] = NAN;
+                /* Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = R_ */
+                double nxS[3];
+                cross3(nh, S, nxS);
+                const double Aq = dot3(kin, S), Bq = dot3(kin, nxS), Dq = dot3(kin, nh) * dot3(nh, S);
+                const double Cq = dot3(kin, kin) + dot3(S, S);
+                const double Eq = (1.0 / (lam * lam) - Cq) / 2.0 - Dq;
+                const double Pp = Aq - Dq, Qp = Bq, Rp = Eq;
+                const double ratio = Rp / sqrt(Pp * Pp + Qp * Qp);
+                if (!(fabs(ratio) <= 1.0)) continue;
+                const double phi0 = atan2(Qp, Pp), dphi = acos(ratio);
+                for (int br = 0; br < 2; br++) {
+                    const double phi = br == 0 ? phi0 + dphi : phi0 - dphi;
+                    const double cp = cos(phi), sp = sin(phi), nS = dot3(nh, S);
+                    double ko[3];
+                    for (int q = 0; q < 3; q++) ko[q] = kin[q] + S[q] * cp + nxS[q] * sp + nh[q] * nS * (1.0 - cp);
+                    const double kb = dot3(ko, bh);
+                    if (!(kb > 0.0)) continue;
+                    const double xp = p->distance * dot3(ko, uh) / kb / p->pixel + 0.5 * p->n_x;
+                    const double yp = p->distance * dot3(ko, vh) / kb / p->pixel + 0.5 * p->n_y;
+                    if (o) o[3 + 2 * br] = xp, o[4 + 2 * br] = yp;
+                    const double fi = floor(xp), fj = floor(yp);
+                    if (fi < 0.0 || fj < 0.0 || fi >= p->n_x || fj >= p->n_y) continue;
+                    loc[(size_t)fj * p->n_x + (size_t)fi] += dV * L * I;
+                }
+            }
+        }
+#pragma omp critical
+        {
+            for (int q = 0; q < npx; q++) img[q] += loc[q];
+            etot += eloc;
+        }
+        free(loc);
+    }
+    if (E) *E = etot;
     free(d1); free(d2); free(w); free(beta); free(Pv); free(DWv); free(G);
 }
 

@@ -198,22 +198,54 @@ __device__ __forceinline__ void clear(PairAcc &a) {
 // sin/cos(pi tau) once per pixel and pair, sin/cos(pi sigma) (scaled by
 // sqrt(1 - beta_i^2)) once per staged node: one FMA per denominator on top of
 // the two products.
-template <int LS, int MODE, int NB, int PPL>
-__device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix<PPL> &g, const float *rec,
-                                          float4 *buf, float4 *buf2, float4 *bsc, float4 *bsc2, int lane,
-                                          PairAcc (&acc)[PPL]) {
-    constexpr bool PACKED = (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT);
-    const int n = P.n_nodes;
-    // node rows/columns that can be in each pixel's support: gnomonic
-    // projection of the support box's corners around (p - D)/r0 (FP32, bounds only)
-    int j0 = n, j1 = -1, m0 = n, m1 = -1;
+// Query points of one warp for one reflection: per lane and point p, the
+// offset (p - D)/r0 in the reflection frame (FP32, bounds only), tau_i =
+// a_i . (p - p_ref) (small; 1e4 for invalid points, far outside any support),
+// and the warp's reference offset (p_ref - D)/r0 in float-float.
+template <int PPL>
+struct QueryPts {
+    float P[PPL][3];
+    float tau[PPL][3];
+    bool valid[PPL];
+    ff dP[3];
+};
+
+// Pixel query points (reading R12): p = Z n + R e_R(D) for the lane's pixels.
+template <int PPL>
+__device__ __forceinline__ QueryPts<PPL> pixel_queries(const PatternParams &P, const PatchPix<PPL> &g, const float *rec) {
+    QueryPts<PPL> q;
 #pragma unroll
     for (int p = 0; p < PPL; ++p) {
         const float dZ = (g.Zh[p] - rec[REC_ZD]) + (g.Zl[p] - rec[REC_ZD + 1]);
         const float dR = (g.Rh[p] - rec[REC_RD]) + (g.Rl[p] - rec[REC_RD + 1]);
-        const float P0 = fmaf(dZ, rec[REC_NFR], dR * rec[REC_EFR]);
-        const float P1 = fmaf(dZ, rec[REC_NFR + 1], dR * rec[REC_EFR + 1]);
-        const float P2 = fmaf(dZ, rec[REC_NFR + 2], dR * rec[REC_EFR + 2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) q.P[p][k] = fmaf(dZ, rec[REC_NFR + k], dR * rec[REC_EFR + k]);
+        q.valid[p] = g.valid[p];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            q.tau[p][i] = g.valid[p] ? fmaf(g.dZl[p], P.AZ[i], g.dRl[p] * rec[REC_AR + i]) : 1.0e4f;
+    }
+    const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
+    const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        q.dP[k] = ff_add(ff_mul(dZr, ff{rec[REC_NFR + k], rec[REC_NFR + 3 + k]}),
+                         ff_mul(dRr, ff{rec[REC_EFR + k], rec[REC_EFR + 3 + k]}));
+    return q;
+}
+
+template <int LS, int MODE, int NB, int PPL>
+__device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts<PPL> &qp, const float *rec,
+                                          float4 *buf, float4 *buf2, float4 *bsc, float4 *bsc2, int lane,
+                                          PairAcc (&acc)[PPL]) {
+    constexpr bool PACKED = (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT);
+    const int n = P.n_nodes;
+    // node rows/columns that can be in each point's support: gnomonic
+    // projection of the support box's corners around (p - D)/r0 (FP32, bounds only)
+    int j0 = n, j1 = -1, m0 = n, m1 = -1;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        const float P0 = qp.P[p][0], P1 = qp.P[p][1], P2 = qp.P[p][2];
         float d1lo = 3.0e38f, d1hi = -3.0e38f, d2lo = 3.0e38f, d2hi = -3.0e38f;
         bool degenerate = false;
 #pragma unroll
@@ -231,7 +263,7 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
                 d2lo = fminf(d2lo, d2), d2hi = fmaxf(d2hi, d2);
             }
         }
-        if (g.valid[p]) {
+        if (qp.valid[p]) {
             if (degenerate) {
                 j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
             } else {
@@ -247,13 +279,11 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     const int M0 = __reduce_min_sync(FDX_FULL_MASK, m0), M1 = __reduce_max_sync(FDX_FULL_MASK, m1);
     if (J0 > J1 || M0 > M1) return false;
 
-    // tau_i = a_i . (p - p_ref), small; invalid pixels get a value far outside any support
     float tau[PPL][3];
 #pragma unroll
     for (int p = 0; p < PPL; ++p)
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            tau[p][i] = g.valid[p] ? fmaf(g.dZl[p], P.AZ[i], g.dRl[p] * rec[REC_AR + i]) : 1.0e4f;
+        for (int i = 0; i < 3; ++i) tau[p][i] = qp.tau[p][i];
     float st[PPL][3], ct[PPL][3];
     if (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT) {
 #pragma unroll
@@ -268,15 +298,8 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     const float E1[3] = {rec[REC_E1], rec[REC_E1 + 1], rec[REC_E1 + 2]};
     const float E2[3] = {rec[REC_E2], rec[REC_E2 + 1], rec[REC_E2 + 2]};
 
-    // (p_ref - D)/r0 in the local frame, float-float (every lane computes it for the reference pixel)
-    const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
-    const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
-    ff dP[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        dP[q] = ff_add(ff_mul(dZr, ff{rec[REC_NFR + q], rec[REC_NFR + 3 + q]}),
-                       ff_mul(dRr, ff{rec[REC_EFR + q], rec[REC_EFR + 3 + q]}));
-    }
+    // (p_ref - D)/r0 in the local frame, float-float
+    const ff dP[3] = {qp.dP[0], qp.dP[1], qp.dP[2]};
 
     // warp-wide tau box: a node can be in some pixel's support only if sigma_i
     // lies within [min tau_i - tm_i, max tau_i + tm_i] for every i
@@ -286,7 +309,7 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
         float lo = 3.0e38f, hi = -3.0e38f;
 #pragma unroll
         for (int p = 0; p < PPL; ++p)
-            if (g.valid[p]) lo = fminf(lo, tau[p][i]), hi = fmaxf(hi, tau[p][i]);
+            if (qp.valid[p]) lo = fminf(lo, tau[p][i]), hi = fmaxf(hi, tau[p][i]);
         lo = warp_min(lo), hi = warp_max(hi);
         tc[i] = 0.5f * (lo + hi);
         th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
@@ -549,6 +572,14 @@ __device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix
     }
     if (nr > 0 || nc > 0) flush();
     return true;
+}
+
+// The pair (pixel patch, reflection) of the gather form.
+template <int LS, int MODE, int NB, int PPL>
+__device__ __forceinline__ bool eval_pair(const PatternParams &P, const PatchPix<PPL> &g, const float *rec,
+                                          float4 *buf, float4 *buf2, float4 *bsc, float4 *bsc2, int lane,
+                                          PairAcc (&acc)[PPL]) {
+    return eval_core<LS, MODE, NB, PPL>(P, pixel_queries<PPL>(P, g, rec), rec, buf, buf2, bsc, bsc2, lane, acc);
 }
 
 // Copy a 64-float reflection record into the warp's shared slot.

@@ -371,6 +371,31 @@ def small_tilted() -> Problem:
     return tilted(small_helix(), 20.0)
 
 
+def scatter_samples(n_r: int, n_1: int, n_2: int, seed: int = SEED_BASE + 50) -> np.ndarray:
+    """Seeded stratified samples for the scatter form: one jittered point in
+    each cell of an n_r x n_1 x n_2 grid on [-1, 1]^3, float32 rows (x_r, x_1,
+    x_2, q) with q = 8 / (n_r n_1 n_2), ordered in bricks of 2 x 4 x 4 cells so
+    that every 32 consecutive samples are neighbours.  n_r even, n_1 and n_2
+    multiples of 4."""
+    if n_r % 2 or n_1 % 4 or n_2 % 4:
+        raise ValueError("grid must be a multiple of 2 x 4 x 4")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jit = rng.uniform(0.0, 1.0, size=(n_r, n_1, n_2, 3))
+    out = np.empty((n_r * n_1 * n_2, 4), dtype=np.float32)
+    k = 0
+    for br in range(0, n_r, 2):
+        for b1 in range(0, n_1, 4):
+            for b2 in range(0, n_2, 4):
+                for ir in range(br, br + 2):
+                    for i1 in range(b1, b1 + 4):
+                        for i2 in range(b2, b2 + 4):
+                            j = jit[ir, i1, i2]
+                            out[k] = (-1.0 + 2.0 * (ir + j[0]) / n_r, -1.0 + 2.0 * (i1 + j[1]) / n_1,
+                                      -1.0 + 2.0 * (i2 + j[2]) / n_2, 8.0 / (n_r * n_1 * n_2))
+                            k += 1
+    return out
+
+
 def small_triclinic() -> Problem:
     """A general triclinic cell (alpha, beta, gamma != 90 deg), Voigt
     orientation, anisotropic g and axis B, 18x18 nodes, 64x48 detector;
