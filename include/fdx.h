@@ -200,6 +200,36 @@ int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const 
  */
 int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream);
 
+/* Bytes of workspace fdx_scatter / fdx_scatter_evals need. */
+size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples);
+
+/*
+ * fdx_scatter -- the scatter form of the projection, the paper's own pipeline
+ * (Sects. "Numerical evaluation: per-reflection shell quadrature", "Lorentz
+ * correction on a sampled reciprocal lattice", "Analytical Solution of the
+ * Ewald Diffraction Condition").  samples is [n_samples][4] float (device,
+ * 16-byte aligned): normalised (x_r, x_1, x_2) in [-1, 1]^3 and a quadrature
+ * weight q, shared by all reflections.  For each reflection (radius r0,
+ * support circumradius h_r) and sample:
+ *   S  = (r0 + x_r h_r) c (S^ + d1 e1 + d2 e2),  d_i = x_i T,  c = (1 + d^2)^(-1/2)  (Eq. gnomonic)
+ *   dV = q h_r T^2 (r0 + x_r h_r)^2 c^3,
+ *   I  = M r0^2 sum_{k: |t_i| <= t_max,i} w_k prod_i K_i(a_i . (S - s_k))           (Eq. direct_sum)
+ *   L  = delta_L / (R + delta_L),  R = |S - (S . n) n|                              (Eq. lorentz)
+ * S is rotated about the fiber axis into the diffraction condition (Eqs.
+ * harmonic, solutions; no contribution when Eq. valid fails); each of the two
+ * hits with k_out . b > 0 adds dV L I to the detector pixel it falls in (spot
+ * size one pixel).  image is [n_y][n_x] float (device), overwritten.  Every
+ * lineshape.  Accumulation is in FP64 (atomics): the result does not depend
+ * on the order at FP32 resolution.  Asynchronous.
+ */
+int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, float *image, void *workspace,
+                size_t ws_bytes, void *stream);
+
+/* fdx_scatter_evals -- the number of in-support (sample, node) terms of the
+ * scatter form over all reflections, written to *count (int64, device). */
+int fdx_scatter_evals(const fdx_problem *prob, int32_t n_samples, const float *samples, int64_t *count,
+                      void *workspace, size_t ws_bytes, void *stream);
+
 /* Gradients written by fdx_pattern_backward; every pointer is a device pointer
  * or NULL (not written). */
 typedef struct fdx_grads {

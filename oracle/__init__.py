@@ -257,18 +257,19 @@ def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, **over):
 def scatter(problem, hkl, M, samples, with_samples=False, **over):
     """Scatter form: image [n_y, n_x] accumulated over all reflections and
     samples (samples [n_s, 4]: xi_r, xi_1, xi_2, q), the in-support count,
-    and optionally per (reflection, sample) rows (I, dV, L, x0, y0, x1, y1)."""
+    and optionally per (reflection, sample) rows (I, dV, L, x0, y0, x1, y1,
+    distance of the nearest node from the edge of the support)."""
     hkl = _i32(hkl).reshape(-1, 3)
     xs = _f64(samples).reshape(-1, 4)
     prm = params(problem, **over)
     img = np.zeros(problem.geom.n_x * problem.geom.n_y)
     E = C.c_int64(0)
-    samp = np.zeros(7 * max(1, len(hkl) * len(xs))) if with_samples else None
+    samp = np.zeros(8 * max(1, len(hkl) * len(xs))) if with_samples else None
     lib().or_scatter(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(xs), xs.reshape(-1), img,
                      samp.ctypes.data_as(C.c_void_p) if samp is not None else None, C.byref(E))
     img = img.reshape(problem.geom.n_y, problem.geom.n_x)
     if with_samples:
-        return img, E.value, samp[:7 * len(hkl) * len(xs)].reshape(len(hkl), len(xs), 7)
+        return img, E.value, samp[:8 * len(hkl) * len(xs)].reshape(len(hkl), len(xs), 8)
     return img, E.value
 
 

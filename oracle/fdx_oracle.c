@@ -596,8 +596,11 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
  * k_out . b > 0 is followed to the flat detector at distance SF, and the
  * pixel containing the hit (spot size one pixel) receives dV L I.
  * img[ny][nx] is accumulated (not cleared).  samp (nullable) receives per
- * (reflection, sample) 7 values: I, dV, L, and the two hits' continuous pixel
- * coordinates x = u/p + n_x/2, y = v/p + n_y/2 (NaN when there is no hit).
+ * (reflection, sample) 8 values: I, dV, L, the two hits' continuous pixel
+ * coordinates x = u/p + n_x/2, y = v/p + n_y/2 (NaN when there is no hit),
+ * and the smallest distance of any node from the edge of the support,
+ * min_k |max_i (|t_i| - t_max,i)| (how close the sample is to a node entering
+ * or leaving the sum).
  * E (nullable) receives the number of in-support (sample, node) terms.
  */
 void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_s,
@@ -635,19 +638,21 @@ void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
                 double S[3];
                 for (int q = 0; q < 3; q++) S[q] = rr * c * (g->Sh[q] + dd1 * g->e1[q] + dd2 * g->e2[q]);
                 const double dV = x[3] * hr * T * T * rr * rr * c * c * c;
-                double sum = 0.0;
+                double sum = 0.0, edge = 1e300;
                 for (int k = 0; k < nn; k++) {
                     double inv = 1.0 / sqrt(1.0 + d1[k] * d1[k] + d2[k] * d2[k]);
                     double X[3];
                     for (int q = 0; q < 3; q++)
                         X[q] = S[q] - g->r0 * (g->Sh[q] + d1[k] * g->e1[q] + d2[k] * g->e2[q]) * inv;
                     double t[3];
-                    int in = 1;
+                    double excess = -1e300;
                     for (int i = 0; i < 3; i++) {
                         t[i] = dot3(A + 3 * i, X);
-                        if (fabs(t[i]) > g->tmax[i]) in = 0;
+                        double ex = fabs(t[i]) - g->tmax[i];
+                        if (ex > excess) excess = ex;
                     }
-                    if (!in) continue;
+                    if (fabs(excess) < edge) edge = fabs(excess);
+                    if (excess > 0.0) continue;
                     eloc++;
                     double Kp = 1.0;
                     for (int i = 0; i < 3; i++) Kp *= or_lineshape(p->lineshape, t[i], g->beta[i], NULL);
@@ -659,8 +664,8 @@ void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
                 for (int q = 0; q < 3; q++) perp[q] = S[q] - Z * nh[q];
                 const double R = norm3(perp);
                 const double L = p->delta_L / (R + p->delta_L);
-                double *o = samp ? samp + 7 * ((size_t)r * n_s + m) : NULL;
-                if (o) o[0] = I, o[1] = dV, o[2] = L, o[3] = o[4] = o[5] = o[6] = NAN;
+                double *o = samp ? samp + 8 * ((size_t)r * n_s + m) : NULL;
+                if (o) o[0] = I, o[1] = dV, o[2] = L, o[3] = o[4] = o[5] = o[6] = NAN, o[7] = edge;
                 /* Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = R_ */
                 double nxS[3];
                 cross3(nh, S, nxS);

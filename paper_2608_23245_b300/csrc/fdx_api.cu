@@ -127,7 +127,7 @@ void cross3(const double *x, const double *y, double *z) {
 // Queue the set-up kernels (pixel geometry, node table, reflection records)
 // for one problem and fill the pattern kernel's parameters.
 int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes,
-                  double *nodes64 = nullptr) {
+                  double *nodes64 = nullptr, double *frames = nullptr) {
     const Layout L = layout_for(p);
     double A[9], As[9];
     cell_basis(p->cell, A, As);
@@ -166,6 +166,7 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
     rp.hkl = p->hkl, rp.M = p->M;
     rp.recs = reinterpret_cast<float *>(ws + L.recs);
     rp.reach = reinterpret_cast<float4 *>(ws + L.reach);
+    rp.frames = frames;
     if (launch_refl_setup(rp, st) != cudaSuccess) return FDX_ERR_CUDA;
 
     P.nx = p->geom.n_x, P.ny = p->geom.n_y, P.n_refl = p->n_refl, P.n_nodes = p->br.n_nodes;
@@ -292,6 +293,61 @@ BatchLayout batch_layout(int n, const fdx_problem *const *probs, const fdx_atoms
     }
     L.total = off;
     return L;
+}
+
+// Scatter-form workspace: the pattern layout (records, nodes) followed by the
+// FP64 reflection frames, the per-sample table and the FP64 image.
+struct ScatterLayout {
+    size_t frames, stab, img64, total;
+};
+
+ScatterLayout scatter_layout(const fdx_problem *p, int n_s) {
+    ScatterLayout S;
+    size_t off = layout_for(p).total;
+    S.frames = off, off += align_up(sizeof(double) * 12 * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    S.stab = off, off += align_up(sizeof(float4) * 3 * (size_t)n_s);
+    S.img64 = off, off += align_up(sizeof(double) * (size_t)p->geom.n_x * p->geom.n_y);
+    S.total = off;
+    return S;
+}
+
+int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, float *image, int64_t *count,
+                void *workspace, size_t ws_bytes, void *stream) {
+    int rc = validate_problem(prob);
+    if (rc) return rc;
+    if (n_s < 1 || !samples || ((uintptr_t)samples % 16)) return FDX_ERR_ARG;
+    const ScatterLayout SL = scatter_layout(prob, n_s);
+    if (!workspace || ws_bytes < SL.total || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    const size_t npx = (size_t)prob->geom.n_x * prob->geom.n_y;
+    if (prob->n_refl == 0) {
+        if (image && cudaMemsetAsync(image, 0, sizeof(float) * npx, st) != cudaSuccess) return FDX_ERR_CUDA;
+        if (count && cudaMemsetAsync(count, 0, sizeof(int64_t), st) != cudaSuccess) return FDX_ERR_CUDA;
+        return FDX_OK;
+    }
+    ScatterParams S;
+    memset(&S, 0, sizeof S);
+    rc = setup_pattern(prob, ws, st, S.P, false, nullptr, reinterpret_cast<double *>(ws + SL.frames));
+    if (rc) return rc;
+    S.n_s = n_s;
+    S.samples = reinterpret_cast<const float4 *>(samples);
+    S.stab = reinterpret_cast<float4 *>(ws + SL.stab);
+    S.frames = reinterpret_cast<const double *>(ws + SL.frames);
+    S.T = prob->br.T, S.lambda = prob->geom.wavelength, S.dist = prob->geom.distance, S.pix = prob->geom.pixel;
+    S.delta_L = prob->geom.delta_L;
+    unit3(prob->geom.fiber_axis, S.nh);
+    unit3(prob->geom.beam_axis, S.bh);
+    cross3(S.nh, S.bh, S.uh);
+    unit3(S.uh, S.uh);
+    cross3(S.bh, S.uh, S.vh);
+    S.img64 = reinterpret_cast<double *>(ws + SL.img64);
+    S.image = image;
+    S.count = reinterpret_cast<unsigned long long *>(count);
+    if (image && cudaMemsetAsync(S.img64, 0, sizeof(double) * npx, st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (count && cudaMemsetAsync(count, 0, sizeof(int64_t), st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (launch_scatter(S, prob->br.lineshape, count != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
+    return FDX_OK;
 }
 
 }  // namespace
@@ -802,6 +858,23 @@ int fdx_loss(int64_t n_px, const float *I, const float *I_target, const float *m
     lp.loss = loss_out;
     if (launch_loss(lp, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
+}
+
+size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples) {
+    if (!prob || n_samples < 1) return 0;
+    return scatter_layout(prob, n_samples).total;
+}
+
+int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, float *image, void *workspace,
+                size_t ws_bytes, void *stream) {
+    if (!image) return FDX_ERR_ARG;
+    return run_scatter(prob, n_samples, samples, image, nullptr, workspace, ws_bytes, stream);
+}
+
+int fdx_scatter_evals(const fdx_problem *prob, int32_t n_samples, const float *samples, int64_t *count,
+                      void *workspace, size_t ws_bytes, void *stream) {
+    if (!count || ((uintptr_t)count % 8)) return FDX_ERR_ARG;
+    return run_scatter(prob, n_samples, samples, nullptr, count, workspace, ws_bytes, stream);
 }
 
 int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream) {

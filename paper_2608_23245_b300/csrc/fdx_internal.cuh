@@ -157,6 +157,7 @@ struct ReflSetupParams {
     const float *M;       // may be null (then M = 1)
     float *recs;
     float4 *reach;
+    double *frames;       // may be null: [n_refl][12] (S^, e1, e2, r0, rho_B, 0) for the scatter form
 };
 
 struct NodeParams {
@@ -214,6 +215,21 @@ struct SFParams {
 };
 
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);
+
+// Scatter form (fdx_scatter.cu).
+struct ScatterParams {
+    PatternParams P;          // records, nodes (pixgeo/image unused)
+    int n_s;                  // samples per reflection
+    const float4 *samples;    // [n_s] (x_r, x_1, x_2, q)
+    float4 *stab;             // [n_s][3] per-sample table (set-up kernel)
+    const double *frames;     // [n_refl][12]
+    double T, lambda, dist, pix, delta_L;
+    double nh[3], bh[3], uh[3], vh[3];
+    double *img64;            // [ny][nx] accumulation
+    float *image;             // [ny][nx] output
+    unsigned long long *count;  // evaluation count (count mode)
+};
+cudaError_t launch_scatter(const ScatterParams &p, int lineshape, bool count_mode, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);
 size_t sf_bind(SFParams *p, char *ws, int n_atoms, int n_refl, int max_split);
 

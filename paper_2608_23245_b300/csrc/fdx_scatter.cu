@@ -1,0 +1,191 @@
+// Scatter form of the projection: the paper's own pipeline (Sects. "Numerical
+// evaluation: per-reflection shell quadrature", "Lorentz correction on a
+// sampled reciprocal lattice", "Analytical Solution of the Ewald Diffraction
+// Condition").  Each reflection is sampled on its shell, the intensity at
+// every sample is the direct sum of Eq. direct_sum, the sample carries the
+// Lorentz factor of Eq. lorentz, is rotated about the fiber axis into the
+// diffraction condition with the closed form of Eqs. harmonic/solutions, and
+// its two hits are added to the detector pixels they fall in.
+//
+// Samples: normalised (x_r, x_1, x_2) in [-1, 1]^3 with quadrature weight q,
+// shared by all reflections; for a reflection with radius r0 and support
+// circumradius h_r = rho_B:  S = (r0 + x_r h_r) c (S^ + d1 e1 + d2 e2),
+// d_i = x_i T, c = (1 + d^2)^(-1/2), volume element dV = q h_r T^2
+// (r0 + x_r h_r)^2 c^3.  The pixel value is sum over hits of dV L I.
+//
+// Work decomposition: a warp evaluates 32 consecutive samples of one
+// reflection (one sample per lane) with the same pair evaluation as the
+// gather form (eval_core: block culling, live-node staging, packed walk); the
+// query points are the samples, referred to a centre sample of the warp.  The
+// per-sample Lorentz factor and Ewald rotation run in FP64 (one lane per
+// sample), and the hits are added with FP64 atomics into an FP64 image that a
+// last kernel rounds to FP32 (order effects far below FP32 resolution).
+#include "fdx_pair.cuh"
+
+namespace fdx {
+
+static constexpr int SCAT_NODE_BUF = 288;
+
+// Per-sample table from the normalised samples (FP64, once per call):
+// (c - 1, c d1) and (c d2) as float-float, c, q T^2 c^3, x_r.
+__global__ void scatter_table_kernel(ScatterParams p) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= p.n_s) return;
+    const float4 x = p.samples[m];
+    const double d1 = (double)x.y * p.T, d2 = (double)x.z * p.T;
+    const double rho2 = d1 * d1 + d2 * d2;
+    const double qn = sqrt(1.0 + rho2), c = 1.0 / qn;
+    const double cm1 = -rho2 / (qn * (1.0 + qn));
+    float4 a, b;
+    split_double(cm1, a.x, a.y);
+    split_double(c * d1, a.z, a.w);
+    split_double(c * d2, b.x, b.y);
+    b.z = (float)c;
+    b.w = (float)((double)x.w * p.T * p.T * c * c * c);
+    p.stab[3 * m] = a;
+    p.stab[3 * m + 1] = b;
+    p.stab[3 * m + 2] = make_float4(x.x, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ double dot3d(const double *x, const double *y) {
+    return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+}
+
+// Lorentz factor, Ewald rotation (both solutions) and splat of one sample.
+__device__ __forceinline__ void splat_sample(const ScatterParams &p, const double *S, double val) {
+    const double Z = dot3d(S, p.nh);
+    double perp[3];
+    for (int q = 0; q < 3; ++q) perp[q] = S[q] - Z * p.nh[q];
+    const double R = sqrt(dot3d(perp, perp));
+    const double v = val * p.delta_L / (R + p.delta_L);
+    // Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = R_
+    double kin[3], nxS[3];
+    for (int q = 0; q < 3; ++q) kin[q] = p.bh[q] / p.lambda;
+    nxS[0] = p.nh[1] * S[2] - p.nh[2] * S[1];
+    nxS[1] = p.nh[2] * S[0] - p.nh[0] * S[2];
+    nxS[2] = p.nh[0] * S[1] - p.nh[1] * S[0];
+    const double nS = dot3d(p.nh, S);
+    const double A = dot3d(kin, S), B = dot3d(kin, nxS), D = dot3d(kin, p.nh) * nS;
+    const double C = dot3d(kin, kin) + dot3d(S, S);
+    const double E = (1.0 / (p.lambda * p.lambda) - C) / 2.0 - D;
+    const double Pp = A - D, Qp = B;
+    const double rpq = sqrt(Pp * Pp + Qp * Qp);
+    const double ratio = E / rpq;
+    if (!(fabs(ratio) <= 1.0)) return;  // Eq. valid: no rotation reaches the Ewald sphere
+    // phi = phi0 +- delta with cos(phi0), sin(phi0) = (P, Q)/rpq, cos(delta) = ratio
+    const double c0 = Pp / rpq, s0 = Qp / rpq, cd = ratio, sd = sqrt(fmax(0.0, 1.0 - ratio * ratio));
+    for (int br = 0; br < 2; ++br) {
+        const double sgn = br == 0 ? 1.0 : -1.0;
+        const double cp = c0 * cd - sgn * s0 * sd, sp = s0 * cd + sgn * c0 * sd;
+        double ko[3];
+        for (int q = 0; q < 3; ++q) ko[q] = kin[q] + S[q] * cp + nxS[q] * sp + p.nh[q] * nS * (1.0 - cp);
+        const double kb = dot3d(ko, p.bh);
+        if (!(kb > 0.0)) continue;
+        const double xp = p.dist * dot3d(ko, p.uh) / kb / p.pix + 0.5 * p.P.nx;
+        const double yp = p.dist * dot3d(ko, p.vh) / kb / p.pix + 0.5 * p.P.ny;
+        const double fi = floor(xp), fj = floor(yp);
+        if (!(fi >= 0.0) || !(fj >= 0.0) || fi >= (double)p.P.nx || fj >= (double)p.P.ny) continue;
+        atomicAdd(&p.img64[(size_t)fj * p.P.nx + (size_t)fi], v);
+    }
+}
+
+template <int LS, int MODE>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterParams p) {
+    __shared__ float4 s_nodes[PAIR_WARPS][SCAT_NODE_BUF];
+    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? SCAT_NODE_BUF : 1];
+    __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? SCAT_NODE_BUF / 2 : 1];
+    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n_chunks = (p.n_s + 31) / 32;
+    const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
+    if (item >= (long long)p.P.n_refl * n_chunks) return;
+    const int r = (int)(item / n_chunks), chunk = (int)(item % n_chunks);
+    float *rec = s_rec[warp];
+    load_record(p.P.recs, r, rec, lane);
+    const double *fr = p.frames + (size_t)r * 12;
+    const double r0 = fr[9], hr = fr[10];
+
+    const int m = chunk * 32 + lane;
+    const int n_valid = min(32, p.n_s - chunk * 32);
+    const bool valid = lane < n_valid;
+    float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tc = ta;
+    if (valid) ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
+    // (S - D)/r0 in the reflection frame: (1 + rho) (c, c d1, c d2) - (1, 0, 0), rho = x_r h_r / r0
+    const float rho = (float)((double)tc.x * hr / r0);
+    const ff u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
+    const ff u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
+    const ff u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
+    const int rl = min(26, n_valid - 1);  // a central sample of the 2 x 4 x 4 brick
+    const ff v0 = {__shfl_sync(FDX_FULL_MASK, u0.hi, rl), __shfl_sync(FDX_FULL_MASK, u0.lo, rl)};
+    const ff v1 = {__shfl_sync(FDX_FULL_MASK, u1.hi, rl), __shfl_sync(FDX_FULL_MASK, u1.lo, rl)};
+    const ff v2 = {__shfl_sync(FDX_FULL_MASK, u2.hi, rl), __shfl_sync(FDX_FULL_MASK, u2.lo, rl)};
+    QueryPts<1> q;
+    q.valid[0] = valid;
+    q.P[0][0] = u0.hi, q.P[0][1] = u1.hi, q.P[0][2] = u2.hi;
+    const float w0 = (u0.hi - v0.hi) + (u0.lo - v0.lo);
+    const float w1 = (u1.hi - v1.hi) + (u1.lo - v1.lo);
+    const float w2 = (u2.hi - v2.hi) + (u2.lo - v2.lo);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        q.tau[0][i] = valid ? fmaf(rec[REC_H + i], w0, fmaf(rec[REC_E1 + i], w1, rec[REC_E2 + i] * w2)) : 1.0e4f;
+    q.dP[0] = v0, q.dP[1] = v1, q.dP[2] = v2;
+
+    PairAcc pa[1];
+    clear(pa[0]);
+    const bool any = eval_core<LS, MODE, SCAT_NODE_BUF, 1>(p.P, q, rec, s_nodes[warp], nullptr, s_sc[warp],
+                                                           s_sc2[warp], lane, pa);
+    if (MODE == MODE_CNT) {
+        unsigned long long c = any ? (unsigned long long)pa[0].cnt : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FDX_FULL_MASK, c, o);
+        if (lane == 0 && c) atomicAdd(p.count, c);
+        return;
+    }
+    if (!valid || !any) return;
+    const double I = (double)rec[REC_FR] * ((double)pa[0].s0.hi + (double)pa[0].s0.lo);
+    if (!(I != 0.0)) return;
+    // S in the laboratory frame, (r0 + x_r h_r) (c, c d1, c d2) from the FP64
+    // frame and the float-float table (no FP32 rounding: the hit position of a
+    // sample near the edge of the Ewald condition is sensitive to S), and the
+    // volume element
+    const double rr = r0 + (double)tc.x * hr;
+    const double U0 = 1.0 + ((double)ta.x + (double)ta.y), U1 = (double)ta.z + (double)ta.w,
+                 U2 = (double)tb.x + (double)tb.y;
+    double S[3];
+    for (int k = 0; k < 3; ++k) S[k] = rr * (U0 * fr[k] + U1 * fr[3 + k] + U2 * fr[6 + k]);
+    const double dV = (double)tb.w * hr * rr * rr;
+    splat_sample(p, S, dV * I);
+}
+
+__global__ void scatter_finish_kernel(const double *img64, float *image, long long n) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) image[k] = (float)img64[k];
+}
+
+template <int LS>
+static void launch_scatter_ls(const ScatterParams &p, bool count_mode, cudaStream_t s) {
+    const long long items = (long long)p.P.n_refl * ((p.n_s + 31) / 32);
+    const unsigned grid = (unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS);
+    if (grid == 0) return;
+    if (count_mode)
+        scatter_kernel<LS, MODE_CNT><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
+    else
+        scatter_kernel<LS, MODE_FWD><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
+}
+
+cudaError_t launch_scatter(const ScatterParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+    scatter_table_kernel<<<(p.n_s + 127) / 128, 128, 0, s>>>(p);
+    if (lineshape == FDX_LINESHAPE_HOSEMANN)
+        launch_scatter_ls<FDX_LINESHAPE_HOSEMANN>(p, count_mode, s);
+    else if (lineshape == FDX_LINESHAPE_GAUSS)
+        launch_scatter_ls<FDX_LINESHAPE_GAUSS>(p, count_mode, s);
+    else
+        launch_scatter_ls<FDX_LINESHAPE_SINC>(p, count_mode, s);
+    if (!count_mode) {
+        const long long n = (long long)p.P.nx * p.P.ny;
+        scatter_finish_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.img64, p.image, n);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fdx

@@ -288,6 +288,11 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
         o[REC_DBF + i] = beta[i] < 1.0 ? (float)(2.0 * beta[i] / (1.0 - beta[i] * beta[i])) : 0.0f;
     }
     o[REC_M] = (float)M;
+    if (p.frames) {
+        double *fr64 = p.frames + (size_t)r * 12;
+        for (int q = 0; q < 3; ++q) fr64[q] = Sh[q], fr64[3 + q] = e1[q], fr64[6 + q] = e2[q];
+        fr64[9] = r0, fr64[10] = rhoB, fr64[11] = 0.0;
+    }
     const double psiD = atan2(RD, ZD);
     const double dpsi = atan(p.T * sqrt(2.0)) + (rhoB < r0 ? asin(rhoB / r0) : FDX_PI);
     p.reach[r] = make_float4((float)r0, (float)(rhoB * (1.0 + 1e-4) + 1e-6), (float)psiD,

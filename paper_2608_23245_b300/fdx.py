@@ -83,6 +83,12 @@ def lib():
             L.fdx_pattern.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem)), C.POINTER(C.c_void_p), C.c_void_p,
                                       C.c_size_t, C.c_void_p]
             L.fdx_pattern_evals.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.fdx_scatter_workspace_size.restype = C.c_size_t
+            L.fdx_scatter_workspace_size.argtypes = [C.POINTER(Problem), C.c_int32]
+            L.fdx_scatter.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                      C.c_void_p]
+            L.fdx_scatter_evals.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_size_t, C.c_void_p]
             _lib = L
     return _lib
 
@@ -267,6 +273,32 @@ def fdx_pattern_evals(problem, counts, workspace=None, stream=None):
     return counts
 
 
+def fdx_scatter_workspace_size(problem, n_samples: int) -> int:
+    return int(lib().fdx_scatter_workspace_size(C.byref(problem), int(n_samples)))
+
+
+def fdx_scatter(problem, samples, image, workspace=None, stream=None):
+    """Scatter form: samples [n_s, 4] float32 (device), image [n_y, n_x] float32 (device)."""
+    import torch
+    n_s = int(samples.shape[0])
+    if workspace is None:
+        workspace = torch.empty(fdx_scatter_workspace_size(problem, n_s), dtype=torch.uint8, device=image.device)
+    _check(lib().fdx_scatter(C.byref(problem), n_s, _ptr(samples), _ptr(image), _ptr(workspace),
+                             int(workspace.numel()), _stream(stream)), "fdx_scatter")
+    return image
+
+
+def fdx_scatter_evals(problem, samples, count, workspace=None, stream=None):
+    """In-support (sample, node) term count of the scatter form into count (int64 scalar, device)."""
+    import torch
+    n_s = int(samples.shape[0])
+    if workspace is None:
+        workspace = torch.empty(fdx_scatter_workspace_size(problem, n_s), dtype=torch.uint8, device=count.device)
+    _check(lib().fdx_scatter_evals(C.byref(problem), n_s, _ptr(samples), _ptr(count), _ptr(workspace),
+                                   int(workspace.numel()), _stream(stream)), "fdx_scatter_evals")
+    return count
+
+
 # ---------------------------------------------------------------------------
 # convenience: the whole forward path for one workloads.Problem
 # ---------------------------------------------------------------------------
@@ -308,6 +340,19 @@ class Simulation:
         counts = torch.empty_like(self.image, dtype=torch.int32)
         fdx_pattern_evals(self.prob, counts, self.ws, stream)
         return counts
+
+    def scatter(self, samples, image=None, workspace=None, stream=None):
+        """Structure factors (for M) must have been computed; scatter-form image."""
+        import torch
+        if image is None:
+            image = torch.empty_like(self.image)
+        return fdx_scatter(self.prob, samples, image, workspace, stream)
+
+    def scatter_evals(self, samples, workspace=None, stream=None):
+        import torch
+        count = torch.zeros((), dtype=torch.int64, device=self.image.device)
+        fdx_scatter_evals(self.prob, samples, count, workspace, stream)
+        return count
 
 
 # ---------------------------------------------------------------------------
