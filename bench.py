@@ -257,6 +257,38 @@ def large_measurements(g=0.01, reps=2, roi=128):
             "fp32_over_plain_fp64_roi": t_roi64 / t_roi32, "roi_max_rel_diff_fp32_vs_fp64": rel}
 
 
+def scatter_measurements(grid=(16, 16, 16), reps=2):
+    """Scatter form (the paper's own pipeline) on the headline workload:
+    n_r x n_1 x n_2 stratified samples per reflection (4,096 by default; the
+    paper's tutorial uses 5,000), each evaluated by the direct sum, Lorentz
+    corrected, rotated into the Ewald condition and added to its pixels.
+    Reported as in-support (sample, node) evaluations per second and samples
+    per second."""
+    import torch
+    from paper_2608_23245_b300 import fdx, workloads as W
+    p = W.config1()
+    sim = fdx.Simulation(p)
+    sim.structure_factors()
+    xs = torch.as_tensor(W.scatter_samples(*grid), device="cuda")
+    ws = torch.empty(fdx.fdx_scatter_workspace_size(sim.prob, xs.shape[0]), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(sim.image)
+    E = int(sim.scatter_evals(xs, ws).item())
+    sim.scatter(xs, out, ws)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        sim.scatter(xs, out, ws)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    n_samples = int(sim.hkl.shape[0]) * int(xs.shape[0])
+    return {"workload": "helix config: 5,062 reflections x %d stratified samples, 64^2 nodes, 1024^2 detector"
+                        % xs.shape[0],
+            "evals": E, "ms": 1e3 * t, "evals_per_s": E / t, "samples_per_s": n_samples / t,
+            "frac_of_fp32_peak": FLOPS_PER_EVAL * E / t / 1e12 / fp32_peak_tflops(_peaks().get("sm_max_mhz", 2032.0))}
+
+
 def batch_measurements(n_models=256, tune_models=8):
     """Batched refinement (config-4 recipe): n_models seeded candidate models of
     uneven size, each against its own perturbed target.  One step = structure
@@ -392,6 +424,7 @@ def main():
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--no-scatter", action="store_true")
     ap.add_argument("--batch-models", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -498,6 +531,8 @@ def main():
         line["refine"] = refine_measurements()
     if not args.no_large:
         line["large"] = large_measurements()
+    if not args.no_scatter:
+        line["scatter"] = scatter_measurements()
     if not args.no_batch:
         line["batch"] = batch_measurements(args.batch_models)
     if not args.no_cpu_baseline:
