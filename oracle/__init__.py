@@ -94,6 +94,11 @@ def lib():
                                         _dp, _dp]
             L.or_scatter.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _dp, _dp,
                                      C.c_void_p, C.POINTER(C.c_int64)]
+            L.or_ring.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _ip, C.c_int32, C.c_int32,
+                                  _dp, _lp]
+            L.or_point.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _dp, _dp]
+            L.or_ring_grid.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.c_int32,
+                                       C.POINTER(C.c_double), C.POINTER(C.c_int32)]
             L.or_num_threads.restype = C.c_int32
             L.or_set_threads.argtypes = [C.c_int32]
             _lib = L
@@ -252,6 +257,43 @@ def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, **over):
     lib().or_pattern(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(pix), pix.reshape(-1),
                      int(bool(cull)), float(eta), I, E)
     return I[:len(pix)], E[:3 * len(pix)].reshape(-1, 3)
+
+
+RING_MAX_N = 1024  # cap on the azimuth points per reflection of the ring average
+
+
+def ring(problem, hkl, M, pix=None, max_n=RING_MAX_N, refine=1, **over):
+    """Ring-integrated cylindrical average (Eq. cyl-average) at the pixels;
+    returns (I[n_pix], E[n_pix]) with E the in-support term counts.  refine > 1
+    multiplies the azimuth points (convergence checks; 1 is the definition)."""
+    if pix is None:
+        pix = all_pixels(problem)
+    pix = _i32(pix).reshape(-1, 2)
+    hkl = _i32(hkl).reshape(-1, 3)
+    prm = params(problem, **over)
+    I = np.zeros(max(len(pix), 1))
+    E = np.zeros(max(len(pix), 1), dtype=np.int64)
+    lib().or_ring(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(pix), pix.reshape(-1), int(max_n),
+                  int(refine), I, E)
+    return I[:len(pix)], E[:len(pix)]
+
+
+def point(problem, hkl, M, pts, **over):
+    """Reciprocal-space intensity sum_r M r0^2 sum_k w_k prod K at 3-D points [n, 3]."""
+    hkl = _i32(hkl).reshape(-1, 3)
+    pts = _f64(pts).reshape(-1, 3)
+    prm = params(problem, **over)
+    I = np.zeros(max(len(pts), 1))
+    lib().or_point(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(pts), pts.reshape(-1), I)
+    return I[:len(pts)]
+
+
+def ring_grid(r0, RD, rhoB, T, w_min, max_n=RING_MAX_N):
+    """(Phi_r, N_r) of the ring average's azimuth rule for one reflection."""
+    Phi, N = C.c_double(0.0), C.c_int32(0)
+    lib().or_ring_grid(float(r0), float(RD), float(rhoB), float(T), float(w_min), int(max_n), C.byref(Phi),
+                       C.byref(N))
+    return Phi.value, N.value
 
 
 def scatter(problem, hkl, M, samples, with_samples=False, **over):

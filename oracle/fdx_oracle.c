@@ -32,6 +32,8 @@
  *                                      Gauss-Legendre quadrature
  *   shell nodes and weights .......... Eqs. gnomonic and node_weight on a
  *                                      midpoint grid
+ *   ring average ..................... Eq. cyl-average by a per-reflection
+ *                                      midpoint rule over the ring azimuth
  *   scatter form ..................... per-reflection samples of the shell
  *                                      (Eq. gnomonic), Eq. direct_sum at each,
  *                                      Eq. lorentz per sample, Ewald rotation
@@ -575,6 +577,154 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
             E_out[3 * q + 1] = e1c;
             E_out[3 * q + 2] = e2c;
         }
+    }
+    free(d1); free(d2); free(w); free(beta); free(Pv); free(DWv); free(G);
+}
+
+/*
+ * Ring-integrated cylindrical average (Eq. cyl-average; reading R21): the
+ * pixel value is the average of the reciprocal-space intensity over the ring
+ * of the pixel's (R, Z) about the fiber axis, with no Lorentz factor:
+ *   I = sum_r M_r r0^2 (1/2pi) int dphi sum_k w_k prod_i K_i(a_i . (p(phi) - s_k)),
+ *   p(phi) = Z n + R (cos(phi) e_R + sin(phi) e_P),  e_P = n x e_R,
+ * phi measured from the reflection's meridional half-plane.  Quadrature per
+ * reflection (or_ring_grid): the midpoint rule with N_r points on
+ * [-Phi_r, Phi_r], outside which the ring cannot come within
+ * rho_tot = rho_B + sqrt(2) r0 T of D (no node is in the support there), and
+ * N_r = clamp(ceil(2 Phi_r / dphi), 4, max_n) with the step dphi =
+ * w_min / (4 (R_D + rho_tot)), w_min = min_i beta_i / |a_i| (a quarter of the
+ * narrowest lattice breadth along the ring at its largest radius).  `over`
+ * multiplies N_r (1 for the definition; larger values refine the rule, for
+ * convergence checks).
+ */
+void or_ring_grid_over(double r0, double RD, double rhoB, double T, double w_min, int32_t max_n, int32_t over,
+                       double *Phi, int32_t *N) {
+    const double rt = rhoB + sqrt(2.0) * r0 * T;
+    double ph = OR_PI;
+    const double inner = RD - rt;
+    if (inner > 0.0) {
+        const double x = rt / (2.0 * sqrt(inner * RD));
+        if (x < 1.0) ph = 2.0 * asin(x);
+    }
+    const double dphi = w_min / (4.0 * (RD + rt));
+    double n = ceil(2.0 * ph / dphi) * over;
+    if (!(n >= 4.0)) n = 4.0;
+    if (n > (double)max_n) n = (double)max_n;
+    *Phi = ph;
+    *N = (int32_t)n;
+}
+
+void or_ring_grid(double r0, double RD, double rhoB, double T, double w_min, int32_t max_n, double *Phi, int32_t *N) {
+    or_ring_grid_over(r0, RD, rhoB, T, w_min, max_n, 1, Phi, N);
+}
+
+/* sum_k w_k prod_i K_i(a_i . (pq - s_k)) over the nodes in the support of pq;
+ * *E (nullable) counts them. */
+static double node_sum(const or_params *p, const double *A, const refl_geo *g, const double *d1, const double *d2,
+                       const double *w, int nn, const double *pq, int64_t *E) {
+    double sum = 0.0;
+    for (int k = 0; k < nn; k++) {
+        double inv = 1.0 / sqrt(1.0 + d1[k] * d1[k] + d2[k] * d2[k]);
+        double X[3];
+        for (int c = 0; c < 3; c++) X[c] = pq[c] - g->r0 * (g->Sh[c] + d1[k] * g->e1[c] + d2[k] * g->e2[c]) * inv;
+        double t[3];
+        int in = 1;
+        for (int i = 0; i < 3; i++) {
+            t[i] = dot3(A + 3 * i, X);
+            if (fabs(t[i]) > g->tmax[i]) in = 0;
+        }
+        if (!in) continue;
+        if (E) (*E)++;
+        double Kp = 1.0;
+        for (int i = 0; i < 3; i++) Kp *= or_lineshape(p->lineshape, t[i], g->beta[i], NULL);
+        sum += w[k] * Kp;
+    }
+    return sum;
+}
+
+void or_ring(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_pix,
+             const int32_t *pix, int32_t max_n, int32_t over, double *I_out, int64_t *E_out) {
+    double A[9], As[9];
+    or_basis(p->cell, A, As);
+    double bh[3], nh[3], uh[3], vh[3];
+    detector_frame(p, bh, nh, uh, vh);
+    int nn = p->n_nodes * p->n_nodes;
+    double *d1 = malloc(sizeof(double) * nn), *d2 = malloc(sizeof(double) * nn), *w = malloc(sizeof(double) * nn);
+    or_nodes(p, d1, d2, w, NULL, NULL);
+    double *beta = malloc(sizeof(double) * 3 * (n_refl > 0 ? n_refl : 1));
+    double *Pv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    double *DWv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    or_refl_scalars(p, n_refl, hkl, beta, Pv, DWv);
+    refl_geo *G = malloc(sizeof(refl_geo) * (n_refl > 0 ? n_refl : 1));
+    build_refl_geo(p, A, As, nh, bh, n_refl, hkl, beta, G);
+    double alen[3];
+    for (int i = 0; i < 3; i++) alen[i] = norm3(A + 3 * i);
+
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t q = 0; q < n_pix; q++) {
+        double S[3], R, Z;
+        or_pixel_S(p, pix[2 * q], pix[2 * q + 1], S, &R, &Z);
+        const double plen = sqrt(R * R + Z * Z);
+        double acc = 0.0;
+        int64_t e0 = 0;
+        for (int32_t r = 0; r < n_refl; r++) {
+            const refl_geo *g = &G[r];
+            if (fabs(plen - g->r0) > g->rhoB * (1.0 + 1e-9) + 1e-12) continue;
+            double D[3];
+            for (int c = 0; c < 3; c++) D[c] = g->r0 * g->Sh[c];
+            const double RD = dot3(D, g->eR);
+            double eP[3];
+            cross3(nh, g->eR, eP);
+            double w_min = 1e300;
+            for (int i = 0; i < 3; i++) {
+                const double wi = g->beta[i] / alen[i];
+                if (wi < w_min) w_min = wi;
+            }
+            double Phi;
+            int32_t N;
+            or_ring_grid_over(g->r0, RD, g->rhoB, p->T, w_min, max_n, over, &Phi, &N);
+            const double rt = g->rhoB + sqrt(2.0) * g->r0 * p->T;
+            const double h = 2.0 * Phi / N;
+            double ring = 0.0;
+            for (int32_t j = 0; j < N; j++) {
+                const double phi = -Phi + (j + 0.5) * h;
+                double pq[3], dd[3];
+                for (int c = 0; c < 3; c++) pq[c] = Z * nh[c] + R * (cos(phi) * g->eR[c] + sin(phi) * eP[c]);
+                for (int c = 0; c < 3; c++) dd[c] = pq[c] - D[c];
+                if (norm3(dd) > rt) continue; /* no node can be in the support */
+                ring += node_sum(p, A, g, d1, d2, w, nn, pq, &e0);
+            }
+            acc += M[r] * g->r0 * g->r0 * ring * h / (2.0 * OR_PI);
+        }
+        I_out[q] = acc;
+        if (E_out) E_out[q] = e0;
+    }
+    free(d1); free(d2); free(w); free(beta); free(Pv); free(DWv); free(G);
+}
+
+/* Reciprocal-space intensity at arbitrary points (no Lorentz factor):
+ *   I(S) = sum_r M_r r0^2 sum_k w_k prod_i K_i(a_i . (S - s_k)). */
+void or_point(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_pt,
+              const double *pts, double *I_out) {
+    double A[9], As[9];
+    or_basis(p->cell, A, As);
+    double bh[3], nh[3], uh[3], vh[3];
+    detector_frame(p, bh, nh, uh, vh);
+    int nn = p->n_nodes * p->n_nodes;
+    double *d1 = malloc(sizeof(double) * nn), *d2 = malloc(sizeof(double) * nn), *w = malloc(sizeof(double) * nn);
+    or_nodes(p, d1, d2, w, NULL, NULL);
+    double *beta = malloc(sizeof(double) * 3 * (n_refl > 0 ? n_refl : 1));
+    double *Pv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    double *DWv = malloc(sizeof(double) * (n_refl > 0 ? n_refl : 1));
+    or_refl_scalars(p, n_refl, hkl, beta, Pv, DWv);
+    refl_geo *G = malloc(sizeof(refl_geo) * (n_refl > 0 ? n_refl : 1));
+    build_refl_geo(p, A, As, nh, bh, n_refl, hkl, beta, G);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int32_t q = 0; q < n_pt; q++) {
+        double acc = 0.0;
+        for (int32_t r = 0; r < n_refl; r++)
+            acc += M[r] * G[r].r0 * G[r].r0 * node_sum(p, A, &G[r], d1, d2, w, nn, pts + 3 * (size_t)q, NULL);
+        I_out[q] = acc;
     }
     free(d1); free(d2); free(w); free(beta); free(Pv); free(DWv); free(G);
 }
