@@ -200,6 +200,32 @@ int fdx_pattern(int32_t n_models, const fdx_problem *const *probs, float *const 
  */
 int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream);
 
+/* Cap on the azimuth points per reflection of the ring average. */
+#define FDX_RING_MAX_N 1024
+
+/* Bytes of workspace fdx_ring / fdx_ring_evals need. */
+size_t fdx_ring_workspace_size(const fdx_problem *prob);
+
+/*
+ * fdx_ring -- the ring-integrated cylindrical average (Eq. cyl-average), the
+ * other projection the paper describes: every pixel's value is the average of
+ * the reciprocal-space intensity over the ring of its (R, Z) about the fiber
+ * axis, with no Lorentz factor,
+ *   I_pix = sum_hkl M r0^2 (1/2pi) int dphi sum_k w_k prod_i K_i(a_i . (p(phi) - s_k)),
+ *   p(phi) = Z n + R (cos(phi) e_R + sin(phi) e_P),  e_P = n x e_R(D),
+ * by the midpoint rule in phi over [-Phi_r, Phi_r] with N_r points per
+ * reflection: Phi_r is the half-width outside which the ring stays farther
+ * than rho_tot = rho_B + sqrt(2) r0 T from D, N_r = clamp(ceil(2 Phi_r /
+ * dphi), 4, FDX_RING_MAX_N) with dphi = w_min / (4 (R_D + rho_tot)) and
+ * w_min = min_i beta_i / |a_i|.  image is [n_y][n_x] float (device).  Every
+ * lineshape.  Asynchronous.  The cost is about N_r times that of fdx_pattern.
+ */
+int fdx_ring(const fdx_problem *prob, float *image, void *workspace, size_t ws_bytes, void *stream);
+
+/* fdx_ring_evals -- per-pixel in-support (reflection, azimuth point, node)
+ * term counts of fdx_ring, [n_y][n_x] int32 (device). */
+int fdx_ring_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream);
+
 /* Bytes of workspace fdx_scatter / fdx_scatter_evals need. */
 size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples);
 

@@ -127,7 +127,7 @@ void cross3(const double *x, const double *y, double *z) {
 // Queue the set-up kernels (pixel geometry, node table, reflection records)
 // for one problem and fill the pattern kernel's parameters.
 int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes,
-                  double *nodes64 = nullptr, double *frames = nullptr) {
+                  double *nodes64 = nullptr, double *frames = nullptr, float *ring = nullptr) {
     const Layout L = layout_for(p);
     double A[9], As[9];
     cell_basis(p->cell, A, As);
@@ -167,6 +167,9 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
     rp.recs = reinterpret_cast<float *>(ws + L.recs);
     rp.reach = reinterpret_cast<float4 *>(ws + L.reach);
     rp.frames = frames;
+    rp.ring = ring;
+    rp.ring_max_n = FDX_RING_MAX_N;
+    for (int q = 0; q < 3; ++q) rp.alen3[q] = rp.alen[q];
     if (launch_refl_setup(rp, st) != cudaSuccess) return FDX_ERR_CUDA;
 
     P.nx = p->geom.n_x, P.ny = p->geom.n_y, P.n_refl = p->n_refl, P.n_nodes = p->br.n_nodes;
@@ -347,6 +350,34 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     if (image && cudaMemsetAsync(S.img64, 0, sizeof(double) * npx, st) != cudaSuccess) return FDX_ERR_CUDA;
     if (count && cudaMemsetAsync(count, 0, sizeof(int64_t), st) != cudaSuccess) return FDX_ERR_CUDA;
     if (launch_scatter(S, prob->br.lineshape, count != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
+    return FDX_OK;
+}
+
+// Ring-average workspace: the pattern layout followed by the ring records.
+size_t ring_layout(const fdx_problem *p, size_t *ring_off) {
+    size_t off = layout_for(p).total;
+    *ring_off = off;
+    off += align_up(sizeof(float) * RING_REC * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    return off;
+}
+
+int run_ring(const fdx_problem *prob, float *image, int32_t *counts, void *workspace, size_t ws_bytes, void *stream) {
+    int rc = validate_problem(prob);
+    if (rc) return rc;
+    if (!image && !counts) return FDX_ERR_ARG;
+    size_t roff = 0;
+    const size_t need = ring_layout(prob, &roff);
+    if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    char *ws = static_cast<char *>(workspace);
+    RingParams R;
+    memset(&R, 0, sizeof R);
+    rc = setup_pattern(prob, ws, st, R.P, false, nullptr, nullptr, reinterpret_cast<float *>(ws + roff));
+    if (rc) return rc;
+    R.P.image = image;
+    R.P.counts = counts;
+    R.ring = reinterpret_cast<const float *>(ws + roff);
+    if (launch_ring(R, prob->br.lineshape, counts != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
 }
 
@@ -858,6 +889,22 @@ int fdx_loss(int64_t n_px, const float *I, const float *I_target, const float *m
     lp.loss = loss_out;
     if (launch_loss(lp, static_cast<cudaStream_t>(stream)) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
+}
+
+size_t fdx_ring_workspace_size(const fdx_problem *prob) {
+    if (!prob) return 0;
+    size_t roff = 0;
+    return ring_layout(prob, &roff);
+}
+
+int fdx_ring(const fdx_problem *prob, float *image, void *workspace, size_t ws_bytes, void *stream) {
+    if (!image) return FDX_ERR_ARG;
+    return run_ring(prob, image, nullptr, workspace, ws_bytes, stream);
+}
+
+int fdx_ring_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream) {
+    if (!counts) return FDX_ERR_ARG;
+    return run_ring(prob, nullptr, counts, workspace, ws_bytes, stream);
 }
 
 size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples) {

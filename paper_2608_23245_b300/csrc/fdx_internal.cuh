@@ -158,6 +158,20 @@ struct ReflSetupParams {
     float *recs;
     float4 *reach;
     double *frames;       // may be null: [n_refl][12] (S^, e1, e2, r0, rho_B, 0) for the scatter form
+    float *ring;          // may be null: [n_refl][RING_REC] ring-average record
+    double alen3[3];      // |a_i| (ring-average step rule)
+    int ring_max_n;       // cap on the ring-average azimuth points per reflection
+};
+
+// Ring-average record per reflection (fdx_ring.cu): e_P = n x e_R.
+enum RingField {
+    RING_TFR = 0,   // e_P . (S^, e1, e2) / r0, hi[3] then lo[3]
+    RING_AT = 6,    // a_i . e_P
+    RING_PHI = 9,   // window half-width Phi_r, hi, lo
+    RING_N = 11,    // azimuth points N_r (exact integer as float)
+    RING_HW = 12,   // quadrature weight (2 Phi_r / N_r) / (2 pi)
+    RING_RT = 13,   // rho_tot = rho_B + sqrt(2) r0 T
+    RING_REC = 16
 };
 
 struct NodeParams {
@@ -230,6 +244,13 @@ struct ScatterParams {
     unsigned long long *count;  // evaluation count (count mode)
 };
 cudaError_t launch_scatter(const ScatterParams &p, int lineshape, bool count_mode, cudaStream_t s);
+
+// Ring-integrated cylindrical average (fdx_ring.cu).
+struct RingParams {
+    PatternParams P;          // pixel geometry, records, nodes; P.image / P.counts are the outputs
+    const float *ring;        // [n_refl][RING_REC]
+};
+cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);
 size_t sf_bind(SFParams *p, char *ws, int n_atoms, int n_refl, int max_split);
 

@@ -1,0 +1,159 @@
+// Ring-integrated cylindrical average (Eq. cyl-average): the pixel value is
+// the average of the reciprocal-space intensity over the ring of the pixel's
+// (R, Z) about the fiber axis, with no Lorentz factor,
+//   I = sum_hkl M r0^2 (1/2pi) int dphi sum_k w_k prod_i K_i(a_i . (p(phi) - s_k)),
+//   p(phi) = Z n + R (cos(phi) e_R + sin(phi) e_P),  e_P = n x e_R,
+// with phi measured from the reflection's meridional half-plane, by the
+// per-reflection midpoint rule over [-Phi_r, Phi_r] (N_r points; window and
+// step from the reflection set-up kernel, reading R21).
+//
+// Work decomposition: as the gather form, a warp owns an 8 x 4 pixel patch
+// and scans the reflections with the reach test (the ring points of a pixel
+// have its |S| and polar angle, so the test is exact for every azimuth); for
+// each azimuth point of a surviving reflection the patch's query points are
+// the pixels' ring points p(phi_j), evaluated by eval_core (block culling,
+// staging, packed walk) against a reference at the patch's centre pixel.  The
+// azimuth points' sin(phi_j) and 1 - cos(phi_j) are computed in FP64, 32 at a
+// time (one per lane), and broadcast; points whose ring arc cannot reach the
+// support for any pixel of the patch are skipped.
+#include "fdx_pair.cuh"
+
+namespace fdx {
+
+static constexpr int RING_NODE_BUF = 288;
+
+template <int LS, int MODE>
+__device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0, float4 *buf, float4 *bsc,
+                                          float4 *bsc2, float *rec, int lane) {
+    const PatternParams &P = RP.P;
+    const PatchPix<1> g = load_patch<1>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
+    float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
+    if (g.valid[0]) {
+        const float rlen = sqrtf(g.Rh[0] * g.Rh[0] + g.Zh[0] * g.Zh[0]), psi = atan2f(g.Rh[0], g.Zh[0]);
+        rmin = rmax = rlen, pmin = pmax = psi;
+    }
+    rmin = warp_min(rmin), rmax = warp_max(rmax), pmin = warp_min(pmin), pmax = warp_max(pmax);
+    ff acc = {0.0f, 0.0f};
+    int32_t cnt = 0;
+
+    for (int base = 0; base < P.n_refl; base += 32) {
+        bool cand = false;
+        const int rr = base + lane;
+        if (rr < P.n_refl) {
+            const float4 q = P.reach[rr];
+            cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - q.w <= pmax) && (q.z + q.w >= pmin);
+        }
+        unsigned mask = __ballot_sync(FDX_FULL_MASK, cand);
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int r = base + b;
+            load_record(P.recs, r, rec, lane);
+            const float *gr = RP.ring + (size_t)r * RING_REC;
+            const int N = (int)gr[RING_N];
+            const double Phi = (double)gr[RING_PHI] + (double)gr[RING_PHI + 1];
+            const double hstep = 2.0 * Phi / N;
+            const float hw = gr[RING_HW], rt = gr[RING_RT];
+            float AT[3], tfrh[3], tfrl[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) AT[k] = gr[RING_AT + k], tfrh[k] = gr[RING_TFR + k], tfrl[k] = gr[RING_TFR + 3 + k];
+            // this lane's pixel relative to D (float, bounds and reach of the arc)
+            const float dZ = (g.Zh[0] - rec[REC_ZD]) + (g.Zl[0] - rec[REC_ZD + 1]);
+            const float dR = (g.Rh[0] - rec[REC_RD]) + (g.Rl[0] - rec[REC_RD + 1]);
+            const float RDf = rec[REC_RD], Rf = g.Rh[0];
+            const float rt2 = rt * rt * (1.0f + 1e-4f) + 1e-12f;
+            const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
+            const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
+            const ff RD = {rec[REC_RD], rec[REC_RD + 1]}, Rr = {g.Rrh, g.Rrl};
+            ff pair = {0.0f, 0.0f};
+            for (int j0 = 0; j0 < N; j0 += 32) {
+                // azimuth points j0 .. j0 + 31, one per lane, in FP64
+                float sh = 0.f, sl = 0.f, oh = 0.f, ol = 0.f;
+                {
+                    const double phi = -Phi + (j0 + lane + 0.5) * hstep;
+                    const double sh2 = sin(0.5 * phi);
+                    split_double(sin(phi), sh, sl);
+                    split_double(2.0 * sh2 * sh2, oh, ol);  // 1 - cos(phi) without cancellation
+                }
+                const int je = min(32, N - j0);
+                for (int jj = 0; jj < je; ++jj) {
+                    const ff sp = {__shfl_sync(FDX_FULL_MASK, sh, jj), __shfl_sync(FDX_FULL_MASK, sl, jj)};
+                    const ff om = {__shfl_sync(FDX_FULL_MASK, oh, jj), __shfl_sync(FDX_FULL_MASK, ol, jj)};
+                    const float cp = 1.0f - om.hi;
+                    // |p(phi) - D|^2 = dZ^2 + dR^2 + 2 R R_D (1 - cos phi): skip arcs out of reach
+                    const bool nearp = g.valid[0] && fmaf(dZ, dZ, fmaf(dR, dR, 2.0f * Rf * RDf * om.hi)) <= rt2;
+                    if (!__any_sync(FDX_FULL_MASK, nearp)) continue;
+                    QueryPts<1> q;
+                    q.valid[0] = g.valid[0];
+                    // p - D = dZ n + (dR cos phi - R_D (1 - cos phi)) e_R + R sin phi e_P
+                    const float er = fmaf(dR, cp, -RDf * om.hi), et = Rf * sp.hi;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        q.P[0][k] = fmaf(dZ, rec[REC_NFR + k], fmaf(er, rec[REC_EFR + k], et * tfrh[k]));
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+                        q.tau[0][i] = g.valid[0]
+                                          ? fmaf(g.dZl[0], P.AZ[i], g.dRl[0] * fmaf(cp, rec[REC_AR + i], sp.hi * AT[i]))
+                                          : 1.0e4f;
+                    // reference (p_ref - D)/r0 in the reflection frame, float-float
+                    const ff cpf = ff_add(ff{1.0f, 0.0f}, ff{-om.hi, -om.lo});
+                    const ff erf_ = ff_sub(ff_mul(dRr, cpf), ff_mul(RD, om));
+                    const ff etf = ff_mul(Rr, sp);
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        q.dP[k] = ff_add(ff_add(ff_mul(dZr, ff{rec[REC_NFR + k], rec[REC_NFR + 3 + k]}),
+                                                ff_mul(erf_, ff{rec[REC_EFR + k], rec[REC_EFR + 3 + k]})),
+                                         ff_mul(etf, ff{tfrh[k], tfrl[k]}));
+                    PairAcc pa[1];
+                    clear(pa[0]);
+                    if (!eval_core<LS, MODE, RING_NODE_BUF, 1>(P, q, rec, buf, nullptr, bsc, bsc2, lane, pa)) continue;
+                    if (MODE == MODE_CNT)
+                        cnt += pa[0].cnt;
+                    else
+                        pair = ff_add(pair, pa[0].s0);
+                }
+            }
+            if (MODE != MODE_CNT) acc = ff_add(acc, ff_mul_f(pair, rec[REC_FR] * hw));
+        }
+    }
+    if (!g.valid[0]) return;
+    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
+    const size_t out = (size_t)py * P.nx + px;
+    if (MODE == MODE_CNT)
+        P.counts[out] = cnt;
+    else
+        P.image[out] = acc.hi + acc.lo;
+}
+
+template <int LS, int MODE>
+__global__ void __launch_bounds__(PAIR_WARPS * 32, 4) ring_kernel(RingParams RP) {
+    __shared__ float4 s_nodes[PAIR_WARPS][RING_NODE_BUF];
+    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? RING_NODE_BUF : 1];
+    __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? RING_NODE_BUF / 2 : 1];
+    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * 8 + (warp >> 1) * 4;
+    if (px0 >= RP.P.nx || py0 >= RP.P.ny) return;
+    ring_warp<LS, MODE>(RP, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+}
+
+template <int LS>
+static void launch_ring_ls(const RingParams &p, bool count_mode, cudaStream_t s) {
+    dim3 grid((p.P.nx + 15) / 16, (p.P.ny + 7) / 8);
+    if (count_mode)
+        ring_kernel<LS, MODE_CNT><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
+    else
+        ring_kernel<LS, MODE_FWD><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
+}
+
+cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+    if (lineshape == FDX_LINESHAPE_HOSEMANN)
+        launch_ring_ls<FDX_LINESHAPE_HOSEMANN>(p, count_mode, s);
+    else if (lineshape == FDX_LINESHAPE_GAUSS)
+        launch_ring_ls<FDX_LINESHAPE_GAUSS>(p, count_mode, s);
+    else
+        launch_ring_ls<FDX_LINESHAPE_SINC>(p, count_mode, s);
+    return cudaGetLastError();
+}
+
+}  // namespace fdx

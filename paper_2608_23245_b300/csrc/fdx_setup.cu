@@ -288,6 +288,33 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
         o[REC_DBF + i] = beta[i] < 1.0 ? (float)(2.0 * beta[i] / (1.0 - beta[i] * beta[i])) : 0.0f;
     }
     o[REC_M] = (float)M;
+    if (p.ring) {
+        // ring-average record (Eq. cyl-average; azimuth rule of reading R21)
+        float *g = p.ring + (size_t)r * RING_REC;
+        const double eP[3] = {p.nh[1] * eR[2] - p.nh[2] * eR[1], p.nh[2] * eR[0] - p.nh[0] * eR[2],
+                              p.nh[0] * eR[1] - p.nh[1] * eR[0]};
+        for (int q = 0; q < 3; ++q) split_double(dot3(eP, frame[q]) / r0, g[RING_TFR + q], g[RING_TFR + 3 + q]);
+        double w_min = 1e300;
+        for (int i = 0; i < 3; ++i) {
+            g[RING_AT + i] = (float)dot3(p.A + 3 * i, eP);
+            w_min = fmin(w_min, beta[i] / p.alen3[i]);
+        }
+        const double rt = rhoB + sqrt(2.0) * r0 * p.T;
+        double ph = FDX_PI;
+        const double inner = RD - rt;
+        if (inner > 0.0) {
+            const double x = rt / (2.0 * sqrt(inner * RD));
+            if (x < 1.0) ph = 2.0 * asin(x);
+        }
+        double nr = ceil(2.0 * ph / (w_min / (4.0 * (RD + rt))));
+        if (!(nr >= 4.0)) nr = 4.0;
+        if (nr > (double)p.ring_max_n) nr = (double)p.ring_max_n;
+        split_double(ph, g[RING_PHI], g[RING_PHI + 1]);
+        g[RING_N] = (float)nr;
+        g[RING_HW] = (float)(2.0 * ph / nr / (2.0 * FDX_PI));
+        g[RING_RT] = (float)rt;
+        g[14] = g[15] = 0.0f;
+    }
     if (p.frames) {
         double *fr64 = p.frames + (size_t)r * 12;
         for (int q = 0; q < 3; ++q) fr64[q] = Sh[q], fr64[3 + q] = e1[q], fr64[6 + q] = e2[q];

@@ -83,6 +83,10 @@ def lib():
             L.fdx_pattern.argtypes = [C.c_int32, C.POINTER(C.POINTER(Problem)), C.POINTER(C.c_void_p), C.c_void_p,
                                       C.c_size_t, C.c_void_p]
             L.fdx_pattern_evals.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.fdx_ring_workspace_size.restype = C.c_size_t
+            L.fdx_ring_workspace_size.argtypes = [C.POINTER(Problem)]
+            L.fdx_ring.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+            L.fdx_ring_evals.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
             L.fdx_scatter_workspace_size.restype = C.c_size_t
             L.fdx_scatter_workspace_size.argtypes = [C.POINTER(Problem), C.c_int32]
             L.fdx_scatter.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -273,6 +277,29 @@ def fdx_pattern_evals(problem, counts, workspace=None, stream=None):
     return counts
 
 
+def fdx_ring_workspace_size(problem) -> int:
+    return int(lib().fdx_ring_workspace_size(C.byref(problem)))
+
+
+def fdx_ring(problem, image, workspace=None, stream=None):
+    """Ring-integrated cylindrical average into image [n_y, n_x] float32 (device)."""
+    import torch
+    if workspace is None:
+        workspace = torch.empty(fdx_ring_workspace_size(problem), dtype=torch.uint8, device=image.device)
+    _check(lib().fdx_ring(C.byref(problem), _ptr(image), _ptr(workspace), int(workspace.numel()), _stream(stream)),
+           "fdx_ring")
+    return image
+
+
+def fdx_ring_evals(problem, counts, workspace=None, stream=None):
+    import torch
+    if workspace is None:
+        workspace = torch.empty(fdx_ring_workspace_size(problem), dtype=torch.uint8, device=counts.device)
+    _check(lib().fdx_ring_evals(C.byref(problem), _ptr(counts), _ptr(workspace), int(workspace.numel()),
+                                _stream(stream)), "fdx_ring_evals")
+    return counts
+
+
 def fdx_scatter_workspace_size(problem, n_samples: int) -> int:
     return int(lib().fdx_scatter_workspace_size(C.byref(problem), int(n_samples)))
 
@@ -340,6 +367,18 @@ class Simulation:
         counts = torch.empty_like(self.image, dtype=torch.int32)
         fdx_pattern_evals(self.prob, counts, self.ws, stream)
         return counts
+
+    def ring(self, image=None, workspace=None, stream=None):
+        """Structure factors (for M) must have been computed; ring-average image."""
+        import torch
+        if image is None:
+            image = torch.empty_like(self.image)
+        return fdx_ring(self.prob, image, workspace, stream)
+
+    def ring_evals(self, workspace=None, stream=None):
+        import torch
+        counts = torch.empty_like(self.image, dtype=torch.int32)
+        return fdx_ring_evals(self.prob, counts, workspace, stream)
 
     def scatter(self, samples, image=None, workspace=None, stream=None):
         """Structure factors (for M) must have been computed; scatter-form image."""

@@ -1,0 +1,55 @@
+"""Ring-integrated cylindrical average on the GPU (fdx_ring) against the FP64
+oracle, full images of reduced detectors, every lineshape and a tilted fiber.
+Gate: the pattern tolerances; in-support term counts within 1e-4 (a node at
+the edge of the support is a floating-point decision)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_2608_23245_b300 import workloads as W
+from _common import L2_REL, MAX_REL, api_precision, parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2608_23245_b300 import _build, fdx
+    _build.build()
+    return fdx
+
+
+def _small(make):
+    p = make()
+    return replace(p, geom=replace(p.geom, n_x=30, n_y=24, pixel=p.geom.pixel * p.geom.n_x / 30),
+                   br=replace(p.br, n_nodes=16))
+
+
+@pytest.mark.parametrize("make", [W.small_helix, W.small_gauss, W.small_tilted, W.small_sinc, W.small_lorentz])
+def test_ring_matches_oracle(gpu, orc, make):
+    import torch
+    p = api_precision(_small(make))
+    sim = gpu.Simulation(p)
+    sim.structure_factors()
+    img = sim.ring().cpu().numpy().reshape(-1)
+    cnt = sim.ring_evals().cpu().numpy().reshape(-1)
+    torch.cuda.synchronize()
+    hkl = sim.hkl_host
+    I, E = orc.ring(p, hkl, orc.intensities_M(p, hkl))
+    assert I.max() > 0
+    mr, l2 = parity(img, I)
+    assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
+    assert abs(int(cnt.sum()) - int(E.sum())) <= 1e-4 * E.sum()
+
+
+def test_ring_mirror_symmetry_gpu(gpu):
+    import torch
+    p = api_precision(_small(W.small_helix))
+    sim = gpu.Simulation(p)
+    sim.structure_factors()
+    img = sim.ring().cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(img - img[:, ::-1])) <= MAX_REL * img.max()
