@@ -257,6 +257,40 @@ def large_measurements(g=0.01, reps=2, roi=128):
             "fp32_over_plain_fp64_roi": t_roi64 / t_roi32, "roi_max_rel_diff_fp32_vs_fp64": rel}
 
 
+def ring_measurements(roi=128, reps=2):
+    """Ring-integrated cylindrical average (Eq. cyl-average) on the central
+    roi x roi pixels of the headline workload (same pixel size): evaluations
+    per second, and the time of the same pixels by the default gather form."""
+    import torch
+    from dataclasses import replace
+    from paper_2608_23245_b300 import fdx, workloads as W
+    p = W.config1()
+    p = replace(p, geom=replace(p.geom, n_x=roi, n_y=roi))
+    sim = fdx.Simulation(p)
+    sim.structure_factors()
+    ws = torch.empty(fdx.fdx_ring_workspace_size(sim.prob), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(sim.image)
+    E = int(sim.ring_evals(ws).to(torch.int64).sum().item())
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    t = timed(lambda: sim.ring(out, ws))
+    tg = timed(sim.pattern)
+    return {"workload": "helix config, central %dx%d pixels (0.1 mm), 64^2 nodes, azimuth rule of the ring average"
+                        % (roi, roi),
+            "evals": E, "ms": 1e3 * t, "evals_per_s": E / t, "gather_ms_same_pixels": 1e3 * tg,
+            "frac_of_fp32_peak": FLOPS_PER_EVAL * E / t / 1e12 / fp32_peak_tflops(_peaks().get("sm_max_mhz", 2032.0))}
+
+
 def scatter_measurements(grid=(16, 16, 16), reps=2):
     """Scatter form (the paper's own pipeline) on the headline workload:
     n_r x n_1 x n_2 stratified samples per reflection (4,096 by default; the
@@ -425,6 +459,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--no-scatter", action="store_true")
+    ap.add_argument("--no-ring", action="store_true")
     ap.add_argument("--batch-models", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -533,6 +568,8 @@ def main():
         line["large"] = large_measurements()
     if not args.no_scatter:
         line["scatter"] = scatter_measurements()
+    if not args.no_ring:
+        line["ring"] = ring_measurements()
     if not args.no_batch:
         line["batch"] = batch_measurements(args.batch_models)
     if not args.no_cpu_baseline:
