@@ -558,7 +558,10 @@ def main():
                               "%.0f MHz (FP32 FMA pipe)" % (FLOPS_PER_EVAL, peaks.get("sm_max_mhz", 2032.0)),
                      "pattern_ms": 1e3 * pat_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 7 * args.steps,
+        # per step: structure factors (pack, group count, group scan, group
+        # scatter, main, reduce) + pattern call (pixel geometry, nodes,
+        # reflection set-up, pattern kernel)
+        "gpu_launches": 10 * args.steps,
         "clocks": clocks,
         "wall_s": wall,
     }
