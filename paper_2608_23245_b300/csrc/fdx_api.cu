@@ -353,11 +353,23 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     return FDX_OK;
 }
 
-// Ring-average workspace: the pattern layout followed by the ring records.
-size_t ring_layout(const fdx_problem *p, size_t *ring_off) {
+// Warps per 8 x 4 patch of the ring average: about 16384 warps in all (some
+// seven waves of 16 resident warps on each of 148 SMs), at most 64.
+int ring_split(const fdx_problem *p) {
+    const long long patches = (long long)((p->geom.n_x + 7) / 8) * ((p->geom.n_y + 3) / 4);
+    const long long s = (16384 + patches - 1) / (patches > 0 ? patches : 1);
+    return (int)(s < 1 ? 1 : (s > 64 ? 64 : s));
+}
+
+// Ring-average workspace: the pattern layout followed by the ring records and,
+// when the azimuth points are split, the partial images.
+size_t ring_layout(const fdx_problem *p, size_t *ring_off, size_t *part_off = nullptr) {
     size_t off = layout_for(p).total;
     *ring_off = off;
     off += align_up(sizeof(float) * RING_REC * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    if (part_off) *part_off = off;
+    const int S = ring_split(p);
+    if (S > 1) off += align_up(sizeof(float2) * (size_t)S * p->geom.n_x * p->geom.n_y);
     return off;
 }
 
@@ -365,8 +377,8 @@ int run_ring(const fdx_problem *prob, float *image, int32_t *counts, void *works
     int rc = validate_problem(prob);
     if (rc) return rc;
     if (!image && !counts) return FDX_ERR_ARG;
-    size_t roff = 0;
-    const size_t need = ring_layout(prob, &roff);
+    size_t roff = 0, poff = 0;
+    const size_t need = ring_layout(prob, &roff, &poff);
     if (!workspace || ws_bytes < need || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     char *ws = static_cast<char *>(workspace);
@@ -377,6 +389,8 @@ int run_ring(const fdx_problem *prob, float *image, int32_t *counts, void *works
     R.P.image = image;
     R.P.counts = counts;
     R.ring = reinterpret_cast<const float *>(ws + roff);
+    R.n_split = ring_split(prob);
+    R.partial = R.n_split > 1 ? reinterpret_cast<float2 *>(ws + poff) : nullptr;
     if (launch_ring(R, prob->br.lineshape, counts != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
 }

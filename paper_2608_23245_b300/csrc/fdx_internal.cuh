@@ -249,6 +249,8 @@ cudaError_t launch_scatter(const ScatterParams &p, int lineshape, bool count_mod
 struct RingParams {
     PatternParams P;          // pixel geometry, records, nodes; P.image / P.counts are the outputs
     const float *ring;        // [n_refl][RING_REC]
+    int n_split;              // azimuth points of a reflection are dealt round-robin to n_split warps per patch
+    float2 *partial;          // [n_split][n_y][n_x] float-float partial sums (int32 in count mode); null if n_split == 1
 };
 cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);

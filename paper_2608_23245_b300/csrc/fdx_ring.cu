@@ -15,7 +15,10 @@
 // staging, packed walk) against a reference at the patch's centre pixel.  The
 // azimuth points' sin(phi_j) and 1 - cos(phi_j) are computed in FP64, 32 at a
 // time (one per lane), and broadcast; points whose ring arc cannot reach the
-// support for any pixel of the patch are skipped.
+// support for any pixel of the patch are skipped.  A small detector region has
+// too few patches to fill the GPU, so the points of every reflection are dealt
+// round-robin to n_split warps per patch (grid z); each writes a float-float
+// partial image and a second kernel sums them in split order.
 #include "fdx_pair.cuh"
 
 namespace fdx {
@@ -66,16 +69,19 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
             const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
             const ff RD = {rec[REC_RD], rec[REC_RD + 1]}, Rr = {g.Rrh, g.Rrl};
             ff pair = {0.0f, 0.0f};
-            for (int j0 = 0; j0 < N; j0 += 32) {
-                // azimuth points j0 .. j0 + 31, one per lane, in FP64
+            // this warp's share of the points: j = z + S m, m = 0, 1, ...
+            const int S = RP.n_split, z = blockIdx.z;
+            const int nz = N > z ? (N - z + S - 1) / S : 0;
+            for (int m0 = 0; m0 < nz; m0 += 32) {
+                // azimuth points of m0 .. m0 + 31, one per lane, in FP64
                 float sh = 0.f, sl = 0.f, oh = 0.f, ol = 0.f;
                 {
-                    const double phi = -Phi + (j0 + lane + 0.5) * hstep;
+                    const double phi = -Phi + (z + (double)S * (m0 + lane) + 0.5) * hstep;
                     const double sh2 = sin(0.5 * phi);
                     split_double(sin(phi), sh, sl);
                     split_double(2.0 * sh2 * sh2, oh, ol);  // 1 - cos(phi) without cancellation
                 }
-                const int je = min(32, N - j0);
+                const int je = min(32, nz - m0);
                 for (int jj = 0; jj < je; ++jj) {
                     const ff sp = {__shfl_sync(FDX_FULL_MASK, sh, jj), __shfl_sync(FDX_FULL_MASK, sl, jj)};
                     const ff om = {__shfl_sync(FDX_FULL_MASK, oh, jj), __shfl_sync(FDX_FULL_MASK, ol, jj)};
@@ -119,10 +125,36 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
     if (!g.valid[0]) return;
     const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
     const size_t out = (size_t)py * P.nx + px;
-    if (MODE == MODE_CNT)
+    if (RP.partial) {
+        const size_t slot = (size_t)blockIdx.z * P.nx * P.ny + out;
+        if (MODE == MODE_CNT)
+            reinterpret_cast<int32_t *>(RP.partial)[slot] = cnt;
+        else
+            RP.partial[slot] = make_float2(acc.hi, acc.lo);
+    } else if (MODE == MODE_CNT) {
         P.counts[out] = cnt;
-    else
+    } else {
         P.image[out] = acc.hi + acc.lo;
+    }
+}
+
+// Sum of the n_split partial results of a pixel, in split order.
+__global__ void ring_reduce_kernel(const float2 *partial, int n_split, int npix, float *image, int32_t *counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npix) return;
+    if (counts) {
+        const int32_t *pc = reinterpret_cast<const int32_t *>(partial);
+        int32_t c = 0;
+        for (int z = 0; z < n_split; ++z) c += pc[(size_t)z * npix + i];
+        counts[i] = c;
+    } else {
+        ff a = {0.0f, 0.0f};
+        for (int z = 0; z < n_split; ++z) {
+            const float2 v = partial[(size_t)z * npix + i];
+            a = ff_add(a, ff{v.x, v.y});
+        }
+        image[i] = a.hi + a.lo;
+    }
 }
 
 template <int LS, int MODE>
@@ -139,11 +171,17 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) ring_kernel(RingParams RP)
 
 template <int LS>
 static void launch_ring_ls(const RingParams &p, bool count_mode, cudaStream_t s) {
-    dim3 grid((p.P.nx + 15) / 16, (p.P.ny + 7) / 8);
+    dim3 grid((p.P.nx + 15) / 16, (p.P.ny + 7) / 8, p.n_split);
     if (count_mode)
         ring_kernel<LS, MODE_CNT><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
     else
         ring_kernel<LS, MODE_FWD><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
+    if (p.partial) {
+        const int npix = p.P.nx * p.P.ny;
+        ring_reduce_kernel<<<(npix + 255) / 256, 256, 0, s>>>(p.partial, p.n_split, npix,
+                                                              count_mode ? nullptr : p.P.image,
+                                                              count_mode ? p.P.counts : nullptr);
+    }
 }
 
 cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s) {
