@@ -49,9 +49,10 @@ FLOPS_PER_EVAL = 55
 # form factor (1); two accumulating FMAs (4): 29 -> 30.  The kernel evaluates
 # groups of four consecutive-l reflections: per group and atom, remainder
 # scale (1), r^2 (1), polynomials (19), three complex rotations (18), and per
-# term exponent (2), exp2 (1), form factor (1), accumulation (4): 71 / 4.
+# term exponent (2), exp2 (1), accumulation (4): 67 / 4; the form factor
+# multiplies each 64-atom chunk's sum (2 per term and chunk): + 2 / 64.
 SF_FLOPS_DIRECT_PER_TERM = 30
-SF_FLOPS_PER_TERM = 17.75
+SF_FLOPS_PER_TERM = 16.78125
 
 
 def _peaks():
@@ -245,7 +246,7 @@ def large_measurements(g=0.01, reps=2, roi=128):
             "sf_terms_per_s": terms / t_sf, "sf_ms": 1e3 * t_sf,
             "sf_roofline": {"bound": "alu", "achieved": sf_tflops, "peak": peak, "unit": "TFLOP/s",
                             "frac": sf_tflops / peak,
-                            "basis": "%.2f executed FP32 flops per atom-reflection term (groups of four "
+                            "basis": "%.5g executed FP32 flops per atom-reflection term (groups of four "
                                      "consecutive-l reflections share one sin/cos per atom; exp2 counted as one)"
                                      % SF_FLOPS_PER_TERM,
                             "direct_equivalent": {"flops_per_term": SF_FLOPS_DIRECT_PER_TERM, "achieved": sf_direct,

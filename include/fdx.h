@@ -160,8 +160,9 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
  * has no counterpart: this is a deployment convenience of the library.
  *   - No workspace argument: the kernels' scratch is a fixed array of
  *     FDX_NOALLOC_SF_SCRATCH_BYTES (8 MiB) in device memory that every GPU
- *     loading libfdx holds until the process exits.  It must fit 24 bytes per
- *     atom, 4 bytes per reflection, and 16 bytes per reflection per row of
+ *     loading libfdx holds until the process exits.  It must fit 24.25 bytes per
+ *     atom (plus 97 KiB of padding: the kernels keep the atoms sorted by
+ *     element), 4 bytes per reflection, and 16 bytes per reflection per row of
  *     partial sums (the call uses as many rows as fit, at most 64); larger
  *     sizes return FDX_ERR_WORKSPACE before any work is queued.  The call
  *     allocates nothing.

@@ -217,6 +217,10 @@ struct SFParams {
     const uint8_t *elem;
     uint4 *atoms_q;        // packed: X, Y, Z (fixed point), elem
     float2 *atoms_w;       // packed: Bq = -B log2(e)/4, log2(occ)
+    int *elem_off;         // [n_elem + 1] element-sorted copy: first entry of each element, total
+    int *elem_cnt;         // [64] atoms of each element
+    int *acnt;             // [n_achunks][64] atoms of each element per 1024-atom chunk, then their first entries
+    int n_achunks;         // ceil(n_atoms / 1024)
     const int32_t *hkl;
     int *groups;           // [<= n_refl] first reflection of each group (consecutive l, equal h, k)
     int *gblk;             // [n_refl / 1024 + 1] per-block group offsets
@@ -226,6 +230,7 @@ struct SFParams {
     int has_br, intensity_model;
     int e_lo, n_fe, split_base, n_rows;  // element pass and partial rows (set by the launcher)
     double g[3], Bax[3], alen[3];
+    double hx[3], dwc[3];  // pi^2 g_i^2 and -B_i / (4 |a_i|^2) (set by the launcher)
 };
 
 cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);

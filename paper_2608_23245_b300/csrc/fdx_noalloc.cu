@@ -82,9 +82,9 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     }
     if (n_refl == 0) return FDX_OK;
 
-    // Scratch: packed atoms (uint4 + float2 each), the group list of the
-    // reflections (one int each) and one float4 partial per (partial row,
-    // reflection).  Use as many rows as fit, at most 64.
+    // Scratch: packed atoms (uint4 + float2 each, element-sorted and padded),
+    // the group list of the reflections (one int each) and one float4 partial
+    // per (partial row, reflection).  Use as many rows as fit, at most 64.
     const size_t fixed = sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, 0);
     const size_t per_split = sizeof(float4) * (size_t)n_refl;
     if (fixed + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;

@@ -87,6 +87,51 @@ def test_structure_factors_large_subset(gpu, orc):
     assert err.max() <= SF_TOL, err.max()
 
 
+def _many_elements(p, n_elem=48, seed=4811):
+    """p's atoms re-typed over n_elem element types (more than one pass of the
+    form-factor table), a few types left without atoms, occupancies in
+    {0, 0.5, 1}: every element run of the sorted atom list has a ragged tail."""
+    rng = np.random.default_rng(seed)
+    a = p.atoms
+    n = a.n
+    used = np.setdiff1d(np.arange(n_elem), [3, 17, 41, 47])
+    elem = rng.choice(used, size=n).astype(np.uint8)
+    ff = np.concatenate([rng.uniform(0.5, 3.0, (n_elem, 4)), rng.uniform(0.5, 40.0, (n_elem, 4)),
+                         rng.uniform(0.0, 1.0, (n_elem, 1))], axis=1)
+    occ = rng.choice([0.0, 0.5, 1.0], size=n, p=[0.1, 0.2, 0.7])
+    return api_precision(replace(p, atoms=replace(a, elem=elem, ff=ff, occ=occ)))
+
+
+@pytest.mark.parametrize("make", [W.small_helix, W.config1])
+def test_structure_factors_many_elements(gpu, orc, make):
+    """48 element types (two passes of the form-factor table), unused types
+    and partial occupancies, against the oracle with the same tolerance."""
+    import torch
+    p = _many_elements(make())
+    hkl = gpu.fdx_reflections(p.cell, p.d_min)
+    atoms = gpu.DeviceAtoms(p.atoms)
+    F, _ = gpu.fdx_structure_factors(p.cell, atoms, torch.as_tensor(hkl, device="cuda"), p.br)
+    _sync()
+    Fg = F.cpu().numpy().astype(np.float64)
+    Fg = Fg[:, 0] + 1j * Fg[:, 1]
+    Fo = orc.structure_factors(p.cell, p.atoms, hkl)
+    err = np.abs(Fg - Fo) / _amp_scale(p, hkl)
+    assert err.max() <= SF_TOL, err.max()
+
+
+def test_structure_factors_bad_element_is_nan(gpu):
+    """An element index >= n_elem poisons every F with NaN (documented)."""
+    import torch
+    p = api_precision(W.small_helix())
+    elem = p.atoms.elem.copy()
+    elem[37] = p.atoms.ff.shape[0]
+    p = replace(p, atoms=replace(p.atoms, elem=elem))
+    hkl = gpu.fdx_reflections(p.cell, p.d_min)
+    F, _ = gpu.fdx_structure_factors(p.cell, gpu.DeviceAtoms(p.atoms), torch.as_tensor(hkl, device="cuda"), p.br)
+    _sync()
+    assert torch.isnan(F).all()
+
+
 def _gpu_pattern(gpu, p, hkl, M):
     import torch
     hk = torch.as_tensor(np.ascontiguousarray(hkl, np.int32), device="cuda").reshape(-1, 3)
