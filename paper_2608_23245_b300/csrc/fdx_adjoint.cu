@@ -148,6 +148,10 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
     double acc[ADJ_ITEM_VALS];
 #pragma unroll
     for (int k = 0; k < ADJ_ITEM_VALS; ++k) acc[k] = warp_sum_d((double)ia[k].hi + (double)ia[k].lo);
+    // the beta sums were accumulated as sum w / (den_i prod den); subtract the
+    // profile sum for sum (w / prod den) (1/den_i - 1)
+#pragma unroll
+    for (int k = 1; k <= 3; ++k) acc[k] -= acc[0];
     if (lane < ADJ_ITEM_VALS) {
         double o = acc[0];
 #pragma unroll

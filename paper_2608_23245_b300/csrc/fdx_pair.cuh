@@ -166,7 +166,7 @@ __device__ __forceinline__ PatchPix<PPL> load_patch(const float4 *pixgeo, int nx
 
 struct PairAcc {
     ff s0;           // sum of w / prod den (Hosemann) or w * sinc product
-    ff sb[3];        // adjoint: sum of (w / prod den) (1/den_i - 1)
+    ff sb[3];        // adjoint: sum of (w / prod den) / den_i
     ff ss, sg;       // adjoint: sums of dw/dsigma / prod den and dw/dgamma / prod den
     int32_t cnt;     // count mode: in-support terms
 };
@@ -389,7 +389,6 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
         for (int i = 0; i < 3; ++i) la2[i] = f2(la[i]);
     }
     const float inf = __int_as_float(0x7f800000);
-    const float2 neg1 = f2(-1.0f);
     // rearrange n staged nodes at slots [base, base + n) into pairs, 32 nodes
     // (16 pairs) at a time; a pair never straddles two such groups, so reading
     // the group before writing it is enough.  Padding node (odd n): weight 0,
@@ -468,11 +467,12 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     } else {
                         const float2 kv = __fmul2_rn(w, rp);
                         r0[p] = __fadd2_rn(r0[p], kv);
-                        // 1/den_i = (product of the other two) * rp
+                        // kv / den_i = (kv rp) (product of the other two)
+                        const float2 q = __fmul2_rn(kv, rp);
                         const float2 dbc = __fmul2_rn(db, dc), dac = __fmul2_rn(da, dc);
-                        rb0[p] = __ffma2_rn(kv, __ffma2_rn(dbc, rp, neg1), rb0[p]);
-                        rb1[p] = __ffma2_rn(kv, __ffma2_rn(dac, rp, neg1), rb1[p]);
-                        rb2[p] = __ffma2_rn(kv, __ffma2_rn(dab, rp, neg1), rb2[p]);
+                        rb0[p] = __ffma2_rn(q, dbc, rb0[p]);
+                        rb1[p] = __ffma2_rn(q, dac, rb1[p]);
+                        rb2[p] = __ffma2_rn(q, dab, rb2[p]);
                         rss[p] = __ffma2_rn(make_float2(W4.x, W4.y), rp, rss[p]);
                         rsg[p] = __ffma2_rn(make_float2(W4.z, W4.w), rp, rsg[p]);
                     }
