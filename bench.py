@@ -53,6 +53,12 @@ FLOPS_PER_EVAL = 55
 # multiplies each 64-atom chunk's sum (2 per term and chunk): + 2 / 64.
 SF_FLOPS_DIRECT_PER_TERM = 30
 SF_FLOPS_PER_TERM = 16.78125
+# DRAM bytes (read + written) of one forward pattern_kernel<Hosemann> launch
+# of this step, from an ncu --set full capture of it: 18.20 MB read (pixel
+# geometry at 16 B per pixel, reflection records, node tables), 0 written (the
+# 4 MB image stays in L2 during the launch).  Valid only for the kernel as
+# captured: set to None whenever the pattern kernel changes.
+PATTERN_DRAM_BYTES = 18198016
 
 
 def _peaks():
@@ -554,15 +560,16 @@ def main():
                    "l2_flush": "512 MiB write between steps, outside the per-step events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": PATTERN_DRAM_BYTES,
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "basis": "%d algorithmic FP32 flops per in-support eval; peak = 148 SMs x 128 lanes x 2 x "
                               "%.0f MHz (FP32 FMA pipe)" % (FLOPS_PER_EVAL, peaks.get("sm_max_mhz", 2032.0)),
                      "pattern_ms": 1e3 * pat_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        # per step: structure factors (pack, group count, group scan, group
-        # scatter, main, reduce) + pattern call (pixel geometry, nodes,
-        # reflection set-up, pattern kernel)
-        "gpu_launches": 10 * args.steps,
+        # per step: structure factors (group and atom counts, group scan and
+        # atom offsets, group scatter and atom packing, main, reduce) + pattern
+        # call (pixel geometry, nodes, reflection set-up, pattern kernel)
+        "gpu_launches": 9 * args.steps,
         "clocks": clocks,
         "wall_s": wall,
     }
