@@ -412,6 +412,60 @@ def small_triclinic() -> Problem:
     return Problem("small_triclinic", cell, atoms, 3.2, 0.0, br, geom, seed)
 
 
+# ---------------------------------------------------------------------------
+# The paper's model figures with |F| = 1 (Figs. GvL and equator): a hexagonal
+# cell a = b = 10 A, c = 5 A, gamma = 120 deg and a structure factor of one
+# for every reflection.  Neither figure states its remaining parameters; the
+# values below (d >= 2 A, crystallite size, detector) are this project's.
+# ---------------------------------------------------------------------------
+
+FIGURE_CELL = (10.0, 10.0, 5.0, math.pi / 2, math.pi / 2, 2.0 * math.pi / 3.0)
+
+
+def unit_atoms() -> Atoms:
+    """One atom at the origin with f(s) = 1 (all Gaussian amplitudes zero,
+    constant 1), B = 0 and occupancy 1: F_hkl = 1 for every reflection."""
+    ff = np.zeros((1, 9))
+    ff[0, 4:8] = 1.0
+    ff[0, 8] = 1.0
+    return Atoms(frac=np.zeros((1, 3)), B=np.zeros(1), occ=np.ones(1), elem=np.zeros(1, np.uint8), ff=ff)
+
+
+def gvl(kind: str, n_px: int = 511, n_nodes: int = 64, L: float = 150.0) -> Problem:
+    """Fig. GvL: Gaussian (sigma = 3 deg, gamma = 0) or Lorentzian (sigma = 0,
+    gamma = 3 deg) orientation distribution, |F| = 1, Hosemann lineshape with
+    no paracrystal term (g = 0), d >= 2 A, square detector of n_px 0.2 mm
+    pixels at the distance of Eq. SF for 2 A."""
+    if kind not in ("gauss", "lorentz"):
+        raise ValueError("kind is 'gauss' or 'lorentz'")
+    sig, gam = (math.radians(3.0), 0.0) if kind == "gauss" else (0.0, math.radians(3.0))
+    br = Broadening(L=(L, L, L), g=(0.0, 0.0, 0.0), lineshape=LINESHAPE_HOSEMANN,
+                    intensity_model=INTENSITY_HOSEMANN, sigma=sig, gamma=gam, T=patch_extent(sig, gam),
+                    n_nodes=n_nodes)
+    pix = 0.2
+    geom = Geometry(wavelength=1.0, distance=distance_for_resolution(n_px, pix, 1.0, 2.0), pixel=pix,
+                    n_x=n_px, n_y=n_px)
+    return Problem("gvl_" + kind, FIGURE_CELL, unit_atoms(), 2.0, 0.0, br, geom, 0)
+
+
+def equator(g: float, B: float, n_x: int = 1023, n_y: int = 15, n_nodes: int = 48, L: float = 150.0) -> Problem:
+    """Fig. equator: |F| = 1 with isotropic paracrystal disorder g_a = g_b =
+    g_c = g and isotropic axis Debye-Waller B_a = B_b = B_c = B, Gaussian
+    orientation sigma = 2 deg, d >= 2 A.  A strip of n_x x n_y 0.1 mm pixels
+    (n_y odd: the middle row lies on the equator) at the distance of Eq. SF
+    for 2 A across n_x pixels."""
+    if n_y % 2 == 0:
+        raise ValueError("n_y must be odd")
+    sig = math.radians(2.0)
+    br = Broadening(L=(L, L, L), g=(g, g, g), B_axis=(B, B, B), lineshape=LINESHAPE_HOSEMANN,
+                    intensity_model=INTENSITY_HOSEMANN, sigma=sig, gamma=0.0, T=patch_extent(sig, 0.0),
+                    n_nodes=n_nodes)
+    pix = 0.1
+    geom = Geometry(wavelength=1.0, distance=distance_for_resolution(n_x, pix, 1.0, 2.0), pixel=pix,
+                    n_x=n_x, n_y=n_y)
+    return Problem("equator_g%g_B%g" % (g, B), FIGURE_CELL, unit_atoms(), 2.0, 0.0, br, geom, 0)
+
+
 CONFIGS = {
     0: config0,
     1: config1,
