@@ -299,15 +299,17 @@ BatchLayout batch_layout(int n, const fdx_problem *const *probs, const fdx_atoms
 }
 
 // Scatter-form workspace: the pattern layout (records, nodes) followed by the
-// FP64 reflection frames, the per-sample table and the FP64 image.
+// FP64 reflection frames and their projections, the per-sample table and the
+// FP64 image.
 struct ScatterLayout {
-    size_t frames, stab, img64, total;
+    size_t frames, proj, stab, img64, total;
 };
 
 ScatterLayout scatter_layout(const fdx_problem *p, int n_s) {
     ScatterLayout S;
     size_t off = layout_for(p).total;
     S.frames = off, off += align_up(sizeof(double) * 12 * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    S.proj = off, off += align_up(sizeof(double) * SCAT_PROJ * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
     S.stab = off, off += align_up(sizeof(float4) * 3 * (size_t)n_s);
     S.img64 = off, off += align_up(sizeof(double) * (size_t)p->geom.n_x * p->geom.n_y);
     S.total = off;
@@ -344,6 +346,19 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     cross3(S.nh, S.bh, S.uh);
     unit3(S.uh, S.uh);
     cross3(S.bh, S.uh, S.vh);
+    S.proj = reinterpret_cast<double *>(ws + SL.proj);
+    const double *w3[3] = {S.uh, S.vh, S.bh};
+    for (int q = 0; q < 3; ++q) S.wdir[0][q] = S.nh[q];
+    for (int j = 0; j < 3; ++j) {
+        for (int q = 0; q < 3; ++q) S.wdir[1 + j][q] = w3[j][q];
+        cross3(w3[j], S.nh, S.wdir[4 + j]);
+        S.kw[j] = (S.bh[0] * w3[j][0] + S.bh[1] * w3[j][1] + S.bh[2] * w3[j][2]) / S.lambda;
+        S.nw[j] = S.nh[0] * w3[j][0] + S.nh[1] * w3[j][1] + S.nh[2] * w3[j][2];
+    }
+    S.il = 1.0 / S.lambda;
+    S.kn = (S.bh[0] * S.nh[0] + S.bh[1] * S.nh[1] + S.bh[2] * S.nh[2]) / S.lambda;
+    S.dp = S.dist / S.pix;
+    S.hx = 0.5 * prob->geom.n_x, S.hy = 0.5 * prob->geom.n_y;
     S.img64 = reinterpret_cast<double *>(ws + SL.img64);
     S.image = image;
     S.count = reinterpret_cast<unsigned long long *>(count);

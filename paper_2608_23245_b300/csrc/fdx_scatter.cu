@@ -17,9 +17,11 @@
 // reflection (one sample per lane) with the same pair evaluation as the
 // gather form (eval_core: block culling, live-node staging, packed walk); the
 // query points are the samples, referred to a centre sample of the warp.  The
-// per-sample Lorentz factor and Ewald rotation run in FP64 (one lane per
-// sample), and the hits are added with FP64 atomics into an FP64 image that a
-// last kernel rounds to FP32 (order effects far below FP32 resolution).
+// per-sample Ewald rotation runs in FP64 (one lane per sample) on seven
+// projections of S, with Newton-refined reciprocals in place of FP64 division
+// and square root; the Lorentz weight is FP32.  The hits are added with FP64
+// atomics into an FP64 image that a last kernel rounds to FP32 (order effects
+// far below FP32 resolution).
 #include "fdx_pair.cuh"
 
 namespace fdx {
@@ -47,42 +49,67 @@ __global__ void scatter_table_kernel(ScatterParams p) {
     p.stab[3 * m + 2] = make_float4(x.x, 0.0f, 0.0f, 0.0f);
 }
 
-__device__ __forceinline__ double dot3d(const double *x, const double *y) {
-    return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
+// Per reflection: its frame vectors (S^, e1, e2) projected on the seven
+// directions of the Ewald rotation and the detector map (n, u, v, b, u x n,
+// v x n, b x n), so that every projection of a sample's S is three FMAs of its
+// frame coordinates; then rho_B / r0, r0, rho_B.
+__global__ void scatter_proj_kernel(ScatterParams p) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= p.P.n_refl) return;
+    const double *fr = p.frames + (size_t)r * 12;
+    double *pr = p.proj + (size_t)r * SCAT_PROJ;
+    for (int j = 0; j < 7; ++j)
+        for (int i = 0; i < 3; ++i)
+            pr[3 * j + i] = fr[3 * i] * p.wdir[j][0] + fr[3 * i + 1] * p.wdir[j][1] + fr[3 * i + 2] * p.wdir[j][2];
+    pr[21] = fr[10] / fr[9];
+    pr[22] = fr[9], pr[23] = fr[10];
 }
 
-// Lorentz factor, Ewald rotation (both solutions) and splat of one sample.
-__device__ __forceinline__ void splat_sample(const ScatterParams &p, const double *S, double val) {
-    const double Z = dot3d(S, p.nh);
-    double perp[3];
-    for (int q = 0; q < 3; ++q) perp[q] = S[q] - Z * p.nh[q];
-    const double R = sqrt(dot3d(perp, perp));
-    const double v = val * p.delta_L / (R + p.delta_L);
-    // Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = R_
-    double kin[3], nxS[3];
-    for (int q = 0; q < 3; ++q) kin[q] = p.bh[q] / p.lambda;
-    nxS[0] = p.nh[1] * S[2] - p.nh[2] * S[1];
-    nxS[1] = p.nh[2] * S[0] - p.nh[0] * S[2];
-    nxS[2] = p.nh[0] * S[1] - p.nh[1] * S[0];
-    const double nS = dot3d(p.nh, S);
-    const double A = dot3d(kin, S), B = dot3d(kin, nxS), D = dot3d(kin, p.nh) * nS;
-    const double C = dot3d(kin, kin) + dot3d(S, S);
-    const double E = (1.0 / (p.lambda * p.lambda) - C) / 2.0 - D;
-    const double Pp = A - D, Qp = B;
-    const double rpq = sqrt(Pp * Pp + Qp * Qp);
-    const double ratio = E / rpq;
+// FP64 reciprocal and reciprocal square root: the FP32 hardware value refined
+// by one Newton step, which squares its relative error (~1e-7 -> ~1e-14).
+// FP64 division and square root take many more FP64 instructions, and FP64
+// runs at a small fraction of the FP32 rate on this GPU.
+__device__ __forceinline__ double rcp_nr(double x) {
+    const double r = (double)__frcp_rn((float)x);
+    return r * fma(-x, r, 2.0);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    const double y = (double)rsqrtf((float)x);
+    return y * fma(-0.5 * x * y, y, 1.5);
+}
+
+// Lorentz factor, Ewald rotation (both solutions) and splat of one sample,
+// from its projections s = (S.n, S.u, S.v, S.b, S.(u x n), S.(v x n), S.(b x n))
+// and |S| = rr.  The rotation by phi about n is Rodrigues' formula, so for any
+// direction w,  k_out . w = k_in . w + (S.w) cos phi + (S.(w x n)) sin phi
+// + (n.w)(S.n)(1 - cos phi).
+__device__ __forceinline__ void splat_sample(const ScatterParams &p, const double *s, double rr, double val) {
+    const double Z = s[0];
+    const float R = sqrtf((float)fmax(rr * rr - Z * Z, 0.0));
+    const float dl = (float)p.delta_L;
+    const double v = val * (double)(dl / (R + dl));  // Eq. lorentz (a weight: FP32 is enough)
+    // Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = E with
+    // P = k_in.S - D, Q = k_in.(n x S), D = (k_in.n)(n.S), E = -|S|^2/2 - D
+    const double D = p.kn * Z;
+    const double E = -0.5 * rr * rr - D;
+    const double Pp = p.il * s[3] - D, Qp = p.il * s[6];
+    const double inv = rsqrt_nr(Pp * Pp + Qp * Qp);
+    const double ratio = E * inv;
     if (!(fabs(ratio) <= 1.0)) return;  // Eq. valid: no rotation reaches the Ewald sphere
     // phi = phi0 +- delta with cos(phi0), sin(phi0) = (P, Q)/rpq, cos(delta) = ratio
-    const double c0 = Pp / rpq, s0 = Qp / rpq, cd = ratio, sd = sqrt(fmax(0.0, 1.0 - ratio * ratio));
+    const double c0 = Pp * inv, s0 = Qp * inv, cd = ratio;
+    const double t = (1.0 - ratio) * (1.0 + ratio);
+    const double sd = t > 1e-30 ? t * rsqrt_nr(t) : sqrt(t);
     for (int br = 0; br < 2; ++br) {
         const double sgn = br == 0 ? 1.0 : -1.0;
         const double cp = c0 * cd - sgn * s0 * sd, sp = s0 * cd + sgn * c0 * sd;
-        double ko[3];
-        for (int q = 0; q < 3; ++q) ko[q] = kin[q] + S[q] * cp + nxS[q] * sp + p.nh[q] * nS * (1.0 - cp);
-        const double kb = dot3d(ko, p.bh);
+        const double zc = Z * (1.0 - cp);
+        const double kb = p.kw[2] + s[3] * cp + s[6] * sp + p.nw[2] * zc;
         if (!(kb > 0.0)) continue;
-        const double xp = p.dist * dot3d(ko, p.uh) / kb / p.pix + 0.5 * p.P.nx;
-        const double yp = p.dist * dot3d(ko, p.vh) / kb / p.pix + 0.5 * p.P.ny;
+        const double ku = p.kw[0] + s[1] * cp + s[4] * sp + p.nw[0] * zc;
+        const double kv = p.kw[1] + s[2] * cp + s[5] * sp + p.nw[1] * zc;
+        const double ib = p.dp * rcp_nr(kb);
+        const double xp = fma(ku, ib, p.hx), yp = fma(kv, ib, p.hy);
         const double fi = floor(xp), fj = floor(yp);
         if (!(fi >= 0.0) || !(fj >= 0.0) || fi >= (double)p.P.nx || fj >= (double)p.P.ny) continue;
         atomicAdd(&p.img64[(size_t)fj * p.P.nx + (size_t)fi], v);
@@ -102,8 +129,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     const int r = (int)(item / n_chunks), chunk = (int)(item % n_chunks);
     float *rec = s_rec[warp];
     load_record(p.P.recs, r, rec, lane);
-    const double *fr = p.frames + (size_t)r * 12;
-    const double r0 = fr[9], hr = fr[10];
+    const double *pr = p.proj + (size_t)r * SCAT_PROJ;
+    const double r0 = pr[22], hr = pr[23];
 
     const int m = chunk * 32 + lane;
     const int n_valid = min(32, p.n_s - chunk * 32);
@@ -111,7 +138,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tc = ta;
     if (valid) ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
     // (S - D)/r0 in the reflection frame: (1 + rho) (c, c d1, c d2) - (1, 0, 0), rho = x_r h_r / r0
-    const float rho = (float)((double)tc.x * hr / r0);
+    const float rho = tc.x * (float)pr[21];
     const ff u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
     const ff u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
     const ff u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
@@ -144,17 +171,18 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     if (!valid || !any) return;
     const double I = (double)rec[REC_FR] * ((double)pa[0].s0.hi + (double)pa[0].s0.lo);
     if (!(I != 0.0)) return;
-    // S in the laboratory frame, (r0 + x_r h_r) (c, c d1, c d2) from the FP64
-    // frame and the float-float table (no FP32 rounding: the hit position of a
-    // sample near the edge of the Ewald condition is sensitive to S), and the
-    // volume element
+    // projections of S = (r0 + x_r h_r) (c, c d1, c d2) in the reflection frame
+    // from the FP64 frame projections and the float-float table (no FP32
+    // rounding: the hit position of a sample near the edge of the Ewald
+    // condition is sensitive to S), and the volume element
     const double rr = r0 + (double)tc.x * hr;
     const double U0 = 1.0 + ((double)ta.x + (double)ta.y), U1 = (double)ta.z + (double)ta.w,
                  U2 = (double)tb.x + (double)tb.y;
-    double S[3];
-    for (int k = 0; k < 3; ++k) S[k] = rr * (U0 * fr[k] + U1 * fr[3 + k] + U2 * fr[6 + k]);
+    double sp[7];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) sp[j] = rr * fma(U0, pr[3 * j], fma(U1, pr[3 * j + 1], U2 * pr[3 * j + 2]));
     const double dV = (double)tb.w * hr * rr * rr;
-    splat_sample(p, S, dV * I);
+    splat_sample(p, sp, rr, dV * I);
 }
 
 __global__ void scatter_finish_kernel(const double *img64, float *image, long long n) {
@@ -175,6 +203,7 @@ static void launch_scatter_ls(const ScatterParams &p, bool count_mode, cudaStrea
 
 cudaError_t launch_scatter(const ScatterParams &p, int lineshape, bool count_mode, cudaStream_t s) {
     scatter_table_kernel<<<(p.n_s + 127) / 128, 128, 0, s>>>(p);
+    scatter_proj_kernel<<<(p.P.n_refl + 127) / 128, 128, 0, s>>>(p);
     if (lineshape == FDX_LINESHAPE_HOSEMANN)
         launch_scatter_ls<FDX_LINESHAPE_HOSEMANN>(p, count_mode, s);
     else if (lineshape == FDX_LINESHAPE_GAUSS)
