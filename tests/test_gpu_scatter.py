@@ -74,6 +74,27 @@ def test_scatter_matches_oracle(gpu, orc, make):
     assert abs(E - E_ref) <= 1e-4 * E_ref, (E, E_ref)
 
 
+@pytest.mark.parametrize("n", [1, 31, 77])
+def test_scatter_ragged_sample_counts(gpu, orc, n):
+    """Sample counts that leave the last warp of samples partly empty."""
+    import torch
+    p = api_precision(W.small_helix())
+    xs = W.scatter_samples(4, 8, 8)[:n]
+    sim = gpu.Simulation(p)
+    sim.structure_factors()
+    smp = torch.as_tensor(np.ascontiguousarray(xs), device="cuda")
+    img = sim.scatter(smp).cpu().numpy().astype(np.float64)
+    E = int(sim.scatter_evals(smp).item())
+    torch.cuda.synchronize()
+    hkl = sim.hkl_host
+    ref, E_ref, samp = orc.scatter(p, hkl, orc.intensities_M(p, hkl), xs.astype(np.float64), with_samples=True)
+    assert ref.max() > 0
+    bad = _edge_mask(p, samp)
+    mr, l2 = parity(np.where(bad, 0.0, img).reshape(-1), np.where(bad, 0.0, ref).reshape(-1))
+    assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
+    assert abs(E - E_ref) <= 1e-4 * E_ref + 2, (E, E_ref)
+
+
 def test_scatter_mirror_symmetry_gpu(gpu):
     """The two Ewald solutions are mirror images: the GPU image is symmetric
     about the meridian except where a hit sits at a pixel edge."""
