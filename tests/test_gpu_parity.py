@@ -132,6 +132,45 @@ def test_structure_factors_bad_element_is_nan(gpu):
     assert torch.isnan(F).all()
 
 
+def test_structure_factors_edge_cases(gpu, orc):
+    """One atom (F = occ f(s) exp(-B s^2/4), the closed form of Eq.
+    structure_factor for a single atom at the origin), zero occupancy (F = 0),
+    an empty reflection list (no work, no error), and 1,025 atoms (a ragged
+    second chunk of the element sort)."""
+    import torch
+    p = api_precision(W.small_helix())
+    hkl = gpu.fdx_reflections(p.cell, p.d_min)
+    hk = torch.as_tensor(hkl, device="cuda")
+    a = p.atoms
+    one = replace(a, frac=np.zeros((1, 3)), B=np.array([12.0]), occ=np.array([0.75]), elem=np.array([2], np.uint8))
+    one = api_precision(replace(p, atoms=one)).atoms
+    F, _ = gpu.fdx_structure_factors(p.cell, gpu.DeviceAtoms(one), hk, p.br)
+    _sync()
+    _, As = orc.basis(p.cell)
+    s2 = np.sum((hkl.astype(np.float64) @ np.asarray(As).reshape(3, 3)) ** 2, axis=1)
+    ff = one.ff[2]
+    f = ff[8] + np.sum(ff[None, 0:4] * np.exp(-ff[None, 4:8] * s2[:, None] / 4), axis=1)
+    ref = one.occ[0] * f * np.exp(-one.B[0] * s2 / 4)
+    Fg = F.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(Fg[:, 0] - ref)) <= 2e-6 * np.max(ref) and np.max(np.abs(Fg[:, 1])) <= 2e-6 * np.max(ref)
+    zero = replace(a, occ=np.zeros(a.n))
+    F0, _ = gpu.fdx_structure_factors(p.cell, gpu.DeviceAtoms(zero), hk, p.br)
+    _sync()
+    assert torch.all(F0 == 0)
+    Fe, Me = gpu.fdx_structure_factors(p.cell, gpu.DeviceAtoms(a), hk[:0], p.br)
+    _sync()
+    assert Fe.numel() == 0 and Me.numel() == 0
+    rng = np.random.default_rng(1025)
+    big = api_precision(replace(p, atoms=replace(a, frac=rng.uniform(0, 1, (1025, 3)), B=rng.uniform(10, 30, 1025),
+                                                 occ=np.ones(1025), elem=rng.integers(0, 4, 1025).astype(np.uint8))))
+    Fb, _ = gpu.fdx_structure_factors(p.cell, gpu.DeviceAtoms(big.atoms), hk, p.br)
+    _sync()
+    Fb = Fb.cpu().numpy().astype(np.float64)
+    Fo = orc.structure_factors(p.cell, big.atoms, hkl)
+    err = np.abs(Fb[:, 0] + 1j * Fb[:, 1] - Fo) / _amp_scale(big, hkl)
+    assert err.max() <= SF_TOL, err.max()
+
+
 def _gpu_pattern(gpu, p, hkl, M):
     import torch
     hk = torch.as_tensor(np.ascontiguousarray(hkl, np.int32), device="cuda").reshape(-1, 3)

@@ -80,3 +80,26 @@ def test_ring_unsplit_large_detector(gpu, orc):
     assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
     n = int(cnt[pix[:, 1], pix[:, 0]].astype(np.int64).sum())
     assert abs(n - int(E.sum())) <= 1e-4 * E.sum()
+
+
+def test_ring_edge_cases(gpu, orc):
+    """Empty reflection list (zero image), 1 x 1 and ragged detectors."""
+    import torch
+    p = api_precision(_small(W.small_triclinic))
+    hkl = orc.reflections(p.cell, p.d_min)
+    M = orc.intensities_M(p, hkl)
+    for nx, ny, n in ((30, 24, 0), (1, 1, len(hkl)), (17, 9, len(hkl)), (33, 5, len(hkl))):
+        q = replace(p, geom=replace(p.geom, n_x=nx, n_y=ny, pixel=p.geom.pixel * 30 / nx))
+        hk = torch.as_tensor(np.ascontiguousarray(hkl[:n], np.int32), device="cuda").reshape(-1, 3)
+        Mt = torch.as_tensor(np.ascontiguousarray(M[:n], np.float32), device="cuda")
+        prob = gpu.make_problem(q.cell, q.br, q.geom, hk, Mt)
+        img = torch.full((ny, nx), float("nan"), dtype=torch.float32, device="cuda")
+        gpu.fdx_ring(prob, img)
+        torch.cuda.synchronize()
+        img = img.cpu().numpy().reshape(-1)
+        if n == 0:
+            assert np.all(img == 0.0)
+            continue
+        I, _ = orc.ring(q, hkl[:n], M[:n].astype(np.float32).astype(np.float64))
+        mr, l2 = parity(img, I)
+        assert mr <= MAX_REL and l2 <= L2_REL, (nx, ny, mr, l2)
