@@ -79,15 +79,16 @@ __global__ void band_bounds_kernel(AdjParams A) {
 // One (reflection, band) item of the adjoint for one warp.  With PPL = 2 the
 // warp's patch is 8 x 8 pixels (two rows of 8 x 4 bound patches; bands hold
 // an even number of patch rows).  Per lane, the pair sums times the pixel's
-// c = dL/dI L are accumulated in float-float over the item's patches; the
-// warp adds its lanes in FP64 once at the end.
+// c = dL/dI L (applied to each 16-pair FP32 chunk sum) are accumulated in one
+// float-float sum per quantity over the item's patches; the warp adds its
+// lanes in FP64 once at the end.
 template <int PPL>
 __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item, float4 *buf, float4 *dn, float4 *sc,
                                              float4 *sc2, float *rec, int lane) {
     const int r = (int)(item / A.n_bands), b = (int)(item % A.n_bands);
-    ff ia[ADJ_ITEM_VALS];
+    PairAcc tot[PPL];  // the item's sums, weighted by each pixel's c, in tot[0]
 #pragma unroll
-    for (int k = 0; k < ADJ_ITEM_VALS; ++k) ia[k] = ff{0.0f, 0.0f};
+    for (int p = 0; p < PPL; ++p) clear(tot[p]);
     const float4 q = A.P.reach[r];
     if (reach_overlap(q, A.band_bounds[b])) {
         load_record(A.P.recs, r, rec, lane);
@@ -114,37 +115,23 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
                 const int k = base + bit;
                 const int px0 = 8 * (k % A.npx), py0 = 4 * (pj0 + PPL * (k / A.npx));
                 const PatchPix<PPL> g = load_patch<PPL>(A.P.pixgeo, A.P.nx, A.P.ny, px0, py0, lane);
-                float c[PPL];
+                QueryPts<PPL> qp = pixel_queries<PPL>(A.P, g, rec);
                 bool any = false;
 #pragma unroll
                 for (int p = 0; p < PPL; ++p) {
-                    c[p] = 0.0f;
+                    qp.cw[p] = 0.0f;
                     if (g.valid[p]) {
                         const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
-                        c[p] = A.gI[(size_t)py * A.P.nx + px] * (dl / ((g.Rh[p] + g.Rl[p]) + dl));
+                        qp.cw[p] = A.gI[(size_t)py * A.P.nx + px] * (dl / ((g.Rh[p] + g.Rl[p]) + dl));
                     }
-                    any |= c[p] != 0.0f;
+                    any |= qp.cw[p] != 0.0f;
                 }
                 if (__ballot_sync(FDX_FULL_MASK, any) == 0) continue;
-                PairAcc pa[PPL];
-#pragma unroll
-                for (int p = 0; p < PPL; ++p) clear(pa[p]);
-                if (!eval_pair<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, PPL>(A.P, g, rec, buf, dn, sc, sc2, lane,
-                                                                                    pa))
-                    continue;
-#pragma unroll
-                for (int p = 0; p < PPL; ++p) {
-                    const PairAcc &a = pa[p];
-                    ia[0] = ff_add(ia[0], ff_mul_f(a.s0, c[p]));
-                    ia[1] = ff_add(ia[1], ff_mul_f(a.sb[0], c[p]));
-                    ia[2] = ff_add(ia[2], ff_mul_f(a.sb[1], c[p]));
-                    ia[3] = ff_add(ia[3], ff_mul_f(a.sb[2], c[p]));
-                    ia[4] = ff_add(ia[4], ff_mul_f(a.ss, c[p]));
-                    ia[5] = ff_add(ia[5], ff_mul_f(a.sg, c[p]));
-                }
+                eval_core<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, PPL>(A.P, qp, rec, buf, dn, sc, sc2, lane, tot);
             }
         }
     }
+    const ff ia[ADJ_ITEM_VALS] = {tot[0].s0, tot[0].sb[0], tot[0].sb[1], tot[0].sb[2], tot[0].ss, tot[0].sg};
     double acc[ADJ_ITEM_VALS];
 #pragma unroll
     for (int k = 0; k < ADJ_ITEM_VALS; ++k) acc[k] = warp_sum_d((double)ia[k].hi + (double)ia[k].lo);

@@ -208,6 +208,7 @@ struct QueryPts {
     float tau[PPL][3];
     bool valid[PPL];
     ff dP[3];
+    float cw[PPL];  // adjoint: weight of each point's sums (dL/dI x Lorentz factor)
 };
 
 // Pixel query points (reading R12): p = Z n + R e_R(D) for the lane's pixels.
@@ -478,16 +479,28 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     }
                 }
             }
+            if (MODE == MODE_ADJ) {
+                // adjoint: the lane's points weighted by cw, into one accumulator
+                float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f, x4 = 0.f, x5 = 0.f;
 #pragma unroll
-            for (int p = 0; p < PPL; ++p) {
-                acc[p].s0 = ff_add_f(acc[p].s0, r0[p].x + r0[p].y);
-                if (MODE == MODE_ADJ) {
-                    acc[p].sb[0] = ff_add_f(acc[p].sb[0], rb0[p].x + rb0[p].y);
-                    acc[p].sb[1] = ff_add_f(acc[p].sb[1], rb1[p].x + rb1[p].y);
-                    acc[p].sb[2] = ff_add_f(acc[p].sb[2], rb2[p].x + rb2[p].y);
-                    acc[p].ss = ff_add_f(acc[p].ss, rss[p].x + rss[p].y);
-                    acc[p].sg = ff_add_f(acc[p].sg, rsg[p].x + rsg[p].y);
+                for (int p = 0; p < PPL; ++p) {
+                    const float c = qp.cw[p];
+                    x0 = fmaf(c, r0[p].x + r0[p].y, x0);
+                    x1 = fmaf(c, rb0[p].x + rb0[p].y, x1);
+                    x2 = fmaf(c, rb1[p].x + rb1[p].y, x2);
+                    x3 = fmaf(c, rb2[p].x + rb2[p].y, x3);
+                    x4 = fmaf(c, rss[p].x + rss[p].y, x4);
+                    x5 = fmaf(c, rsg[p].x + rsg[p].y, x5);
                 }
+                acc[0].s0 = ff_add_f(acc[0].s0, x0);
+                acc[0].sb[0] = ff_add_f(acc[0].sb[0], x1);
+                acc[0].sb[1] = ff_add_f(acc[0].sb[1], x2);
+                acc[0].sb[2] = ff_add_f(acc[0].sb[2], x3);
+                acc[0].ss = ff_add_f(acc[0].ss, x4);
+                acc[0].sg = ff_add_f(acc[0].sg, x5);
+            } else {
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) acc[p].s0 = ff_add_f(acc[p].s0, r0[p].x + r0[p].y);
             }
         }
     };
