@@ -58,7 +58,7 @@ SF_FLOPS_PER_TERM = 16.78125
 # geometry at 16 B per pixel, reflection records, node tables), 0 written (the
 # 4 MB image stays in L2 during the launch).  Valid only for the kernel as
 # captured: set to None whenever the pattern kernel changes.
-PATTERN_DRAM_BYTES = 18198016
+PATTERN_DRAM_BYTES = None
 
 
 def _peaks():

@@ -427,8 +427,9 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // walk npair pairs from pair slot ub; TEST: per-pixel support test (rim list)
     auto walk = [&](int ub, int npair, auto test_tag) {
         constexpr bool TEST = decltype(test_tag)::value;
-        for (int u0 = 0; u0 < npair; u0 += 16) {
-            const int ue = ub + min(u0 + 16, npair);
+        constexpr int CH = 32;  // node pairs per FP32 chunk sum
+        for (int u0 = 0; u0 < npair; u0 += CH) {
+            const int ue = ub + min(u0 + CH, npair);
             float2 r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = f2(0.0f);
