@@ -79,7 +79,7 @@ __global__ void band_bounds_kernel(AdjParams A) {
 // One (reflection, band) item of the adjoint for one warp.  With PPL = 2 the
 // warp's patch is 8 x 8 pixels (two rows of 8 x 4 bound patches; bands hold
 // an even number of patch rows).  Per lane, the pair sums times the pixel's
-// c = dL/dI L (applied to each 32-pair FP32 chunk sum) are accumulated in one
+// c = dL/dI L (applied to each 64-pair FP32 chunk sum) are accumulated in one
 // float-float sum per quantity over the item's patches; the warp adds its
 // lanes in FP64 once at the end.
 template <int PPL>

@@ -427,7 +427,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // walk npair pairs from pair slot ub; TEST: per-pixel support test (rim list)
     auto walk = [&](int ub, int npair, auto test_tag) {
         constexpr bool TEST = decltype(test_tag)::value;
-        constexpr int CH = 32;  // node pairs per FP32 chunk sum
+        constexpr int CH = MODE == MODE_ADJ ? 64 : 32;  // node pairs per FP32 chunk sum (the adjoint folds six)
         for (int u0 = 0; u0 < npair; u0 += CH) {
             const int ue = ub + min(u0 + CH, npair);
             float2 r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
