@@ -28,6 +28,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -500,7 +501,8 @@ def main():
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     # dominant kernel (the pattern launch) timed on its own stream position
     pstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks_path = os.path.join(ROOT, "gpurun_out", "bench_clocks_rank%d.csv" % rank)
+    # raw clock samples (the JSON line carries their summary); FDX_CLOCKS_DIR keeps them
+    clocks_path = os.path.join(os.environ.get("FDX_CLOCKS_DIR", tempfile.gettempdir()), "bench_clocks_rank%d.csv" % rank)
     os.makedirs(os.path.dirname(clocks_path), exist_ok=True)
     barrier(world)
     torch.cuda.synchronize()
