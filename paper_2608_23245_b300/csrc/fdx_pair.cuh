@@ -111,6 +111,27 @@ __device__ __forceinline__ void sincospi_f(float x, float &s, float &c) {
 
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 
+// sincospi_f for two arguments: the reduction and the polynomials on packed
+// FP32x2 pairs, the quarter-turn rotation per element.
+__device__ __forceinline__ void sincospi_f2(float2 x, float2 &s, float2 &c) {
+    const float2 q = make_float2(rintf(2.0f * x.x), rintf(2.0f * x.y));
+    const float2 r = __fmul2_rn(f2(0.5f), __ffma2_rn(f2(-0.5f), q, x));
+    const float Sc[4] = FDX_SIN2PI_C;
+    const float Cc[5] = FDX_COS2PI_C;
+    const float2 r2 = __fmul2_rn(r, r);
+    float2 S = f2(Sc[3]), C = f2(Cc[4]);
+#pragma unroll
+    for (int k = 2; k >= 0; --k) S = __ffma2_rn(S, r2, f2(Sc[k]));
+#pragma unroll
+    for (int k = 3; k >= 0; --k) C = __ffma2_rn(C, r2, f2(Cc[k]));
+    S = __fmul2_rn(r, S);
+    const int q0 = (int)q.x, q1 = (int)q.y;
+    const float s0 = (q0 & 1) ? C.x : S.x, c0 = (q0 & 1) ? -S.x : C.x;
+    const float s1 = (q1 & 1) ? C.y : S.y, c1 = (q1 & 1) ? -S.y : C.y;
+    s = make_float2((q0 & 2) ? -s0 : s0, (q1 & 2) ? -s1 : s1);
+    c = make_float2((q0 & 2) ? -c0 : c0, (q1 & 2) ? -c1 : c1);
+}
+
 // v if |a| <= ta and |b| <= tb and |c| <= tc, else o (one predicate chain).
 __device__ __forceinline__ float support_sel(float a, float b, float c, float ta, float tb, float tc, float v, float o) {
     float r;
@@ -394,7 +415,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // (16 pairs) at a time; a pair never straddles two such groups, so reading
     // the group before writing it is enough.  Padding node (odd n): weight 0,
     // and for the rim list far outside every support.
-    auto pack = [&](int base, int n, bool rim) {
+    auto pack_node = [&](int base, int n, bool rim) {
         float *bf = reinterpret_cast<float *>(buf);
         float *bs = reinterpret_cast<float *>(bsc);
         float *be = reinterpret_cast<float *>(bsc2);
@@ -423,6 +444,47 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             }
             __syncwarp();
         }
+    };
+    // The same rearrangement with one pair per lane: lane k reads nodes 2k and
+    // 2k + 1 of the list and writes the packed pair into the same two slots,
+    // so no lane touches another's slots.  Fewer instructions per node, but
+    // 32-byte-strided shared-memory accesses and half as many busy lanes: it
+    // pays only with one point per lane, where staging weighs more.
+    auto pack_pair = [&](int base, int n, bool rim) {
+        const int npair = (n + 1) >> 1;
+        for (int k = lane; k < npair; k += 32) {
+            const float4 pad = rim ? make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const float4 n0 = buf[base + 2 * k];
+            const float4 n1 = 2 * k + 1 < n ? buf[base + 2 * k + 1] : pad;
+            float4 dw = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (MODE == MODE_ADJ) {
+                const float2 d0 = reinterpret_cast<const float2 *>(buf2)[base + 2 * k];
+                const float2 d1 =
+                    2 * k + 1 < n ? reinterpret_cast<const float2 *>(buf2)[base + 2 * k + 1] : make_float2(0.0f, 0.0f);
+                dw = make_float4(d0.x, d1.x, d0.y, d1.y);
+            }
+            float2 sa, ca, sb, cb, sc, cc;
+            sincospi_f2(make_float2(n0.x, n1.x), sa, ca);
+            sincospi_f2(make_float2(n0.y, n1.y), sb, cb);
+            sincospi_f2(make_float2(n0.z, n1.z), sc, cc);
+            const int u = (base >> 1) + k;
+            buf[2 * u] = make_float4(-n0.x, -n1.x, -n0.y, -n1.y);
+            buf[2 * u + 1] = make_float4(-n0.z, -n1.z, n0.w, n1.w);
+            const float2 Ca = __fmul2_rn(f2(slb[0]), ca), Sa = __fmul2_rn(f2(slb[0]), sa);
+            const float2 Cb = __fmul2_rn(f2(slb[1]), cb), Sb = __fmul2_rn(f2(slb[1]), sb);
+            const float2 Cc = __fmul2_rn(f2(slb[2]), cc), Sc = __fmul2_rn(f2(slb[2]), sc);
+            bsc[2 * u] = make_float4(Ca.x, Ca.y, Sa.x, Sa.y);
+            bsc[2 * u + 1] = make_float4(Cb.x, Cb.y, Sb.x, Sb.y);
+            bsc2[u] = make_float4(Cc.x, Cc.y, Sc.x, Sc.y);
+            if (MODE == MODE_ADJ) buf2[u] = dw;
+        }
+        __syncwarp();
+    };
+    auto pack = [&](int base, int n, bool rim) {
+        if constexpr (PPL == 1)
+            pack_pair(base, n, rim);
+        else
+            pack_node(base, n, rim);
     };
     // walk npair pairs from pair slot ub; TEST: per-pixel support test (rim list)
     auto walk = [&](int ub, int npair, auto test_tag) {
