@@ -368,11 +368,11 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     return FDX_OK;
 }
 
-// Warps per 8 x 4 patch of the ring average: about 16384 warps in all (some
-// seven waves of 16 resident warps on each of 148 SMs), at most 64.
+// Warps per 8 x 4 patch of the ring average: about 32768 warps in all (some
+// fourteen waves of 16 resident warps on each of 148 SMs), at most 64.
 int ring_split(const fdx_problem *p) {
     const long long patches = (long long)((p->geom.n_x + 7) / 8) * ((p->geom.n_y + 3) / 4);
-    const long long s = (16384 + patches - 1) / (patches > 0 ? patches : 1);
+    const long long s = (32768 + patches - 1) / (patches > 0 ? patches : 1);
     return (int)(s < 1 ? 1 : (s > 64 ? 64 : s));
 }
 

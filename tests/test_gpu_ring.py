@@ -56,13 +56,13 @@ def test_ring_mirror_symmetry_gpu(gpu):
 
 
 def test_ring_unsplit_large_detector(gpu, orc):
-    """A detector of 1024 x 512 pixels has enough 8 x 4 patches to fill the
+    """A detector of 1024 x 1024 pixels has enough 8 x 4 patches to fill the
     GPU with one warp each, so every reflection's azimuth points stay in one
     warp (the reduced detectors above deal them to several): sampled pixels
     against the oracle, and the in-support count of those pixels."""
     import torch
     p = W.small_helix()
-    p = replace(p, geom=replace(p.geom, n_x=1024, n_y=512, pixel=p.geom.pixel * p.geom.n_x / 1024),
+    p = replace(p, geom=replace(p.geom, n_x=1024, n_y=1024, pixel=p.geom.pixel * p.geom.n_x / 1024),
                 br=replace(p.br, n_nodes=8))
     p = api_precision(p)
     sim = gpu.Simulation(p)
@@ -71,7 +71,7 @@ def test_ring_unsplit_large_detector(gpu, orc):
     cnt = sim.ring_evals().cpu().numpy()
     torch.cuda.synchronize()
     rng = np.random.default_rng(7)
-    pix = np.stack([rng.integers(0, 1024, 32), rng.integers(0, 512, 32)], 1)
+    pix = np.stack([rng.integers(0, 1024, 32), rng.integers(0, 1024, 32)], 1)
     hkl = sim.hkl_host
     I, E = orc.ring(p, hkl, orc.intensities_M(p, hkl), pix=pix)
     got = img[pix[:, 1], pix[:, 0]].astype(np.float64)
