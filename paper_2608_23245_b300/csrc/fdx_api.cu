@@ -309,7 +309,7 @@ ScatterLayout scatter_layout(const fdx_problem *p, int n_s) {
     ScatterLayout S;
     size_t off = layout_for(p).total;
     S.frames = off, off += align_up(sizeof(double) * 12 * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
-    S.proj = off, off += align_up(sizeof(double) * SCAT_PROJ * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
+    S.proj = off, off += align_up(sizeof(float2) * SCAT_PROJ * (size_t)(p->n_refl > 0 ? p->n_refl : 1));
     S.stab = off, off += align_up(sizeof(float4) * 3 * (size_t)n_s);
     S.img64 = off, off += align_up(sizeof(double) * (size_t)p->geom.n_x * p->geom.n_y);
     S.total = off;
@@ -346,7 +346,7 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     cross3(S.nh, S.bh, S.uh);
     unit3(S.uh, S.uh);
     cross3(S.bh, S.uh, S.vh);
-    S.proj = reinterpret_cast<double *>(ws + SL.proj);
+    S.proj = reinterpret_cast<float2 *>(ws + SL.proj);
     const double *w3[3] = {S.uh, S.vh, S.bh};
     for (int q = 0; q < 3; ++q) S.wdir[0][q] = S.nh[q];
     for (int j = 0; j < 3; ++j) {
@@ -359,6 +359,9 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     S.kn = (S.bh[0] * S.nh[0] + S.bh[1] * S.nh[1] + S.bh[2] * S.nh[2]) / S.lambda;
     S.dp = S.dist / S.pix;
     S.hx = 0.5 * prob->geom.n_x, S.hy = 0.5 * prob->geom.n_y;
+    auto ffv = [](double x) { float h, l; split_double(x, h, l); return make_float2(h, l); };
+    S.il_f = ffv(S.il), S.kn_f = ffv(S.kn), S.dp_f = ffv(S.dp), S.hx_f = ffv(S.hx), S.hy_f = ffv(S.hy);
+    for (int j = 0; j < 3; ++j) S.kw_f[j] = ffv(S.kw[j]), S.nw_f[j] = ffv(S.nw[j]);
     S.img64 = reinterpret_cast<double *>(ws + SL.img64);
     S.image = image;
     S.count = reinterpret_cast<unsigned long long *>(count);

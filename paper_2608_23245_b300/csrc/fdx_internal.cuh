@@ -242,12 +242,13 @@ struct ScatterParams {
     const float4 *samples;    // [n_s] (x_r, x_1, x_2, q)
     float4 *stab;             // [n_s][3] per-sample table (set-up kernel)
     const double *frames;     // [n_refl][12]
-    double *proj;             // [n_refl][SCAT_PROJ]: frame vectors projected on wdir, rho_B / r0, r0, rho_B
+    float2 *proj;             // [n_refl][SCAT_PROJ] float-float: frame vectors projected on wdir, r0, rho_B, (rho_B / r0, 0)
     double T, lambda, dist, pix, delta_L;
     double nh[3], bh[3], uh[3], vh[3];
     double wdir[7][3];        // n, u, v, b, u x n, v x n, b x n
     double il, kn, kw[3], nw[3], dp, hx, hy;  // 1/lambda, (b.n)/lambda, (b.w)/lambda and n.w for w = u, v, b,
                                               // distance / pixel, n_x / 2, n_y / 2
+    float2 il_f, kn_f, kw_f[3], nw_f[3], dp_f, hx_f, hy_f;  // the same as float-float (hi, lo)
     double *img64;            // [ny][nx] accumulation
     float *image;             // [ny][nx] output
     unsigned long long *count;  // evaluation count (count mode)

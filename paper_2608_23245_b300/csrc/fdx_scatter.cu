@@ -17,11 +17,10 @@
 // reflection (one sample per lane) with the same pair evaluation as the
 // gather form (eval_core: block culling, live-node staging, packed walk); the
 // query points are the samples, referred to a centre sample of the warp.  The
-// per-sample Ewald rotation runs in FP64 (one lane per sample) on seven
-// projections of S, with Newton-refined reciprocals in place of FP64 division
-// and square root; the Lorentz weight is FP32.  The hits are added with FP64
-// atomics into an FP64 image that a last kernel rounds to FP32 (order effects
-// far below FP32 resolution).
+// per-sample Ewald rotation runs in float-float (one lane per sample) on seven
+// projections of S, with Newton-refined reciprocals; the weights are FP32.
+// The hits are added with FP64 atomics into an FP64 image that a last kernel
+// rounds to FP32 (order effects far below FP32 resolution).
 #include "fdx_pair.cuh"
 
 namespace fdx {
@@ -51,67 +50,95 @@ __global__ void scatter_table_kernel(ScatterParams p) {
 
 // Per reflection: its frame vectors (S^, e1, e2) projected on the seven
 // directions of the Ewald rotation and the detector map (n, u, v, b, u x n,
-// v x n, b x n), so that every projection of a sample's S is three FMAs of its
-// frame coordinates; then rho_B / r0, r0, rho_B.
+// v x n, b x n), so that every projection of a sample's S is three products
+// of its frame coordinates; then r0, rho_B and rho_B / r0.  Computed in FP64,
+// stored as float-float.
 __global__ void scatter_proj_kernel(ScatterParams p) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= p.P.n_refl) return;
     const double *fr = p.frames + (size_t)r * 12;
-    double *pr = p.proj + (size_t)r * SCAT_PROJ;
+    float2 *pr = p.proj + (size_t)r * SCAT_PROJ;
+    float h, l;
     for (int j = 0; j < 7; ++j)
-        for (int i = 0; i < 3; ++i)
-            pr[3 * j + i] = fr[3 * i] * p.wdir[j][0] + fr[3 * i + 1] * p.wdir[j][1] + fr[3 * i + 2] * p.wdir[j][2];
-    pr[21] = fr[10] / fr[9];
-    pr[22] = fr[9], pr[23] = fr[10];
+        for (int i = 0; i < 3; ++i) {
+            split_double(fr[3 * i] * p.wdir[j][0] + fr[3 * i + 1] * p.wdir[j][1] + fr[3 * i + 2] * p.wdir[j][2], h, l);
+            pr[3 * j + i] = make_float2(h, l);
+        }
+    split_double(fr[9], h, l);
+    pr[21] = make_float2(h, l);
+    split_double(fr[10], h, l);
+    pr[22] = make_float2(h, l);
+    pr[23] = make_float2((float)(fr[10] / fr[9]), 0.0f);
 }
 
-// FP64 reciprocal and reciprocal square root: the FP32 hardware value refined
-// by one Newton step, which squares its relative error (~1e-7 -> ~1e-14).
-// FP64 division and square root take many more FP64 instructions, and FP64
-// runs at a small fraction of the FP32 rate on this GPU.
-__device__ __forceinline__ double rcp_nr(double x) {
-    const double r = (double)__frcp_rn((float)x);
-    return r * fma(-x, r, 2.0);
+// Float-float reciprocal and reciprocal square root: the FP32 hardware value
+// refined by one Newton step whose residual is formed in float-float, which
+// squares the relative error (~1e-7 -> ~1e-14).  FP64 runs at a small
+// fraction of the FP32 rate on this GPU, so the per-sample geometry is done in
+// float-float (about 48 significant bits) instead.
+__device__ __forceinline__ ff ffv(float2 v) { return ff{v.x, v.y}; }
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_rcp(ff x) {
+    const float y = __frcp_rn(x.hi);
+    const ff xy = ff_mul_f(x, y);
+    const float r = (1.0f - xy.hi) - xy.lo;
+    return fast_two_sum(y, y * r);
 }
-__device__ __forceinline__ double rsqrt_nr(double x) {
-    const double y = (double)rsqrtf((float)x);
-    return y * fma(-0.5 * x * y, y, 1.5);
+__device__ __forceinline__ ff ff_rsqrt(ff x) {
+    const float y = rsqrtf(x.hi);
+    const float y2 = y * y;
+    const ff yy = {y2, fmaf(y, y, -y2)};  // y^2 exactly
+    const ff xy2 = ff_mul(x, yy);
+    const float r = (1.0f - xy2.hi) - xy2.lo;
+    return fast_two_sum(y, 0.5f * y * r);
+}
+// floor of hi + lo (hi an integer and lo < 0: one below)
+__device__ __forceinline__ float ff_floor(ff x) {
+    float f = floorf(x.hi);
+    if (f == x.hi && x.lo < 0.0f) f -= 1.0f;
+    return f;
 }
 
 // Lorentz factor, Ewald rotation (both solutions) and splat of one sample,
 // from its projections s = (S.n, S.u, S.v, S.b, S.(u x n), S.(v x n), S.(b x n))
-// and |S| = rr.  The rotation by phi about n is Rodrigues' formula, so for any
-// direction w,  k_out . w = k_in . w + (S.w) cos phi + (S.(w x n)) sin phi
-// + (n.w)(S.n)(1 - cos phi).
-__device__ __forceinline__ void splat_sample(const ScatterParams &p, const double *s, double rr, double val) {
-    const double Z = s[0];
-    const float R = sqrtf((float)fmax(rr * rr - Z * Z, 0.0));
+// and |S| = rr, all float-float.  The rotation by phi about n is Rodrigues'
+// formula, so for any direction w,  k_out . w = k_in . w + (S.w) cos phi
+// + (S.(w x n)) sin phi + (n.w)(S.n)(1 - cos phi).
+__device__ __forceinline__ void splat_sample(const ScatterParams &p, const ff *s, ff rr, float val) {
+    const ff Z = s[0];
+    // R^2 = |S|^2 - (S.n)^2 = (rr - Z)(rr + Z), without cancellation near the meridian
+    const float R2 = ff_mul(ff_sub(rr, Z), ff_add(rr, Z)).hi;
+    const float R = sqrtf(fmaxf(R2, 0.0f));
     const float dl = (float)p.delta_L;
-    const double v = val * (double)(dl / (R + dl));  // Eq. lorentz (a weight: FP32 is enough)
+    const double v = (double)(val * (dl / (R + dl)));  // Eq. lorentz (a weight: FP32 is enough)
     // Eqs. harmonic / solutions: P cos(phi) + Q sin(phi) = E with
     // P = k_in.S - D, Q = k_in.(n x S), D = (k_in.n)(n.S), E = -|S|^2/2 - D
-    const double D = p.kn * Z;
-    const double E = -0.5 * rr * rr - D;
-    const double Pp = p.il * s[3] - D, Qp = p.il * s[6];
-    const double inv = rsqrt_nr(Pp * Pp + Qp * Qp);
-    const double ratio = E * inv;
-    if (!(fabs(ratio) <= 1.0)) return;  // Eq. valid: no rotation reaches the Ewald sphere
-    // phi = phi0 +- delta with cos(phi0), sin(phi0) = (P, Q)/rpq, cos(delta) = ratio
-    const double c0 = Pp * inv, s0 = Qp * inv, cd = ratio;
-    const double t = (1.0 - ratio) * (1.0 + ratio);
-    const double sd = t > 1e-30 ? t * rsqrt_nr(t) : sqrt(t);
+    const ff D = ff_mul(ffv(p.kn_f), Z);
+    const ff E = ff_sub(ff_mul_f(ff_mul(rr, rr), -0.5f), D);
+    const ff Pp = ff_sub(ff_mul(ffv(p.il_f), s[3]), D), Qp = ff_mul(ffv(p.il_f), s[6]);
+    const ff rpq2 = ff_add(ff_mul(Pp, Pp), ff_mul(Qp, Qp));
+    if (!(rpq2.hi > 0.0f)) return;
+    const ff inv = ff_rsqrt(rpq2);
+    const ff cd = ff_mul(E, inv);
+    // Eq. valid: no rotation reaches the Ewald sphere unless |cos(delta)| <= 1
+    if (!(fabsf(cd.hi) < 1.0f || (fabsf(cd.hi) == 1.0f && cd.hi * cd.lo <= 0.0f))) return;
+    // phi = phi0 +- delta with cos(phi0), sin(phi0) = (P, Q)/rpq, cos(delta) = cd
+    const ff c0 = ff_mul(Pp, inv), s0 = ff_mul(Qp, inv);
+    const ff t = ff_mul(ff_add_f(ff_neg(cd), 1.0f), ff_add_f(cd, 1.0f));
+    const ff sd = t.hi > 1e-30f ? ff_mul(t, ff_rsqrt(t)) : ff{0.0f, 0.0f};
+    const ff c0cd = ff_mul(c0, cd), s0sd = ff_mul(s0, sd), s0cd = ff_mul(s0, cd), c0sd = ff_mul(c0, sd);
     for (int br = 0; br < 2; ++br) {
-        const double sgn = br == 0 ? 1.0 : -1.0;
-        const double cp = c0 * cd - sgn * s0 * sd, sp = s0 * cd + sgn * c0 * sd;
-        const double zc = Z * (1.0 - cp);
-        const double kb = p.kw[2] + s[3] * cp + s[6] * sp + p.nw[2] * zc;
-        if (!(kb > 0.0)) continue;
-        const double ku = p.kw[0] + s[1] * cp + s[4] * sp + p.nw[0] * zc;
-        const double kv = p.kw[1] + s[2] * cp + s[5] * sp + p.nw[1] * zc;
-        const double ib = p.dp * rcp_nr(kb);
-        const double xp = fma(ku, ib, p.hx), yp = fma(kv, ib, p.hy);
-        const double fi = floor(xp), fj = floor(yp);
-        if (!(fi >= 0.0) || !(fj >= 0.0) || fi >= (double)p.P.nx || fj >= (double)p.P.ny) continue;
+        const ff cp = br == 0 ? ff_sub(c0cd, s0sd) : ff_add(c0cd, s0sd);
+        const ff sp = br == 0 ? ff_add(s0cd, c0sd) : ff_sub(s0cd, c0sd);
+        const ff zc = ff_mul(Z, ff_add_f(ff_neg(cp), 1.0f));
+        const ff kb = ff_add(ff_add(ffv(p.kw_f[2]), ff_mul(s[3], cp)), ff_add(ff_mul(s[6], sp), ff_mul(ffv(p.nw_f[2]), zc)));
+        if (!(kb.hi > 0.0f)) continue;
+        const ff ku = ff_add(ff_add(ffv(p.kw_f[0]), ff_mul(s[1], cp)), ff_add(ff_mul(s[4], sp), ff_mul(ffv(p.nw_f[0]), zc)));
+        const ff kv = ff_add(ff_add(ffv(p.kw_f[1]), ff_mul(s[2], cp)), ff_add(ff_mul(s[5], sp), ff_mul(ffv(p.nw_f[1]), zc)));
+        const ff ib = ff_mul(ffv(p.dp_f), ff_rcp(kb));
+        const float fi = ff_floor(ff_add(ff_mul(ku, ib), ffv(p.hx_f)));
+        const float fj = ff_floor(ff_add(ff_mul(kv, ib), ffv(p.hy_f)));
+        if (!(fi >= 0.0f) || !(fj >= 0.0f) || fi >= (float)p.P.nx || fj >= (float)p.P.ny) continue;
         atomicAdd(&p.img64[(size_t)fj * p.P.nx + (size_t)fi], v);
     }
 }
@@ -129,8 +156,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     const int r = (int)(item / n_chunks), chunk = (int)(item % n_chunks);
     float *rec = s_rec[warp];
     load_record(p.P.recs, r, rec, lane);
-    const double *pr = p.proj + (size_t)r * SCAT_PROJ;
-    const double r0 = pr[22], hr = pr[23];
+    const float2 *pr = p.proj + (size_t)r * SCAT_PROJ;
 
     const int m = chunk * 32 + lane;
     const int n_valid = min(32, p.n_s - chunk * 32);
@@ -138,7 +164,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tc = ta;
     if (valid) ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
     // (S - D)/r0 in the reflection frame: (1 + rho) (c, c d1, c d2) - (1, 0, 0), rho = x_r h_r / r0
-    const float rho = tc.x * (float)pr[21];
+    const float rho = tc.x * pr[23].x;
     const ff u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
     const ff u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
     const ff u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
@@ -169,19 +195,21 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
         return;
     }
     if (!valid || !any) return;
-    const double I = (double)rec[REC_FR] * ((double)pa[0].s0.hi + (double)pa[0].s0.lo);
-    if (!(I != 0.0)) return;
+    const float I = rec[REC_FR] * (pa[0].s0.hi + pa[0].s0.lo);
+    if (!(I != 0.0f)) return;
     // projections of S = (r0 + x_r h_r) (c, c d1, c d2) in the reflection frame
-    // from the FP64 frame projections and the float-float table (no FP32
-    // rounding: the hit position of a sample near the edge of the Ewald
-    // condition is sensitive to S), and the volume element
-    const double rr = r0 + (double)tc.x * hr;
-    const double U0 = 1.0 + ((double)ta.x + (double)ta.y), U1 = (double)ta.z + (double)ta.w,
-                 U2 = (double)tb.x + (double)tb.y;
-    double sp[7];
+    // from the frame projections and the sample table, all float-float (the
+    // hit position of a sample near the edge of the Ewald condition is
+    // sensitive to S), and the volume element (a weight: FP32)
+    const ff rr = ff_add(ffv(pr[21]), ff_mul_f(ffv(pr[22]), tc.x));
+    const ff U0 = ff_add_f(ff{ta.x, ta.y}, 1.0f), U1 = {ta.z, ta.w}, U2 = {tb.x, tb.y};
+    ff sp[7];
 #pragma unroll
-    for (int j = 0; j < 7; ++j) sp[j] = rr * fma(U0, pr[3 * j], fma(U1, pr[3 * j + 1], U2 * pr[3 * j + 2]));
-    const double dV = (double)tb.w * hr * rr * rr;
+    for (int j = 0; j < 7; ++j)
+        sp[j] = ff_mul(rr, ff_add(ff_add(ff_mul(U0, ffv(pr[3 * j])), ff_mul(U1, ffv(pr[3 * j + 1]))),
+                                  ff_mul(U2, ffv(pr[3 * j + 2]))));
+    const float rrf = rr.hi + rr.lo;
+    const float dV = tb.w * pr[22].x * rrf * rrf;
     splat_sample(p, sp, rr, dV * I);
 }
 
