@@ -470,7 +470,7 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
             sp.n_atoms = a->n_atoms, sp.n_elem = a->n_elem, sp.n_refl = pr.n_refl;
             int n_split = 1, per = 1;
             sf_plan(a->n_atoms, pr.n_refl, a->n_elem, 64, n_split, per);
-            sp.n_split = n_split, sp.atoms_per_split = per;
+            sp.n_split = n_split;
             sp.frac = a->frac, sp.B = a->B, sp.occ = a->occ, sp.ff = a->ff, sp.elem = a->elem;
             sf_bind(&sp, ws + L.sf[m], a->n_atoms, pr.n_refl, 64);
             sp.hkl = pr.hkl, sp.F_out = F[m], sp.M_out = M[m];
@@ -680,7 +680,7 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
     p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
     int n_split = 1, per = 1;
     sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, 64, n_split, per);
-    p.n_split = n_split, p.atoms_per_split = per;
+    p.n_split = n_split;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
     sf_bind(&p, static_cast<char *>(workspace), atoms->n_atoms, n_refl, 64);
     p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;

@@ -210,7 +210,7 @@ cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mod
 cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s);
 
 struct SFParams {
-    int n_atoms, n_elem, n_refl, n_split, atoms_per_split;
+    int n_atoms, n_elem, n_refl, n_split;
     double As[9];
     const double *frac;
     const float *B, *occ, *ff;

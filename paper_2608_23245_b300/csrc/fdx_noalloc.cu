@@ -104,7 +104,7 @@ extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_ato
     cell_basis(*cell, A, As);
     memcpy(p.As, As, sizeof As);
     p.n_atoms = atoms->n_atoms, p.n_elem = atoms->n_elem, p.n_refl = n_refl;
-    p.n_split = n_split, p.atoms_per_split = per;
+    p.n_split = n_split;
     p.frac = atoms->frac, p.B = atoms->B, p.occ = atoms->occ, p.ff = atoms->ff, p.elem = atoms->elem;
     sf_bind(&p, static_cast<char *>(base), atoms->n_atoms, n_refl, max_split);
     p.hkl = hkl, p.F_out = F_out, p.M_out = M_out;
