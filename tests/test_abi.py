@@ -120,3 +120,66 @@ def test_structure_factor_argument_checks(fdx):
     assert need > 0
     assert lib.fdx_structure_factors(C.byref(cell), C.byref(a), None, 5, C.c_void_p(16), C.c_void_p(16), None,
                                      C.c_void_p(256), need - 1, None) == -3
+
+
+def test_ring_and_scatter_argument_checks(fdx):
+    """Host-side rejections of the ring average and the scatter form (before
+    any device work): bad geometry, parallel axes, missing outputs or samples,
+    misaligned samples, short or misaligned workspace."""
+    lib = fdx.lib()
+    img = C.c_void_p(16)
+    for kw, code in (({"n_x": 0}, -1), ({"beam_axis": (0.0, 0.0, 1.0)}, -2)):
+        prob = _problem(fdx, **kw)
+        assert lib.fdx_ring(C.byref(prob), img, C.c_void_p(256), 1 << 30, None) == code
+        assert lib.fdx_scatter(C.byref(prob), 16, C.c_void_p(16), img, C.c_void_p(256), 1 << 30, None) == code
+    prob = _problem(fdx)
+    need = lib.fdx_ring_workspace_size(C.byref(prob))
+    assert need >= lib.fdx_workspace_size(1, fdx._problem_array([prob]))
+    assert lib.fdx_ring(C.byref(prob), None, C.c_void_p(256), need, None) == -1
+    assert lib.fdx_ring(C.byref(prob), img, C.c_void_p(256), need - 1, None) == -3
+    assert lib.fdx_ring(C.byref(prob), img, C.c_void_p(264), need, None) == -3
+    need_s = lib.fdx_scatter_workspace_size(C.byref(prob), 64)
+    assert need_s > lib.fdx_scatter_workspace_size(C.byref(prob), 32) > 0
+    assert lib.fdx_scatter(C.byref(prob), 0, C.c_void_p(16), img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, None, img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(24), img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(16), img, C.c_void_p(256), need_s - 1, None) == -3
+
+
+def test_ring_workspace_holds_the_split_partials(fdx):
+    """A small detector deals each reflection's azimuth points to several warps
+    per patch and needs room for their partial images; a detector of 1024 x
+    1024 pixels keeps one warp per patch and needs none."""
+    lib = fdx.lib()
+    small = _problem(fdx, n_x=30, n_y=24)
+    assert lib.fdx_ring_workspace_size(C.byref(small)) >= lib.fdx_workspace_size(1, fdx._problem_array([small])) \
+        + 8 * 30 * 24 * 2
+    big = _problem(fdx, n_x=1024, n_y=1024)
+    extra = lib.fdx_ring_workspace_size(C.byref(big)) - lib.fdx_workspace_size(1, fdx._problem_array([big]))
+    assert 0 < extra < 16 * 64 * 4 + 4096  # the ring records only
+
+
+def test_backward_and_loss_argument_checks(fdx):
+    """The adjoint covers the Hosemann lineshape only; missing inputs and short
+    workspaces are rejected on the host."""
+    lib = fdx._bind_refine(fdx.lib())
+    prob = _problem(fdx)
+    a = fdx.Atoms()
+    a.n_atoms, a.n_elem = 10, 4
+    a.frac = a.B = a.elem = a.ff = 16
+    g = fdx.Grads()
+    prob.br.lineshape = 0  # sinc: forward only
+    assert lib.fdx_pattern_backward(C.byref(prob), C.byref(a), C.c_void_p(16), C.c_void_p(16), C.byref(g),
+                                    C.c_void_p(256), 1 << 30, None) == -1
+    prob.br.lineshape = 1
+    assert lib.fdx_pattern_backward(C.byref(prob), C.byref(a), C.c_void_p(16), None, C.byref(g),
+                                    C.c_void_p(256), 1 << 30, None) == -1
+    need = lib.fdx_backward_workspace_size(C.byref(prob), 10, 4)
+    assert need > 0
+    assert lib.fdx_pattern_backward(C.byref(prob), C.byref(a), C.c_void_p(16), C.c_void_p(16), C.byref(g),
+                                    C.c_void_p(256), need - 1, None) == -3
+    loss = C.c_double(0.0)
+    assert lib.fdx_loss(0, C.c_void_p(16), C.c_void_p(16), None, C.byref(loss), None, C.c_void_p(256), 1 << 20,
+                        None) == -1
+    assert lib.fdx_loss(100, C.c_void_p(16), C.c_void_p(16), None, C.byref(loss), None, C.c_void_p(256),
+                        lib.fdx_loss_workspace_size(100) - 1, None) == -3
