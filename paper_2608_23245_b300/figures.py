@@ -13,8 +13,8 @@ the gather-form pattern); this module only selects rows and writes files.
     python -m paper_2608_23245_b300.figures --out DIR [--gvl-px 511] [--equator-px 1023]
 
 writes ``gvl_gauss.npy``, ``gvl_lorentz.npy`` (float32 images, row j along
-+fiber) and ``equator.npz`` (one profile per (g, B), with the pixel centres'
-distance from the beam centre in mm).
++fiber) with log-scaled ``.pgm`` views, and ``equator.npz`` (one profile per
+(g, B), with the pixel centres' distance from the beam centre in mm).
 """
 from __future__ import annotations
 
@@ -67,6 +67,22 @@ def equator_profiles(params: Iterable[Tuple[float, float]] = EQUATOR_PARAMS, n_x
     return x_mm, out
 
 
+def write_pgm(path: str, image: np.ndarray, decades: float = 4.0) -> None:
+    """An 8-bit binary PGM of log10(image / max) over the top `decades`, row 0
+    at the top (the image's last row, +fiber), for viewing without a plotting
+    library."""
+    img = np.asarray(image, dtype=np.float64)
+    mx = float(img.max()) if img.size else 0.0
+    if mx > 0:
+        x = np.log10(np.maximum(img / mx, 10.0 ** -decades)) / decades + 1.0
+    else:
+        x = np.zeros_like(img)
+    g = np.clip(np.rint(255.0 * x), 0, 255).astype(np.uint8)[::-1]
+    with open(path, "wb") as f:
+        f.write(b"P5\n%d %d\n255\n" % (g.shape[1], g.shape[0]))
+        f.write(np.ascontiguousarray(g).tobytes())
+
+
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", required=True)
@@ -76,6 +92,7 @@ def main(argv=None) -> None:
     os.makedirs(a.out, exist_ok=True)
     for k, img in gvl_images(a.gvl_px).items():
         np.save(os.path.join(a.out, "gvl_%s.npy" % k), img)
+        write_pgm(os.path.join(a.out, "gvl_%s.pgm" % k), img)
     x_mm, prof = equator_profiles(n_x=a.equator_px)
     keys = sorted(prof)
     np.savez(os.path.join(a.out, "equator.npz"), x_mm=x_mm, g=np.array([k[0] for k in keys]),

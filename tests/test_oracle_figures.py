@@ -48,3 +48,18 @@ def test_gvl_azimuthal_tails(orc, h):
     for got, ref in ((g[1:], ga), (lz[1:], la)):
         assert np.all(np.abs(np.asarray(got) / ref - 1.0) < 0.35), (got, ref)
     assert lz[2] > 2.0 * g[2]  # the Lorentzian's heavy tail
+
+
+def test_pgm_writer(tmp_path):
+    """The figure writer's log-scaled 8-bit view: header, size, orientation
+    (last image row first) and the decade clamp."""
+    from paper_2608_23245_b300 import figures
+    img = np.array([[1e-6, 1e-2], [1.0, 0.0]])
+    path = tmp_path / "x.pgm"
+    figures.write_pgm(str(path), img, decades=4.0)
+    raw = path.read_bytes()
+    head = b"P5\n2 2\n255\n"
+    assert raw.startswith(head)
+    px = np.frombuffer(raw[len(head):], np.uint8).reshape(2, 2)
+    assert px[0, 0] == 255 and px[0, 1] == 0          # image row 1 (1.0, 0.0) on top
+    assert px[1, 0] == 0 and px[1, 1] == 128          # 1e-6 clamps to 1e-4; 1e-2 is half-way
