@@ -160,18 +160,22 @@ int fdx_structure_factors(const fdx_cell *cell, const fdx_atoms *atoms, const fd
  * has no counterpart: this is a deployment convenience of the library.
  *   - No workspace argument: the kernels' scratch is a fixed array of
  *     FDX_NOALLOC_SF_SCRATCH_BYTES (8 MiB) in device memory that every GPU
- *     loading libfdx holds until the process exits.  It must fit 24.25 bytes per
- *     atom (plus 97 KiB of padding: the kernels keep the atoms sorted by
- *     element), 4 bytes per reflection, and 16 bytes per reflection per row of
- *     partial sums (the call uses as many rows as fit, at most 64); larger
- *     sizes return FDX_ERR_WORKSPACE before any work is queued.  The call
- *     allocates nothing.
+ *     loading libfdx holds until the process exits.  Each piece of the layout
+ *     is rounded up to 256 bytes; it must fit 24.25 bytes per atom (plus
+ *     96 KiB of padding: the kernels keep the atoms sorted by element),
+ *     4 bytes per reflection, and 16 bytes per reflection for every row of
+ *     partial sums.  Each element pass writes its own rows (one pass for up to
+ *     40 element types, two for 41-64), so at least `passes` rows must fit;
+ *     the call uses as many rows as fit, at most 64.  Larger sizes return
+ *     FDX_ERR_WORKSPACE before any work is queued.  The call allocates
+ *     nothing.
  *   - The first call on a device looks up the array's address on that device
  *     and caches it; make that first call before any stream capture.
  *   - All calls share the array.  Calls whose work overlaps on the GPU race on
  *     it: serialise them (one stream, or events between streams).  Nothing in
  *     it needs to start at zero.
- * Inputs, outputs and return codes as fdx_structure_factors.  Asynchronous.
+ * Inputs, outputs, argument checks and return codes as
+ * fdx_structure_factors.  Asynchronous.
  */
 #define FDX_NOALLOC_SF_SCRATCH_BYTES (8u << 20)
 int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_atoms *atoms, const fdx_broadening *br,

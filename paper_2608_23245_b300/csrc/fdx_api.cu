@@ -27,6 +27,10 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 bool finite3(const double *v) { return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]); }
 
+}  // namespace
+
+namespace fdx {
+
 int validate_cell(const fdx_cell *c) {
     if (!c) return FDX_ERR_ARG;
     const double v[6] = {c->a, c->b, c->c, c->alpha, c->beta, c->gamma};
@@ -60,6 +64,10 @@ int validate_broadening(const fdx_broadening *b) {
     if (!(b->K_z > 0) || !isfinite(b->K_z)) return FDX_ERR_ARG;
     return FDX_OK;
 }
+
+}  // namespace fdx
+
+namespace {
 
 int validate_geometry(const fdx_geometry *g) {
     if (!g) return FDX_ERR_ARG;

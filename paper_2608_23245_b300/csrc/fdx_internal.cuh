@@ -265,6 +265,13 @@ struct RingParams {
 };
 cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);
+// Element passes of the structure factors (form-factor tables of at most 40
+// types in shared memory): each pass writes its own n_split rows of partials.
+int sf_passes(int n_elem);
+
+// Host-side argument checks shared by the entry points (fdx_api.cu).
+int validate_cell(const fdx_cell *c);
+int validate_broadening(const fdx_broadening *b);
 size_t sf_bind(SFParams *p, char *ws, int n_atoms, int n_refl, int max_split);
 
 }  // namespace fdx

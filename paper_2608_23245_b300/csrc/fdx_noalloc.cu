@@ -36,12 +36,9 @@ using namespace fdx;
 namespace {
 
 constexpr size_t kScratchBytes = FDX_NOALLOC_SF_SCRATCH_BYTES;
-constexpr size_t kAlign = 256;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_sf_scratch[kScratchBytes];
-
-size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 std::mutex g_mu;
 void *g_ptr[kMaxDevices] = {nullptr};
@@ -65,37 +62,33 @@ int scratch_address(void **out) {
 extern "C" int fdx_structure_factors_noalloc(const fdx_cell *cell, const fdx_atoms *atoms,
                                              const fdx_broadening *br, int32_t n_refl, const int32_t *hkl,
                                              float *F_out, float *M_out, void *stream) {
-    if (!cell || !atoms) return FDX_ERR_ARG;
-    const double cv[6] = {cell->a, cell->b, cell->c, cell->alpha, cell->beta, cell->gamma};
-    for (double x : cv)
-        if (!isfinite(x)) return FDX_ERR_ARG;
-    if (cell->a <= 0 || cell->b <= 0 || cell->c <= 0) return FDX_ERR_GEOMETRY;
-    if (atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
+    // the same argument checks, in the same order, as fdx_structure_factors
+    int rc = validate_cell(cell);
+    if (rc) return rc;
+    if (!atoms || atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
     if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
     if (n_refl < 0) return FDX_ERR_ARG;
     if (n_refl > 0 && (!hkl || !F_out)) return FDX_ERR_ARG;
-    if (br) {
-        for (int i = 0; i < 3; ++i)
-            if (!(br->g[i] >= 0) || !isfinite(br->g[i]) || !isfinite(br->B_axis[i])) return FDX_ERR_ARG;
-        if (br->intensity_model != FDX_INTENSITY_NONE && br->intensity_model != FDX_INTENSITY_HOSEMANN)
-            return FDX_ERR_ARG;
-    }
+    if (br && (rc = validate_broadening(br))) return rc;
     if (n_refl == 0) return FDX_OK;
 
     // Scratch: packed atoms (uint4 + float2 each, element-sorted and padded),
     // the group list of the reflections (one int each) and one float4 partial
-    // per (partial row, reflection).  Use as many rows as fit, at most 64.
-    const size_t fixed = sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, 0);
-    const size_t per_split = sizeof(float4) * (size_t)n_refl;
-    if (fixed + align_up(per_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
-    int max_split = (int)((kScratchBytes - fixed) / per_split);
-    if (max_split > 64) max_split = 64;
+    // per (partial row, reflection).  Every element pass writes its own n_split
+    // rows, so at least `passes` rows must fit; use the largest row budget
+    // (at most 64) whose aligned layout fits the array.  sf_plan keeps
+    // passes * n_split within that budget.
+    const int passes = sf_passes(atoms->n_elem);
+    int max_split = 64;
+    while (max_split >= passes && sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, max_split) > kScratchBytes)
+        --max_split;
+    if (max_split < passes) return FDX_ERR_WORKSPACE;
     int n_split = 1, per = 1;
     sf_plan(atoms->n_atoms, n_refl, atoms->n_elem, max_split, n_split, per);
-    if (sf_bind(nullptr, nullptr, atoms->n_atoms, n_refl, max_split) > kScratchBytes) return FDX_ERR_WORKSPACE;
+    if (passes * n_split > max_split) return FDX_ERR_WORKSPACE;  // never taken: sf_plan caps n_split
 
     void *base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
 
     SFParams p;

@@ -494,7 +494,7 @@ __global__ void sf_reduce_kernel(SFParams p) {
 
 static size_t sf_align(size_t x) { return (x + 255) / 256 * 256; }
 
-static int sf_passes(int n_elem) { return (n_elem + SF_FE_MAX - 1) / SF_FE_MAX; }
+int sf_passes(int n_elem) { return (n_elem + SF_FE_MAX - 1) / SF_FE_MAX; }
 
 static int sm_count() {
     static int s_sm = 0;

@@ -37,11 +37,16 @@ def amp_scale(p, hkl):
     a = p.atoms
     from oracle import basis
     _, As = basis(p.cell)
-    s2 = np.sum((np.asarray(hkl, np.float64) @ As) ** 2, axis=1)
+    s2_all = np.sum((np.asarray(hkl, np.float64) @ As) ** 2, axis=1)
     ff = a.ff[a.elem]
-    f = ff[:, 8][None, :] + np.sum(ff[None, :, 0:4] * np.exp(-ff[None, :, 4:8] * s2[:, None, None] / 4), axis=2)
-    amp = a.occ[None, :] * f * np.exp(-a.B[None, :] * s2[:, None] / 4)
-    return np.sqrt(np.sum(amp * amp, axis=1))
+    out = np.empty(s2_all.shape[0])
+    step = max(1, (1 << 22) // max(1, 4 * a.n))   # reflections per chunk: bounded temporaries
+    for r0 in range(0, s2_all.shape[0], step):
+        s2 = s2_all[r0:r0 + step]
+        f = ff[:, 8][None, :] + np.sum(ff[None, :, 0:4] * np.exp(-ff[None, :, 4:8] * s2[:, None, None] / 4), axis=2)
+        amp = a.occ[None, :] * f * np.exp(-a.B[None, :] * s2[:, None] / 4)
+        out[r0:r0 + step] = np.sqrt(np.sum(amp * amp, axis=1))
+    return out
 
 
 SF_TOL = 2e-6   # |F_gpu - F_ref| <= SF_TOL * amp_scale per reflection

@@ -183,3 +183,58 @@ def test_backward_and_loss_argument_checks(fdx):
                         None) == -1
     assert lib.fdx_loss(100, C.c_void_p(16), C.c_void_p(16), None, C.byref(loss), None, C.c_void_p(256),
                         lib.fdx_loss_workspace_size(100) - 1, None) == -3
+
+
+def _noalloc_call(fdx, cell, n_atoms, n_elem, n_refl, br=None):
+    """fdx_structure_factors_noalloc with dummy device pointers: only calls
+    that fail validation or sizing may be made this way (nothing is read)."""
+    lib = fdx.lib()
+    c = fdx.make_cell(cell)
+    a = fdx.Atoms()
+    a.n_atoms, a.n_elem = n_atoms, n_elem
+    a.frac = a.B = a.elem = a.ff = 256
+    return lib.fdx_structure_factors_noalloc(C.byref(c), C.byref(a), C.byref(br) if br is not None else None,
+                                             n_refl, C.c_void_p(256), C.c_void_p(256), None, None)
+
+
+def test_noalloc_rejects_two_pass_problem_with_one_row_of_room(fdx):
+    """With more than 40 element types the structure factors take two element
+    passes, each writing its own row of partial sums.  2,000 atoms and 250,000
+    reflections leave room in the fixed 8 MiB scratch for one row of partials
+    (24 B per atom + 4 B per reflection + 16 B per reflection and row) but not
+    two: with 48 types the call must refuse (FDX_ERR_WORKSPACE) instead of
+    writing a second row past the scratch."""
+    orth = (50.0, 50.0, 70.0, math.pi / 2, math.pi / 2, math.pi / 2)
+    per_row = 16 * 250_000
+    assert 24 * 2000 + 4 * 250_000 + 2 * per_row > 8 << 20 > 24 * 2000 + 4 * 250_000 + per_row
+    assert _noalloc_call(fdx, orth, 2000, 48, 250_000) == -3
+
+
+def test_noalloc_validates_like_workspace_path(fdx):
+    """The allocation-free entry point refuses the same cells and broadening
+    parameters as fdx_structure_factors, with the same codes: a cell with an
+    angle outside (0, pi) or no volume is a geometry error, a broadening
+    record with a bad size, lineshape or node count an argument error."""
+    lib = fdx.lib()
+    from paper_2608_23245_b300 import workloads as W
+    p = W.small_helix()
+    a = fdx.Atoms()
+    a.n_atoms, a.n_elem = 100, 4
+    a.frac = a.B = a.elem = a.ff = 256
+    bad_cells = [(10.0, 10.0, 10.0, 0.0, math.pi / 2, math.pi / 2),
+                 (10.0, 10.0, 10.0, math.pi, math.pi / 2, math.pi / 2),
+                 (10.0, 10.0, 10.0, 2.0, 2.0, 2.3)]          # angles with no positive volume
+    for cell in bad_cells:
+        c = fdx.make_cell(cell)
+        ws = lib.fdx_structure_factors(C.byref(c), C.byref(a), None, 10, C.c_void_p(256), C.c_void_p(256), None,
+                                       C.c_void_p(256), 1 << 30, None)
+        na = _noalloc_call(fdx, cell, 100, 4, 10)
+        assert ws == na == -2, (cell, ws, na)
+    for field, value in (("L", (0.0, 1.0, 1.0)), ("lineshape", 7), ("n_nodes", 0), ("T", 0.0), ("K_z", -1.0)):
+        br = fdx.make_broadening(p.br)
+        setattr(br, field, type(getattr(br, field))(*value) if isinstance(value, tuple) else value)
+        c = fdx.make_cell(p.cell)
+        ws = lib.fdx_structure_factors(C.byref(c), C.byref(a), C.byref(br), 10, C.c_void_p(256), C.c_void_p(256),
+                                       None, C.c_void_p(256), 1 << 30, None)
+        na = _noalloc_call(fdx, p.cell, 100, 4, 10, br)
+        assert ws == na == -1, (field, ws, na)

@@ -30,10 +30,12 @@ def gpu():
     return fdx
 
 
-def _compare(gpu, make):
+def _compare(gpu, make, n_refl=None):
     import torch
     p = api_precision(make())
     hkl_host = gpu.fdx_reflections(p.cell, p.d_min, p.d_max)
+    if n_refl is not None:
+        hkl_host = np.ascontiguousarray(hkl_host[:n_refl])
     hkl = torch.as_tensor(hkl_host, device="cuda")
     atoms = gpu.DeviceAtoms(p.atoms)
     F_ref, M_ref = gpu.fdx_structure_factors(p.cell, atoms, hkl, p.br)
@@ -82,3 +84,31 @@ def test_noalloc_rejects_oversize(gpu):
     rc = lib.fdx_structure_factors_noalloc(C.byref(c), C.byref(a), None, 1 << 20, C.c_void_p(256),
                                            C.c_void_p(256), None, None)
     assert rc == -3
+
+
+def _two_pass_tight():
+    """400 atoms over 48 element types (two element passes) in the 50 x 50 x
+    70 A cell, d >= 1.5 A; the first 200,000 reflections of that list are
+    used.  The fixed scratch then holds exactly two rows of partial sums (one
+    per element pass) and not three."""
+    import math
+    rng = np.random.default_rng(48200)
+    n, n_elem = 400, 48
+    ff = np.concatenate([rng.uniform(0.5, 3.0, (n_elem, 4)), rng.uniform(0.5, 40.0, (n_elem, 4)),
+                         rng.uniform(0.0, 1.0, (n_elem, 1))], axis=1)
+    atoms = W.Atoms(frac=rng.uniform(0.0, 1.0, (n, 3)), B=rng.uniform(10.0, 30.0, n), occ=np.ones(n),
+                    elem=rng.integers(0, n_elem, n).astype(np.uint8), ff=ff)
+    br = W.Broadening(L=(300.0, 300.0, 300.0), g=(0.01, 0.01, 0.01), B_axis=(2.0, 3.0, 1.0), gamma=math.radians(4),
+                      T=W.patch_extent(0.0, math.radians(4)), n_nodes=16)
+    geom = W.Geometry(wavelength=1.0, distance=200.0, pixel=0.075, n_x=16, n_y=16)
+    return W.Problem("two_pass_tight", (50.0, 50.0, 70.0, math.pi / 2, math.pi / 2, math.pi / 2), atoms, 1.5, 0.0,
+                     br, geom)
+
+
+def test_noalloc_two_passes_tight_fit(gpu):
+    """Two element passes when only two rows of partials fit: the call uses one
+    atom split per pass (two rows in all) and matches the workspace path.
+    Sizes: 24 B per atom + 4 B per reflection + 16 B per reflection and row."""
+    n_refl = 200_000
+    assert 24 * 400 + 4 * n_refl + 2 * 16 * n_refl < 8 << 20 < 24 * 400 + 4 * n_refl + 3 * 16 * n_refl
+    _compare(gpu, _two_pass_tight, n_refl=n_refl)
