@@ -55,7 +55,6 @@ extern "C" {
 #define FDX_ERR_WORKSPACE (-3) /* workspace too small or misaligned (256-byte alignment) */
 #define FDX_ERR_CUDA (-4)      /* a CUDA runtime call or kernel launch failed */
 #define FDX_ERR_CAPACITY (-5)  /* output capacity too small */
-#define FDX_ERR_TIMEOUT (-6)   /* reserved: bounded device wait expired */
 
 #define FDX_LINESHAPE_SINC 0     /* K = N sinc^2(N t), N = 1/beta, |t| <= min(K_z/N, 1/2) (Eq. I_shape) */
 #define FDX_LINESHAPE_HOSEMANN 1 /* K = beta/(beta^2 + (1-beta^2) sin^2(pi t)), |t| <= 1/2 (Eq. Z) */
@@ -354,6 +353,19 @@ typedef struct fdx_tuning {
  * depend on adj_bands: query them after setting. */
 int fdx_set_tuning(const fdx_tuning *t);
 int fdx_get_tuning(fdx_tuning *t);
+
+/*
+ * fdx_status -- wait for the work queued on `stream` (NULL: the legacy
+ * default stream) and report how it ended.  The library's calls are
+ * asynchronous after validation, so a fault inside a kernel surfaces only
+ * here (or at the caller's next synchronisation).  *device_status (may be
+ * NULL) receives the CUDA error code of the stream's work (0 = success).
+ * Returns FDX_OK, or FDX_ERR_CUDA when that work failed.  No kernel of the
+ * library waits on another kernel, a flag or a peer (the persistent kernels
+ * take independent work items from an atomic counter), so there is no
+ * device-side wait that could time out.
+ */
+int fdx_status(void *stream, int *device_status);
 
 /* Human-readable text for a return code (static storage). */
 const char *fdx_error_string(int code);

@@ -586,6 +586,12 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
 
 int fdx_version(void) { return 100; }
 
+int fdx_status(void *stream, int *device_status) {
+    const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (device_status) *device_status = (int)e;
+    return e == cudaSuccess ? FDX_OK : FDX_ERR_CUDA;
+}
+
 int fdx_set_tuning(const fdx_tuning *t) {
     fdx_tuning v = {2, 4, 3, 64};
     if (t) {
@@ -613,7 +619,6 @@ const char *fdx_error_string(int code) {
         case FDX_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
         case FDX_ERR_CUDA: return "CUDA runtime error";
         case FDX_ERR_CAPACITY: return "output capacity too small";
-        case FDX_ERR_TIMEOUT: return "bounded device wait expired";
         default: return "unknown error";
     }
 }

@@ -187,6 +187,18 @@ def fdx_version() -> int:
     return int(lib().fdx_version())
 
 
+def fdx_status(stream=None) -> int:
+    """Wait for the stream's queued work; returns its CUDA error code (0 =
+    success) and raises FdxError when that work failed."""
+    L = lib()
+    L.fdx_status.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    code = C.c_int(0)
+    rc = L.fdx_status(_stream(stream), C.byref(code))
+    if rc != 0:
+        raise FdxError(rc, "fdx_status: CUDA error %d on the stream" % code.value)
+    return code.value
+
+
 def fdx_reflections(cell, d_min, d_max=0.0) -> np.ndarray:
     """Reflection list as a host int32 [n, 3] array (count, then fill)."""
     c = make_cell(cell)

@@ -34,7 +34,7 @@ def test_exports_every_declared_symbol(fdx):
 
 def test_version_and_errors(fdx):
     assert fdx.fdx_version() >= 100
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5):
         assert fdx.error_string(code)
     assert fdx.error_string(1234) == "unknown error"
 
@@ -238,3 +238,18 @@ def test_noalloc_validates_like_workspace_path(fdx):
                                        None, C.c_void_p(256), 1 << 30, None)
         na = _noalloc_call(fdx, p.cell, 100, 4, 10, br)
         assert ws == na == -1, (field, ws, na)
+
+
+def test_status_reports_cuda_failure_without_device(fdx):
+    """fdx_status waits for a stream and reports how its work ended; on a
+    machine without a usable CUDA device the wait itself fails, which must
+    come back as FDX_ERR_CUDA with the nonzero CUDA code (never FDX_OK)."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present: the GPU tests cover fdx_status")
+    lib = fdx.lib()
+    lib.fdx_status.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+    code = C.c_int(0)
+    assert lib.fdx_status(None, C.byref(code)) == -4
+    assert code.value != 0
+    assert lib.fdx_status(None, None) == -4

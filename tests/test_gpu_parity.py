@@ -321,3 +321,11 @@ def test_mirror_symmetry_gpu(gpu):
     s = img.max()
     assert np.max(np.abs(img - img[:, ::-1])) <= 2e-6 * s
     assert np.max(np.abs(img - img[::-1, :])) <= 2e-6 * s
+
+
+def test_status_after_work(gpu):
+    """fdx_status on the stream of a finished forward pass: success, code 0."""
+    p = api_precision(W.small_helix())
+    sim = gpu.Simulation(p)
+    sim.forward()
+    assert gpu.fdx_status() == 0
