@@ -1,12 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the fiber-diffraction hot path on one B300 (or N replicas).
 
-One step = the whole forward path for the 2,000-atom helical fiber model
-(hexagonal 20x20x28 A cell, d >= 2.0 A: 5,062 reflections; Voigt orientation
-3 deg / 2 deg; Hosemann g = 2 % along a and b; 64x64 shell nodes; 1024^2
-detector): structure factors (fdx_structure_factors) then the
-Lorentz-corrected pattern (fdx_pattern, which includes the per-call pixel
-geometry, node-table and reflection set-up kernels).
+One step = the whole forward path of the large forward workload (20,000
+uniform atoms in a 50 x 50 x 70 A cell, d >= 1.5 A: 217,252 reflections;
+Lorentzian orientation 4 deg; crystallite size 300 A; Hosemann g = 1 %;
+128 x 128 shell nodes; 2048 x 2048 detector of 0.075 mm pixels at 200 mm):
+structure factors (fdx_structure_factors) then the Lorentz-corrected pattern
+(fdx_pattern, which includes the per-call pixel geometry, node-table and
+reflection set-up kernels).
 
 Metric: pixel-reflection-node evaluations per second, where the evaluation
 count E is the number of (pixel, reflection, node) terms inside the lineshape
@@ -16,10 +17,11 @@ to flush L2 (outside the per-step CUDA events).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Under torchrun (N > 1) every rank runs an independent replica (weak scaling,
-no collective on the data path); value = all ranks' evaluations / max time.
-`--impl reference` times the FP64 CPU oracle on a bounded pixel sample of the
-same workload on the host cores.
+Under torchrun (N > 1) every rank runs its own copy of the step (independent
+problems: weak scaling, no collective on the data path); value = all ranks'
+evaluations / max time.  The batched-refinement leg shards its models over
+the ranks.  `--impl reference` times the FP64 CPU oracle on a bounded pixel
+sample of the same workload on the host cores.
 """
 from __future__ import annotations
 
@@ -38,28 +40,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pixel·reflection-node evals/s"
 UNIT = "evals/s"
-WORKLOAD = "helix_2000atoms_hex20x20x28_dmin2.0_voigt3-2deg_g2pct_nodes64_det1024"
-# Algorithmic FP32 operations per in-support evaluation (Hosemann lineshape),
-# counting an FMA as two: t_i = tau_i - sigma_i (3); sin^2(pi t) by a degree-6
-# polynomial in t^2 (3 x 14); Hosemann denominators (3 x 2); their product (2);
-# reciprocal (1); weight (1); accumulation (1).
-FLOPS_PER_EVAL = 55
-# Structure factors, FP32 flops per atom-reflection term (FMA = 2, exp2 = 1).
-# Direct evaluation of each term: remainder to float (5); r^2 (1); sin and cos
-# polynomials (14); sin = r * poly (1); amplitude exponent (2) and exp2 (1);
-# form factor (1); two accumulating FMAs (4): 29 -> 30.  The kernel evaluates
-# groups of four consecutive-l reflections: per group and atom, remainder
-# scale (1), r^2 (1), polynomials (19), three complex rotations (18), and per
-# term exponent (2), exp2 (1), accumulation (4): 67 / 4; the form factor
-# multiplies each 64-atom chunk's sum (2 per term and chunk): + 2 / 64.
-SF_FLOPS_DIRECT_PER_TERM = 30
-SF_FLOPS_PER_TERM = 16.78125
-# DRAM bytes (read + written) of one forward pattern_kernel<Hosemann> launch
-# of this step, from an ncu --set full capture of it: 18.21 MB read (pixel
-# geometry at 16 B per pixel, reflection records, node tables), 0 written (the
-# 4 MB image stays in L2 during the launch).  Valid only for the kernel as
-# captured: set to None whenever the pattern kernel changes.
-PATTERN_DRAM_BYTES = 18210048
+WORKLOAD = "large_forward_20000atoms_orth50x50x70_dmin1.5_lorentz4deg_L300_g1pct_nodes128_det2048"
+# Roofline basis of the pattern kernel: the algorithm's FP32 operations per
+# in-support evaluation, counted as instructions (an FMA is one): the three
+# lattice coordinates t_i (9 FMA), per axis a sine, a reciprocal and about
+# four FMA for the lineshape, the support test and the accumulating FMA --
+# about 25 FP32 operations and 6 SFU operations per evaluation.
+OPS_PER_EVAL = 25
+SFU_PER_EVAL = 6
+# Structure factors, per atom-reflection term: the phase, one sincos, one
+# exp2 and a multiply for the Debye-Waller amplitude, 2-6 FMA for the
+# compensated sum -- about 10 FP32 operations and 2-3 SFU operations.
+SF_OPS_PER_TERM = 10
+# DRAM bytes (read + written) of one forward pattern_kernel launch of this
+# step, from an ncu capture of it (dram__bytes_read.sum +
+# dram__bytes_write.sum).  Valid only for the kernel as captured: None
+# whenever the pattern kernel changes.
+PATTERN_DRAM_BYTES = None
 
 
 def _peaks():
@@ -69,9 +66,46 @@ def _peaks():
         return {}
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """148 SMs x 128 FP32 lanes x 2 flop per FMA x clock."""
-    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def sm_max_mhz() -> float:
+    return float(_peaks().get("sm_max_mhz", 2032.0))
+
+
+def fp32_peak_tops(mhz: float) -> float:
+    """Nominal FP32-pipe peak in Tera lane-operations/s: 148 SMs x 128 FP32
+    lanes x clock (an FMA is one operation).  Not measured: the measured-peaks
+    file carries HBM and bf16 figures only."""
+    return 148 * 128 * mhz * 1e6 / 1e12
+
+
+def xu_peak_tops(mhz: float) -> float:
+    """Nominal SFU (XU pipe) peak: 148 SMs x 16 lanes x clock."""
+    return 148 * 16 * mhz * 1e6 / 1e12
+
+
+def pattern_roofline(E: float, seconds: float) -> dict:
+    """FP32-pipe fraction of a pattern launch on the algorithm's 25 operations
+    per in-support evaluation, and the SFU fraction on its 6 SFU operations."""
+    mhz = sm_max_mhz()
+    ach = OPS_PER_EVAL * E / seconds / 1e12
+    xu = SFU_PER_EVAL * E / seconds / 1e12
+    return {"achieved": ach, "peak": fp32_peak_tops(mhz), "frac": ach / fp32_peak_tops(mhz),
+            "xu_achieved": xu, "xu_peak": xu_peak_tops(mhz), "xu_frac": xu / xu_peak_tops(mhz)}
+
+
+def _timed(fn, k, w=1):
+    """Mean seconds of fn over k calls after w warm-up calls (CUDA events on
+    the current stream, synchronised on both sides)."""
+    import torch
+    for _ in range(w):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(k):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / k
 
 
 class ClockSampler:
@@ -137,12 +171,42 @@ def max_over_ranks(x, world):
     return replicas.max_over_ranks(x, world, "cuda")
 
 
-def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
+def helix_measurements(steps=10, warmup=3):
+    """The helical fiber model (2,000 atoms, hexagonal 20 x 20 x 28 A, 5,062
+    reflections, Voigt 3/2 deg, g = 2 % along a and b, 64^2 nodes, 1024^2
+    detector): the same SF + pattern step, L2 flushed between steps."""
+    import torch
+    from paper_2608_23245_b300 import fdx, workloads as W
+    sim = fdx.Simulation(W.config1())
+    sim.forward()
+    E = int(sim.evals().to(torch.int64).sum().item())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(warmup):
+        flush.fill_(1)
+        sim.forward()
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for s in range(steps):
+        flush.fill_(s & 0xff)
+        ev[s][0].record()
+        sim.structure_factors()
+        ev[s][1].record()
+        sim.pattern()
+        ev[s][2].record()
+    torch.cuda.synchronize()
+    step = sum(e[0].elapsed_time(e[2]) for e in ev) / steps / 1e3
+    pat = sum(e[1].elapsed_time(e[2]) for e in ev) / steps / 1e3
+    return {"workload": "helix_2000atoms_hex20x20x28_dmin2.0_voigt3-2deg_g2pct_nodes64_det1024",
+            "evals_per_step": E, "ms_per_step": 1e3 * step, "evals_per_s": E / step, "pattern_ms": 1e3 * pat,
+            "pattern_roofline": pattern_roofline(E, pat)}
+
+
+def refine_measurements(steps=5, warmup=2, rois=(256, 512), plain_steps=3):
     """Refinement step = structure factors + pattern + loss + hand-written
-    adjoint (all gradients), on the config-3 model against its perturbed
-    target.  Timed at full size for the FP32 path, and on a central roi x roi
-    detector for both the FP32 path and the plain FP64 GPU form of the same
-    method (models/s = 1 / step time)."""
+    adjoint (all gradients), on the helix model against its seeded perturbed
+    target.  Timed at full size for the FP32 path, and on central roi x roi
+    detectors (same pixel size) for both the FP32 path and the plain FP64 GPU
+    form of the same method (models/s = 1 / step time)."""
     import torch
     from dataclasses import replace
     from paper_2608_23245_b300 import fdx, workloads as W
@@ -150,9 +214,8 @@ def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
 
     def fp32_setup(m, t):
         sim = fdx.Simulation(m)
-        tsim = fdx.Simulation(t)
-        It = tsim.forward().clone()
-        na, n = m.atoms.n, sim.hkl.shape[0]
+        It = fdx.Simulation(t).forward().clone()
+        na = m.atoms.n
         bufs = dict(gI=torch.empty_like(sim.image), loss=torch.empty((), dtype=torch.float64, device="cuda"),
                     dfrac=torch.empty((na, 3), dtype=torch.float64, device="cuda"),
                     dB=torch.empty(na, dtype=torch.float64, device="cuda"),
@@ -168,107 +231,79 @@ def refine_measurements(steps=5, warmup=2, roi=256, plain_steps=1):
                                      None, bufs["bws"])
         return step
 
-    def timed(step, k, w):
-        for _ in range(w):
-            step()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(k):
-            step()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / k
+    full = _timed(fp32_setup(model, target), steps, warmup)
+    out = {"workload": "helix model vs seeded perturbed target: SF + pattern + loss + adjoint",
+           "fp32_models_per_s": 1.0 / full, "fp32_ms_per_step": 1e3 * full, "roi": {}}
+    for k, roi in enumerate(rois):
+        mr = replace(model, geom=replace(model.geom, n_x=roi, n_y=roi))
+        tr = replace(target, geom=replace(target.geom, n_x=roi, n_y=roi))
+        roi32 = _timed(fp32_setup(mr, tr), steps, warmup)
+        sim = fdx.Simulation(mr)
+        It = fdx.Simulation(tr).forward().to(torch.float64)
+        img = torch.empty((roi, roi), dtype=torch.float64, device="cuda")
+        loss = torch.empty((), dtype=torch.float64, device="cuda")
+        dfrac = torch.empty((mr.atoms.n, 3), dtype=torch.float64, device="cuda")
+        dB = torch.empty(mr.atoms.n, dtype=torch.float64, device="cuda")
+        dglob = torch.empty(8, dtype=torch.float64, device="cuda")
+        ws = torch.empty(fdx.fdx_plain64_workspace_size(sim.prob, mr.atoms.n, sim.atoms.ff.shape[0]),
+                         dtype=torch.uint8, device="cuda")
 
-    full = timed(fp32_setup(model, target), steps, warmup)
-    mr = replace(model, geom=replace(model.geom, n_x=roi, n_y=roi))
-    tr = replace(target, geom=replace(target.geom, n_x=roi, n_y=roi))
-    roi32 = timed(fp32_setup(mr, tr), steps, warmup)
-    sim = fdx.Simulation(mr)
-    It = fdx.Simulation(tr).forward().to(torch.float64)
-    img = torch.empty((roi, roi), dtype=torch.float64, device="cuda")
-    loss = torch.empty((), dtype=torch.float64, device="cuda")
-    dfrac = torch.empty((mr.atoms.n, 3), dtype=torch.float64, device="cuda")
-    dB = torch.empty(mr.atoms.n, dtype=torch.float64, device="cuda")
-    dglob = torch.empty(8, dtype=torch.float64, device="cuda")
-    ws = torch.empty(fdx.fdx_plain64_workspace_size(sim.prob, mr.atoms.n, sim.atoms.ff.shape[0]), dtype=torch.uint8,
-                     device="cuda")
-
-    def plain_step():
-        fdx.fdx_plain64_refine(sim.prob, sim.atoms, img, It, None, loss, dfrac, dB, dglob, ws)
-    roi64 = timed(plain_step, plain_steps, 1)
-    return {"workload": "helix model vs seeded perturbed target (config-3 recipe): SF + pattern + loss + adjoint",
-            "fp32_models_per_s": 1.0 / full, "fp32_ms_per_step": 1e3 * full,
-            "roi": "central %dx%d pixels (same pixel size)" % (roi, roi),
-            "fp32_roi_models_per_s": 1.0 / roi32, "plain_fp64_roi_models_per_s": 1.0 / roi64,
-            "fp32_over_plain_fp64_roi": roi64 / roi32}
+        def plain_step():
+            fdx.fdx_plain64_refine(sim.prob, sim.atoms, img, It, None, loss, dfrac, dB, dglob, ws)
+        # the first region warms the plain kernels up; the larger one needs no extra step
+        roi64 = _timed(plain_step, plain_steps, 1 if k == 0 else 0)
+        out["roi"]["%dx%d" % (roi, roi)] = {
+            "fp32_models_per_s": 1.0 / roi32, "plain_fp64_models_per_s": 1.0 / roi64,
+            "fp32_over_plain_fp64": roi64 / roi32, "fp32_steps": steps, "plain_fp64_steps": plain_steps}
+    return out
 
 
-def large_measurements(g=0.01, reps=2, roi=128):
-    """Large forward (config-2 recipe: 20,000 atoms, 217,252 reflections,
-    128^2 nodes, 2048^2 detector): the structure-factor kernel at full size
-    (atom x reflection terms/s and its FP32 roofline fraction), the FP32
-    forward pattern at full size (evals/s), and the FP32 forward against the
-    plain FP64 GPU form on a central roi x roi detector (same pixel size)."""
+def large_extras(sim, E, reps=2, roi=128):
+    """On the headline workload: the structure-factor kernel chain alone
+    (atom x reflection terms/s and its FP32-pipe fraction), the FP32 forward
+    against the plain FP64 GPU form on a central roi x roi detector (same
+    pixel size), and the g = 4 % variant's forward pattern."""
     import torch
     from dataclasses import replace
     from paper_2608_23245_b300 import fdx, workloads as W
-    p = W.config2(g)
-    sim = fdx.Simulation(p)
+    p = sim.problem
     n_refl, n_atoms = int(sim.hkl.shape[0]), p.atoms.n
-
-    def timed(fn, k):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(k):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / k
-
-    t_sf = timed(sim.structure_factors, 3)
+    t_sf = _timed(sim.structure_factors, 5, 1)
     terms = n_refl * n_atoms
-    peaks = _peaks()
-    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
-    sf_tflops = SF_FLOPS_PER_TERM * terms / t_sf / 1e12
-    sf_direct = SF_FLOPS_DIRECT_PER_TERM * terms / t_sf / 1e12
-    sim.forward()
-    E = int(sim.evals().to(torch.int64).sum().item())
-    t_fwd = timed(sim.pattern, reps)
+    mhz = sm_max_mhz()
+    sf_ops = SF_OPS_PER_TERM * terms / t_sf / 1e12
     pr = replace(p, geom=replace(p.geom, n_x=roi, n_y=roi))
     rs = fdx.Simulation(pr)
     rs.forward()
     E_roi = int(rs.evals().to(torch.int64).sum().item())
-    t_roi32 = timed(rs.pattern, reps)
+    t_roi32 = _timed(rs.pattern, reps, 1)
     img = torch.empty((roi, roi), dtype=torch.float64, device="cuda")
     ws = torch.empty(fdx.fdx_plain64_workspace_size(rs.prob, n_atoms, rs.atoms.ff.shape[0]), dtype=torch.uint8,
                      device="cuda")
-    t_roi64 = timed(lambda: fdx.fdx_plain64_refine(rs.prob, rs.atoms, img, None, None, None, None, None, None, ws), 1)
+    t_roi64 = _timed(lambda: fdx.fdx_plain64_refine(rs.prob, rs.atoms, img, None, None, None, None, None, None, ws),
+                     reps, 1)
     rel = float((rs.image.to(torch.float64) - img).abs().max() / img.abs().max())
-    return {"workload": "config-2 recipe: 20,000 atoms, 50x50x70 A, d >= 1.5 A, Lorentzian 4 deg, L = 300 A, "
-                        "g = %g, 128^2 nodes, 2048^2 detector (0.075 mm, 200 mm)" % g,
-            "n_refl": n_refl, "n_atoms": n_atoms,
-            "sf_terms_per_s": terms / t_sf, "sf_ms": 1e3 * t_sf,
-            "sf_roofline": {"bound": "alu", "achieved": sf_tflops, "peak": peak, "unit": "TFLOP/s",
-                            "frac": sf_tflops / peak,
-                            "basis": "%.5g executed FP32 flops per atom-reflection term (groups of four "
-                                     "consecutive-l reflections share one sin/cos per atom; exp2 counted as one)"
-                                     % SF_FLOPS_PER_TERM,
-                            "direct_equivalent": {"flops_per_term": SF_FLOPS_DIRECT_PER_TERM, "achieved": sf_direct,
-                                                  "frac": sf_direct / peak}},
-            "pattern_evals": E, "pattern_ms": 1e3 * t_fwd, "pattern_evals_per_s": E / t_fwd,
-            "pattern_frac_of_fp32_peak": FLOPS_PER_EVAL * E / t_fwd / 1e12 / peak,
+    del rs
+    s4 = fdx.Simulation(W.config2(0.04))
+    s4.forward()
+    E4 = int(s4.evals().to(torch.int64).sum().item())
+    t4 = _timed(s4.pattern, reps, 1)
+    return {"sf_terms_per_s": terms / t_sf, "sf_ms": 1e3 * t_sf,
+            "sf_roofline": {"bound": "alu", "achieved": sf_ops, "peak": fp32_peak_tops(mhz), "unit": "Tops/s",
+                            "frac": sf_ops / fp32_peak_tops(mhz),
+                            "basis": "%d FP32 operations per atom-reflection term (the direct sum's count; FMA = 1); "
+                                     "nominal FP32-pipe peak" % SF_OPS_PER_TERM},
             "roi": "central %dx%d pixels" % (roi, roi), "roi_evals": E_roi,
             "fp32_roi_forward_ms": 1e3 * t_roi32, "plain_fp64_roi_forward_ms": 1e3 * t_roi64,
-            "fp32_over_plain_fp64_roi": t_roi64 / t_roi32, "roi_max_rel_diff_fp32_vs_fp64": rel}
+            "fp32_over_plain_fp64_roi": t_roi64 / t_roi32, "roi_max_rel_diff_fp32_vs_fp64": rel,
+            "g4pct": {"evals": E4, "pattern_ms": 1e3 * t4, "evals_per_s": E4 / t4,
+                      "pattern_roofline": pattern_roofline(E4, t4)}}
 
 
 def ring_measurements(roi=128, reps=2):
     """Ring-integrated cylindrical average (Eq. cyl-average) on the central
-    roi x roi pixels of the headline workload (same pixel size): evaluations
-    per second, and the time of the same pixels by the default gather form."""
+    roi x roi pixels of the helix workload (same pixel size): evaluations per
+    second, and the time of the same pixels by the default gather form."""
     import torch
     from dataclasses import replace
     from paper_2608_23245_b300 import fdx, workloads as W
@@ -279,28 +314,16 @@ def ring_measurements(roi=128, reps=2):
     ws = torch.empty(fdx.fdx_ring_workspace_size(sim.prob), dtype=torch.uint8, device="cuda")
     out = torch.empty_like(sim.image)
     E = int(sim.ring_evals(ws).to(torch.int64).sum().item())
-
-    def timed(fn):
-        fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / reps
-
-    t = timed(lambda: sim.ring(out, ws))
-    tg = timed(sim.pattern)
+    t = _timed(lambda: sim.ring(out, ws), reps, 1)
+    tg = _timed(sim.pattern, reps, 1)
     return {"workload": "helix config, central %dx%d pixels (0.1 mm), 64^2 nodes, azimuth rule of the ring average"
                         % (roi, roi),
             "evals": E, "ms": 1e3 * t, "evals_per_s": E / t, "gather_ms_same_pixels": 1e3 * tg,
-            "frac_of_fp32_peak": FLOPS_PER_EVAL * E / t / 1e12 / fp32_peak_tflops(_peaks().get("sm_max_mhz", 2032.0))}
+            "roofline": pattern_roofline(E, t)}
 
 
 def scatter_measurements(grid=(16, 16, 16), reps=2):
-    """Scatter form (the paper's own pipeline) on the headline workload:
+    """Scatter form (the paper's own pipeline) on the helix workload:
     n_r x n_1 x n_2 stratified samples per reflection (4,096 by default; the
     paper's tutorial uses 5,000), each evaluated by the direct sum, Lorentz
     corrected, rotated into the Ewald condition and added to its pixels.
@@ -315,36 +338,31 @@ def scatter_measurements(grid=(16, 16, 16), reps=2):
     ws = torch.empty(fdx.fdx_scatter_workspace_size(sim.prob, xs.shape[0]), dtype=torch.uint8, device="cuda")
     out = torch.empty_like(sim.image)
     E = int(sim.scatter_evals(xs, ws).item())
-    sim.scatter(xs, out, ws)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        sim.scatter(xs, out, ws)
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
+    t = _timed(lambda: sim.scatter(xs, out, ws), reps, 1)
     n_samples = int(sim.hkl.shape[0]) * int(xs.shape[0])
     return {"workload": "helix config: 5,062 reflections x %d stratified samples, 64^2 nodes, 1024^2 detector"
                         % xs.shape[0],
             "evals": E, "ms": 1e3 * t, "evals_per_s": E / t, "samples_per_s": n_samples / t,
-            "frac_of_fp32_peak": FLOPS_PER_EVAL * E / t / 1e12 / fp32_peak_tflops(_peaks().get("sm_max_mhz", 2032.0))}
+            "roofline": pattern_roofline(E, t)}
 
 
-def batch_measurements(n_models=256, tune_models=8):
+def batch_measurements(n_models=256, tune_models=8, replays=5, loops=2, rank=0, world=1):
     """Batched refinement (config-4 recipe): n_models seeded candidate models of
-    uneven size, each against its own perturbed target.  One step = structure
-    factors + pattern + loss + adjoint for every model.  The batched step
+    uneven size, each against its own perturbed target, sharded over the ranks
+    (this rank takes a contiguous share).  One step = structure factors +
+    pattern + loss + adjoint for every model of the share.  The batched step
     (fdx_batch_refine: one persistent forward and one persistent adjoint launch
     over all models) runs as a captured CUDA graph with launch shapes from the
     autotuner (tuned on the first tune_models models); the comparison is a loop
-    over models calling the per-model entry points."""
+    over models calling the per-model entry points, with every buffer
+    allocated before the timed region."""
     import torch
-    from paper_2608_23245_b300 import fdx, tune, workloads as W
-    models = W.config4(n_models)
+    from paper_2608_23245_b300 import fdx, replicas, tune, workloads as W
+    b, e = replicas.shard_range(n_models, rank, world)
+    models = [W.config4_model(m) for m in range(b, e)]
     sims = [fdx.Simulation(p) for p in models]
     tims = []
-    for m, p in enumerate(models):
+    for m, p in zip(range(b, e), models):
         s = fdx.Simulation(W.config4_target(p, m))
         tims.append(s.forward().clone())
         del s
@@ -356,25 +374,27 @@ def batch_measurements(n_models=256, tune_models=8):
     for s in sims:
         s.forward()
         E += int(s.evals().to(torch.int64).sum().item())
+    # per-model loop: every buffer allocated up front (one backward workspace
+    # of the largest size, shared: the loop runs on one stream)
+    bws_n = max(fdx.fdx_backward_workspace_size(s.prob, s.atoms.frac.shape[0], s.atoms.ff.shape[0]) for s in sims)
+    bws = torch.empty(max(bws_n, 256), dtype=torch.uint8, device="cuda")
+    lws = torch.empty(max(fdx.fdx_loss_workspace_size(s.image.numel()) for s in sims), dtype=torch.uint8,
+                      device="cuda")
+    loss = torch.empty((), dtype=torch.float64, device="cuda")
+    bufs = []
+    for s in sims:
+        na = s.atoms.frac.shape[0]
+        bufs.append((torch.empty_like(s.image), torch.empty((na, 3), dtype=torch.float64, device="cuda"),
+                     torch.empty(na, dtype=torch.float64, device="cuda"),
+                     torch.empty(8, dtype=torch.float64, device="cuda")))
 
     def loop():
-        for s, It in zip(sims, tims):
+        for s, It, (gI, dfrac, dB, dg) in zip(sims, tims, bufs):
             s.forward()
-            gI = torch.empty_like(s.image)
-            fdx.fdx_loss(s.image, It, None, dL_dI=gI)
-            na = s.atoms.frac.shape[0]
-            dfrac = torch.empty((na, 3), dtype=torch.float64, device="cuda")
-            dB = torch.empty(na, dtype=torch.float64, device="cuda")
-            dg = torch.empty(8, dtype=torch.float64, device="cuda")
-            fdx.fdx_pattern_backward(s.prob, s.atoms, s.F, gI, dfrac, dB, dg, None)
+            fdx.fdx_loss(s.image, It, None, loss, gI, lws)
+            fdx.fdx_pattern_backward(s.prob, s.atoms, s.F, gI, dfrac, dB, dg, None, bws)
 
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    loop()
-    e1.record()
-    torch.cuda.synchronize()
-    t_loop = e0.elapsed_time(e1) / 1e3
+    t_loop = _timed(loop, loops, 1)
     step = fdx.BatchStep(probs, datoms, targets=tims)
     st = torch.cuda.Stream()
     st.wait_stream(torch.cuda.current_stream())
@@ -385,49 +405,56 @@ def batch_measurements(n_models=256, tune_models=8):
         with torch.cuda.graph(g, stream=st):
             step(st)
     torch.cuda.current_stream().wait_stream(st)
-    g.replay()
-    torch.cuda.synchronize()
-    e0.record()
-    g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) / 1e3
+    t_batch = _timed(g.replay, replays, 1)
+    n_local = e - b
+    t_loop_max = max_over_ranks(t_loop, world)
+    t_batch_max = max_over_ranks(t_batch, world)
     return {"workload": "%d seeded models (config-4 recipe: 500-8,000 atoms, 10-40 A edges, d >= 2 A, "
                         "256^2-960^2 detectors, Gaussian/Voigt, 64^2 nodes), each vs its perturbed target" % n_models,
-            "n_models": n_models, "forward_evals_per_step": E,
-            "batched_graph_models_per_s": n_models / t_batch, "batched_graph_s_per_step": t_batch,
-            "per_model_loop_models_per_s": n_models / t_loop, "per_model_loop_s_per_step": t_loop,
-            "batched_over_loop": t_loop / t_batch, "tuning": best}
+            "n_models": n_models, "models_this_rank": n_local, "forward_evals_per_step_this_rank": E,
+            "batched_graph_models_per_s": n_models / t_batch_max, "batched_graph_s_per_step": t_batch_max,
+            "graph_replays_timed": replays,
+            "per_model_loop_models_per_s": n_models / t_loop_max, "per_model_loop_s_per_step": t_loop_max,
+            "loop_passes_timed": loops, "batched_over_loop": t_loop_max / t_batch_max, "tuning": best}
 
 
-def cpu_baseline(problem, budget_s=12.0, n_pix=None, seed=5):
-    """Time the FP64 oracle (as it stands) on a bounded pixel sample."""
+def _oracle_M(problem):
+    """Oracle structure factors and M for every reflection (FP64, host cores);
+    returns (hkl, M, seconds)."""
     import oracle
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
     oracle.build()
     hkl = oracle.reflections(problem.cell, problem.d_min, problem.d_max)
+    t0 = time.perf_counter()
     M = oracle.intensities_M(problem, hkl)
+    return hkl, M, time.perf_counter() - t0
+
+
+def cpu_baseline(problem, hkl, M, t_sf, budget_s=12.0, seed=5):
+    """Time the FP64 oracle (as it stands) on a bounded sample of seeded pixels
+    drawn over the whole detector.  The oracle's structure factors for all
+    reflections (needed by any pixel) are computed once beforehand and
+    reported separately."""
+    import oracle
     rng = np.random.default_rng(seed)
-    n = problem.geom.n_x
-    # pixels from the central half of the detector, where reflections are dense;
-    # the probe is large enough to amortise the oracle's per-call node table
-    probe = np.stack([rng.integers(n // 4, 3 * n // 4, 256), rng.integers(n // 4, 3 * n // 4, 256)],
-                     1).astype(np.int32)
+    nx, ny = problem.geom.n_x, problem.geom.n_y
+    probe = np.stack([rng.integers(0, nx, 64), rng.integers(0, ny, 64)], 1).astype(np.int32)
     t0 = time.perf_counter()
     oracle.pattern(problem, hkl, M, probe[:1])
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     oracle.pattern(problem, hkl, M, probe)
     per_px = max((time.perf_counter() - t0 - t_setup) / len(probe), 1e-5)
-    k = n_pix or int(max(16, min(200000, budget_s / per_px)))
-    pix = np.stack([rng.integers(n // 4, 3 * n // 4, k), rng.integers(n // 4, 3 * n // 4, k)], 1).astype(np.int32)
+    k = int(max(16, min(200000, budget_s / per_px)))
+    pix = np.stack([rng.integers(0, nx, k), rng.integers(0, ny, k)], 1).astype(np.int32)
     t0 = time.perf_counter()
-    _, E = oracle.pattern(problem, hkl, M, pix)
+    _, Ec = oracle.pattern(problem, hkl, M, pix)
     dt = time.perf_counter() - t0
-    evals = int(E[:, 0].sum())
+    evals = int(Ec[:, 0].sum())
     return {"value": evals / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "%d seeded pixels of the central half of the 1024^2 detector, full reflection list "
-                      "(%d in-support evals in %.1f s)" % (k, evals, dt)}, dt
+            "sample": "%d seeded pixels over the whole %dx%d detector, full reflection list (%d in-support evals "
+                      "in %.1f s); the oracle's structure factors of all %d reflections took %.1f s beforehand"
+                      % (k, nx, ny, evals, dt, len(hkl), t_sf),
+            "sample_evals": evals, "sample_s": dt}, dt
 
 
 def run_reference(args):
@@ -435,15 +462,16 @@ def run_reference(args):
     if rank != 0:
         return
     from paper_2608_23245_b300 import workloads as W
-    p = W.config1()
+    p = W.config2(0.01)
+    hkl, M, t_sf = _oracle_M(p)
     per_step_budget = max(2.0, 100.0 / max(1, args.steps + args.warmup))
     times, evals = [], 0
     cb = None
     for s in range(args.warmup + args.steps):
-        cb, dt = cpu_baseline(p, budget_s=per_step_budget, seed=100 + s)
+        cb, dt = cpu_baseline(p, hkl, M, t_sf, budget_s=per_step_budget, seed=100 + s)
         if s >= args.warmup:
             times.append(dt)
-            evals += int(cb["sample"].split("(")[1].split(" ")[0])
+            evals += cb["sample_evals"]
     total = sum(times)
     value = evals / total
     cb["value"] = value
@@ -463,6 +491,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="fdx", choices=["fdx", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-helix", action="store_true")
     ap.add_argument("--no-refine", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-large", action="store_true")
@@ -480,7 +509,7 @@ def main():
         _build.build()
     barrier(world)
     dev = "cuda"
-    p = W.config1()
+    p = W.config2(0.01)
     sim = fdx.Simulation(p, dev)
     stream = torch.cuda.current_stream()
     # evaluation count E (once, outside the timed region)
@@ -499,7 +528,7 @@ def main():
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    # dominant kernel (the pattern launch) timed on its own stream position
+    # dominant kernel (the pattern call) timed on its own stream position
     pstarts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     # raw clock samples (the JSON line carries their summary); FDX_CLOCKS_DIR keeps them
     clocks_path = os.path.join(os.environ.get("FDX_CLOCKS_DIR", tempfile.gettempdir()), "bench_clocks_rank%d.csv" % rank)
@@ -544,16 +573,17 @@ def main():
     e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
     e2e_value = E * args.steps * world / e2e_s
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_measurements(args.batch_models, rank=rank, world=world)
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
         return
     clocks = cs.summary()
-    peaks = _peaks()
     pat_s = sum(pat_ms) / len(pat_ms) / 1e3
-    achieved = FLOPS_PER_EVAL * E / pat_s / 1e12
-    peak = fp32_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+    rf = pattern_roofline(E, pat_s)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -561,11 +591,18 @@ def main():
         "config": {"workload": WORKLOAD, "evals_per_step": E, "n_refl": int(sim.hkl.shape[0]), "n_atoms": p.atoms.n,
                    "l2_flush": "512 MiB write between steps, outside the per-step events",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": PATTERN_DRAM_BYTES,
+        "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": rf["achieved"],
+                     "peak": rf["peak"], "unit": "Tops/s", "frac": rf["frac"], "traffic": PATTERN_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                     "basis": "%d algorithmic FP32 flops per in-support eval; peak = 148 SMs x 128 lanes x 2 x "
-                              "%.0f MHz (FP32 FMA pipe)" % (FLOPS_PER_EVAL, peaks.get("sm_max_mhz", 2032.0)),
+                     "basis": "%d FP32 operations per in-support evaluation (the algorithm's count, an FMA is one); "
+                              "peak = 148 SMs x 128 FP32 lanes x %.0f MHz, nominal (no measured FP32 peak); "
+                              "time = the whole fdx_pattern call (set-up kernels included)"
+                              % (OPS_PER_EVAL, sm_max_mhz()),
+                     "xu": {"achieved": rf["xu_achieved"], "peak": rf["xu_peak"], "frac": rf["xu_frac"],
+                            "basis": "%d SFU operations per evaluation of the plain form against 148 x 16 SFU lanes "
+                                     "x clock (nominal); the kernel issues about one per evaluation (angle "
+                                     "addition), so this is the algorithm's SFU rate, not the pipe's load"
+                                     % SFU_PER_EVAL},
                      "pattern_ms": 1e3 * pat_s},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         # per step: structure factors (group and atom counts, group scan and
@@ -575,18 +612,22 @@ def main():
         "clocks": clocks,
         "wall_s": wall,
     }
+    if not args.no_large:
+        line["large"] = large_extras(sim, E)
+    del sim
+    if not args.no_helix:
+        line["helix"] = helix_measurements()
     if not args.no_refine:
         line["refine"] = refine_measurements()
-    if not args.no_large:
-        line["large"] = large_measurements()
     if not args.no_scatter:
         line["scatter"] = scatter_measurements()
     if not args.no_ring:
         line["ring"] = ring_measurements()
-    if not args.no_batch:
-        line["batch"] = batch_measurements(args.batch_models)
+    if batch is not None:
+        line["batch"] = batch
     if not args.no_cpu_baseline:
-        cb, _ = cpu_baseline(p)
+        hkl, M, t_sf = _oracle_M(p)
+        cb, _ = cpu_baseline(p, hkl, M, t_sf)
         line["cpu_baseline"] = cb
     print(json.dumps(line))
 
