@@ -247,13 +247,18 @@ size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples);
  *   L  = delta_L / (R + delta_L),  R = |S - (S . n) n|                              (Eq. lorentz)
  * S is rotated about the fiber axis into the diffraction condition (Eqs.
  * harmonic, solutions; no contribution when Eq. valid fails); each of the two
- * hits with k_out . b > 0 adds dV L I to the detector pixel it falls in (spot
- * size one pixel).  image is [n_y][n_x] float (device), overwritten.  Every
- * lineshape.  Accumulation is in FP64 (atomics): the result does not depend
- * on the order at FP32 resolution.  Asynchronous.
+ * hits with k_out . b > 0 is rendered as a detector spot (the paper's
+ * simulate() parameter of that name): the spot_size x spot_size block of
+ * pixels centred on the pixel the hit falls in each receive dV L I /
+ * spot_size^2, the parts off the detector being lost (spot_size odd, 1..15;
+ * 1 = the pixel itself; FDX_ERR_ARG otherwise).  The samples may reach past
+ * [-1, 1] (heavy-tailed sampling of the angular coordinates: S and dV are the
+ * same formulae for any x).  image is [n_y][n_x] float (device), overwritten.
+ * Every lineshape.  Accumulation is in FP64 (atomics): the result does not
+ * depend on the order at FP32 resolution.  Asynchronous.
  */
-int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, float *image, void *workspace,
-                size_t ws_bytes, void *stream);
+int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, int32_t spot_size, float *image,
+                void *workspace, size_t ws_bytes, void *stream);
 
 /* fdx_scatter_evals -- the number of in-support (sample, node) terms of the
  * scatter form over all reflections, written to *count (int64, device). */

@@ -86,13 +86,13 @@ def lib():
             L.or_pixel_S.argtypes = [C.POINTER(Params), C.c_int32, C.c_int32, _dp,
                                      C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_pattern.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _ip, C.c_int32,
-                                     C.c_double, _dp, _lp]
+                                     C.c_double, _dp, _lp, C.c_void_p]
             L.or_pattern_adjoint.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _ip, _dp,
                                              _dp, _dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
             L.or_chain_globals.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, _dp, _dp, _dp, _dp]
             L.or_sf_adjoint.argtypes = [_dp, C.c_int32, _dp, _dp, _dp, _ip, _dp, C.c_int32, _ip, _dp, _dp,
                                         _dp, _dp]
-            L.or_scatter.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _dp, _dp,
+            L.or_scatter.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _dp, C.c_int32, _dp,
                                      C.c_void_p, C.POINTER(C.c_int64)]
             L.or_ring.argtypes = [C.POINTER(Params), C.c_int32, _ip, _dp, C.c_int32, _ip, C.c_int32, C.c_int32,
                                   _dp, _lp]
@@ -243,10 +243,12 @@ def all_pixels(problem) -> np.ndarray:
     return np.stack([ii.reshape(-1), jj.reshape(-1)], axis=1).astype(np.int32)
 
 
-def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, **over):
+def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, with_ambiguous=False, **over):
     """Pixel values I (Eq. direct_sum x Eq. lorentz) and in-support term counts.
 
-    Returns (I[n_pix], E[n_pix, 3]) with E columns (exact, strict, loose)."""
+    Returns (I[n_pix], E[n_pix, 3]) with E columns (exact, strict, loose);
+    with_ambiguous adds A[n_pix], the summed magnitude of the terms whose
+    inclusion is decided within eta of the support's edge."""
     if pix is None:
         pix = all_pixels(problem)
     pix = _i32(pix).reshape(-1, 2)
@@ -254,8 +256,11 @@ def pattern(problem, hkl, M, pix=None, cull=True, eta=1e-6, **over):
     prm = params(problem, **over)
     I = np.zeros(max(len(pix), 1))
     E = np.zeros(3 * max(len(pix), 1), dtype=np.int64)
+    A = np.zeros(max(len(pix), 1)) if with_ambiguous else None
     lib().or_pattern(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(pix), pix.reshape(-1),
-                     int(bool(cull)), float(eta), I, E)
+                     int(bool(cull)), float(eta), I, E, A.ctypes.data_as(C.c_void_p) if A is not None else None)
+    if with_ambiguous:
+        return I[:len(pix)], E[:3 * len(pix)].reshape(-1, 3), A[:len(pix)]
     return I[:len(pix)], E[:3 * len(pix)].reshape(-1, 3)
 
 
@@ -296,18 +301,21 @@ def ring_grid(r0, RD, rhoB, T, w_min, max_n=RING_MAX_N):
     return Phi.value, N.value
 
 
-def scatter(problem, hkl, M, samples, with_samples=False, **over):
+def scatter(problem, hkl, M, samples, with_samples=False, spot=1, **over):
     """Scatter form: image [n_y, n_x] accumulated over all reflections and
-    samples (samples [n_s, 4]: xi_r, xi_1, xi_2, q), the in-support count,
-    and optionally per (reflection, sample) rows (I, dV, L, x0, y0, x1, y1,
-    distance of the nearest node from the edge of the support)."""
+    samples (samples [n_s, 4]: xi_r, xi_1, xi_2, q), each hit rendered as a
+    spot x spot block (spot odd), the in-support count, and optionally per
+    (reflection, sample) rows (I, dV, L, x0, y0, x1, y1, distance of the
+    nearest node from the edge of the support)."""
+    if spot < 1 or spot % 2 == 0:
+        raise ValueError("spot size must be a positive odd number of pixels")
     hkl = _i32(hkl).reshape(-1, 3)
     xs = _f64(samples).reshape(-1, 4)
     prm = params(problem, **over)
     img = np.zeros(problem.geom.n_x * problem.geom.n_y)
     E = C.c_int64(0)
     samp = np.zeros(8 * max(1, len(hkl) * len(xs))) if with_samples else None
-    lib().or_scatter(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(xs), xs.reshape(-1), img,
+    lib().or_scatter(C.byref(prm), len(hkl), hkl.reshape(-1), _f64(M), len(xs), xs.reshape(-1), int(spot), img,
                      samp.ctypes.data_as(C.c_void_p) if samp is not None else None, C.byref(E))
     img = img.reshape(problem.geom.n_y, problem.geom.n_x)
     if with_samples:

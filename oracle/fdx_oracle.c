@@ -515,12 +515,18 @@ static void build_refl_geo(const or_params *p, const double *A, const double *As
  * E_out[3q + 0] = number of (reflection, node) terms inside the support
  * E_out[3q + 1] = same count with the support shrunk by eta (strict)
  * E_out[3q + 2] = same count with the support grown by eta (loose)
+ * A_out[q] (nullable) = L(R) sum_r M_r r0^2 sum over the nodes counted by the
+ * loose count but not by the strict one of |w_k prod_i K_i|: the terms whose
+ * inclusion is decided within eta of the support's edge.  The support ends
+ * where K is not zero (the Hosemann factor is beta at |t| = 1/2), so these
+ * terms are whole jumps of the sum: a computation whose t carries rounding of
+ * order eta may include or drop any of them, and A bounds what that changes.
  * cull != 0 skips reflections with | |p| - r0 | > rhoB, which contain no
  * node inside the support (|p - s| <= rhoB and |s| = r0); the result is
  * identical with cull = 0.
  */
 void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_pix,
-                const int32_t *pix, int32_t cull, double eta, double *I_out, int64_t *E_out) {
+                const int32_t *pix, int32_t cull, double eta, double *I_out, int64_t *E_out, double *A_out) {
     double A[9], As[9];
     or_basis(p->cell, A, As);
     double bh[3], nh[3], uh[3], vh[3];
@@ -540,14 +546,14 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
         double S[3], R, Z;
         or_pixel_S(p, pix[2 * q], pix[2 * q + 1], S, &R, &Z);
         double plen = sqrt(R * R + Z * Z);
-        double acc = 0.0;
+        double acc = 0.0, amb = 0.0;
         int64_t e0 = 0, e1c = 0, e2c = 0;
         for (int32_t r = 0; r < n_refl; r++) {
             const refl_geo *g = &G[r];
             if (cull && fabs(plen - g->r0) > g->rhoB * (1.0 + 1e-9) + 1e-12) continue;
             double pq[3];
             for (int c = 0; c < 3; c++) pq[c] = Z * nh[c] + R * g->eR[c];
-            double sum = 0.0;
+            double sum = 0.0, edge = 0.0;
             for (int k = 0; k < nn; k++) {
                 double inv = 1.0 / sqrt(1.0 + d1[k] * d1[k] + d2[k] * d2[k]);
                 double X[3];
@@ -562,6 +568,11 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
                 }
                 if (excess <= -eta) e1c++;
                 if (excess <= eta) e2c++;
+                if (A_out && excess > -eta && excess <= eta) {
+                    double Ke = 1.0;
+                    for (int i = 0; i < 3; i++) Ke *= or_lineshape(p->lineshape, t[i], g->beta[i], NULL);
+                    edge += fabs(w[k] * Ke);
+                }
                 if (excess > 0.0) continue;
                 e0++;
                 double Kp = 1.0;
@@ -569,9 +580,11 @@ void or_pattern(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
                 sum += w[k] * Kp;
             }
             acc += M[r] * g->r0 * g->r0 * sum;
+            amb += fabs(M[r]) * g->r0 * g->r0 * edge;
         }
         double Lf = p->delta_L / (R + p->delta_L);
         I_out[q] = Lf * acc;
+        if (A_out) A_out[q] = Lf * amb;
         if (E_out) {
             E_out[3 * q] = e0;
             E_out[3 * q + 1] = e1c;
@@ -744,8 +757,11 @@ void or_point(const or_params *p, int32_t n_refl, const int32_t *hkl, const doub
  * closed form of Eqs. harmonic and solutions (two solutions, none when
  * |R/sqrt(P^2+Q^2)| > 1, Eq. valid); each k_out = k_in + S_phi with
  * k_out . b > 0 is followed to the flat detector at distance SF, and the
- * pixel containing the hit (spot size one pixel) receives dV L I.
- * img[ny][nx] is accumulated (not cleared).  samp (nullable) receives per
+ * hit is rendered as a spot (the paper's detector spot size, reading R25):
+ * the spot x spot block of pixels centred on the pixel containing the hit
+ * (spot odd) each receives dV L I / spot^2; parts of the block off the
+ * detector are lost, as a hit off the detector is.  spot = 1 is the pixel
+ * containing the hit.  img[ny][nx] is accumulated (not cleared).  samp (nullable) receives per
  * (reflection, sample) 8 values: I, dV, L, the two hits' continuous pixel
  * coordinates x = u/p + n_x/2, y = v/p + n_y/2 (NaN when there is no hit),
  * and the smallest distance of any node from the edge of the support,
@@ -754,7 +770,7 @@ void or_point(const or_params *p, int32_t n_refl, const int32_t *hkl, const doub
  * E (nullable) receives the number of in-support (sample, node) terms.
  */
 void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const double *M, int32_t n_s,
-                const double *xs, double *img, double *samp, int64_t *E) {
+                const double *xs, int32_t spot, double *img, double *samp, int64_t *E) {
     double A[9], As[9];
     or_basis(p->cell, A, As);
     double bh[3], nh[3], uh[3], vh[3];
@@ -837,8 +853,14 @@ void or_scatter(const or_params *p, int32_t n_refl, const int32_t *hkl, const do
                     const double yp = p->distance * dot3(ko, vh) / kb / p->pixel + 0.5 * p->n_y;
                     if (o) o[3 + 2 * br] = xp, o[4 + 2 * br] = yp;
                     const double fi = floor(xp), fj = floor(yp);
-                    if (fi < 0.0 || fj < 0.0 || fi >= p->n_x || fj >= p->n_y) continue;
-                    loc[(size_t)fj * p->n_x + (size_t)fi] += dV * L * I;
+                    const int half = (spot - 1) / 2;
+                    const double share = dV * L * I / ((double)spot * spot);
+                    for (int dj = -half; dj <= half; dj++)
+                        for (int di = -half; di <= half; di++) {
+                            const double qi = fi + di, qj = fj + dj;
+                            if (qi < 0.0 || qj < 0.0 || qi >= p->n_x || qj >= p->n_y) continue;
+                            loc[(size_t)qj * p->n_x + (size_t)qi] += share;
+                        }
                 }
             }
         }

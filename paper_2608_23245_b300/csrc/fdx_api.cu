@@ -324,11 +324,12 @@ ScatterLayout scatter_layout(const fdx_problem *p, int n_s) {
     return S;
 }
 
-int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, float *image, int64_t *count,
-                void *workspace, size_t ws_bytes, void *stream) {
+int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, int32_t spot, float *image,
+                int64_t *count, void *workspace, size_t ws_bytes, void *stream) {
     int rc = validate_problem(prob);
     if (rc) return rc;
     if (n_s < 1 || !samples || ((uintptr_t)samples % 16)) return FDX_ERR_ARG;
+    if (spot < 1 || spot > 15 || spot % 2 == 0) return FDX_ERR_ARG;
     const ScatterLayout SL = scatter_layout(prob, n_s);
     if (!workspace || ws_bytes < SL.total || ((uintptr_t)workspace % kAlign)) return FDX_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -344,6 +345,7 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, floa
     rc = setup_pattern(prob, ws, st, S.P, false, nullptr, reinterpret_cast<double *>(ws + SL.frames));
     if (rc) return rc;
     S.n_s = n_s;
+    S.spot = spot;
     S.samples = reinterpret_cast<const float4 *>(samples);
     S.stab = reinterpret_cast<float4 *>(ws + SL.stab);
     S.frames = reinterpret_cast<const double *>(ws + SL.frames);
@@ -416,6 +418,7 @@ int run_ring(const fdx_problem *prob, float *image, int32_t *counts, void *works
     R.P.counts = counts;
     R.ring = reinterpret_cast<const float *>(ws + roff);
     R.n_split = ring_split(prob);
+    R.dpsi_extra = (float)((atan(prob->br.T * sqrt(2.0)) - atan(prob->br.T)) * (1.0 + 1e-4) + 1e-6);
     R.partial = R.n_split > 1 ? reinterpret_cast<float2 *>(ws + poff) : nullptr;
     if (launch_ring(R, prob->br.lineshape, counts != nullptr, st) != cudaSuccess) return FDX_ERR_CUDA;
     return FDX_OK;
@@ -957,16 +960,16 @@ size_t fdx_scatter_workspace_size(const fdx_problem *prob, int32_t n_samples) {
     return scatter_layout(prob, n_samples).total;
 }
 
-int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, float *image, void *workspace,
-                size_t ws_bytes, void *stream) {
+int fdx_scatter(const fdx_problem *prob, int32_t n_samples, const float *samples, int32_t spot_size, float *image,
+                void *workspace, size_t ws_bytes, void *stream) {
     if (!image) return FDX_ERR_ARG;
-    return run_scatter(prob, n_samples, samples, image, nullptr, workspace, ws_bytes, stream);
+    return run_scatter(prob, n_samples, samples, spot_size, image, nullptr, workspace, ws_bytes, stream);
 }
 
 int fdx_scatter_evals(const fdx_problem *prob, int32_t n_samples, const float *samples, int64_t *count,
                       void *workspace, size_t ws_bytes, void *stream) {
     if (!count || ((uintptr_t)count % 8)) return FDX_ERR_ARG;
-    return run_scatter(prob, n_samples, samples, nullptr, count, workspace, ws_bytes, stream);
+    return run_scatter(prob, n_samples, samples, 1, nullptr, count, workspace, ws_bytes, stream);
 }
 
 int fdx_pattern_evals(const fdx_problem *prob, int32_t *counts, void *workspace, size_t ws_bytes, void *stream) {

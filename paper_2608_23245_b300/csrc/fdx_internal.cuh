@@ -239,6 +239,7 @@ cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s);
 struct ScatterParams {
     PatternParams P;          // records, nodes (pixgeo/image unused)
     int n_s;                  // samples per reflection
+    int spot;                 // detector spot size (odd): each hit covers spot x spot pixels
     const float4 *samples;    // [n_s] (x_r, x_1, x_2, q)
     float4 *stab;             // [n_s][3] per-sample table (set-up kernel)
     const double *frames;     // [n_refl][12]
@@ -262,6 +263,7 @@ struct RingParams {
     const float *ring;        // [n_refl][RING_REC]
     int n_split;              // azimuth points of a reflection are dealt round-robin to n_split warps per patch
     float2 *partial;          // [n_split][n_y][n_x] float-float partial sums (int32 in count mode); null if n_split == 1
+    float dpsi_extra;         // widening of the reach window for query points off the meridional plane
 };
 cudaError_t launch_ring(const RingParams &p, int lineshape, bool count_mode, cudaStream_t s);
 void sf_plan(int n_atoms, int n_refl, int n_elem, int max_split, int &n_split, int &per);

@@ -262,41 +262,43 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                                           PairAcc (&acc)[PPL]) {
     constexpr bool PACKED = (LS == FDX_LINESHAPE_HOSEMANN && MODE != MODE_CNT);
     const int n = P.n_nodes;
-    // node rows/columns that can be in each point's support: gnomonic
-    // projection of the support box's corners around (p - D)/r0 (FP32, bounds only)
-    int j0 = n, j1 = -1, m0 = n, m1 = -1;
+    // Node rows/columns that can be in any point's support: the gnomonic
+    // projection d = X_perp / X_0 of the 8 corners of the support box around
+    // the reference point, X = (1, 0, 0) + (p_ref - D)/r0 + corner (one corner
+    // per lane on lanes 0-7), widened for the other points.  A point at
+    // p_ref + r0 delta, |delta| <= Dl, moves a corner's projection by at most
+    // Dl (1 + |d_i|) / (X_0 - Dl) along d_i.  FP32, bounds only (the ranges get
+    // one more node on each side).
+    float Dl = 0.0f;
 #pragma unroll
     for (int p = 0; p < PPL; ++p) {
-        const float P0 = qp.P[p][0], P1 = qp.P[p][1], P2 = qp.P[p][2];
-        float d1lo = 3.0e38f, d1hi = -3.0e38f, d2lo = 3.0e38f, d2hi = -3.0e38f;
-        bool degenerate = false;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-#pragma unroll
-            for (int s = 0; s < 2; ++s) {
-                const float sg = s ? -1.0f : 1.0f;
-                const float X0 = 1.0f + P0 + sg * rec[REC_CR + 3 * v];
-                const float X1 = P1 + sg * rec[REC_CR + 3 * v + 1];
-                const float X2 = P2 + sg * rec[REC_CR + 3 * v + 2];
-                degenerate |= !(X0 > 0.05f);
-                const float inv = 1.0f / X0;
-                const float d1 = X1 * inv, d2 = X2 * inv;
-                d1lo = fminf(d1lo, d1), d1hi = fmaxf(d1hi, d1);
-                d2lo = fminf(d2lo, d2), d2hi = fmaxf(d2hi, d2);
-            }
-        }
-        if (qp.valid[p]) {
-            if (degenerate) {
-                j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
-            } else {
-                const float T = P.T, ih = P.inv_h;
-                j0 = min(j0, max(0, (int)ceilf(fmaf(d1lo + T, ih, -0.5f)) - 1));
-                j1 = max(j1, min(n - 1, (int)floorf(fmaf(d1hi + T, ih, -0.5f)) + 1));
-                m0 = min(m0, max(0, (int)ceilf(fmaf(d2lo + T, ih, -0.5f)) - 1));
-                m1 = max(m1, min(n - 1, (int)floorf(fmaf(d2hi + T, ih, -0.5f)) + 1));
-            }
+        if (!qp.valid[p]) continue;
+        const float e0 = qp.P[p][0] - qp.dP[0].hi, e1 = qp.P[p][1] - qp.dP[1].hi, e2 = qp.P[p][2] - qp.dP[2].hi;
+        Dl = fmaxf(Dl, sqrtf(fmaf(e0, e0, fmaf(e1, e1, e2 * e2))));
+    }
+    Dl = warp_max(Dl) * 1.0001f + 1e-7f;
+    int j0 = n, j1 = -1, m0 = n, m1 = -1;
+    bool degenerate = false;
+    if (lane < 8) {
+        const int v = lane & 3;
+        const float sg = (lane & 4) ? -1.0f : 1.0f;
+        const float X0 = 1.0f + qp.dP[0].hi + sg * rec[REC_CR + 3 * v];
+        const float X1 = qp.dP[1].hi + sg * rec[REC_CR + 3 * v + 1];
+        const float X2 = qp.dP[2].hi + sg * rec[REC_CR + 3 * v + 2];
+        const float den = X0 - Dl;
+        degenerate = !(den > 0.05f);
+        if (!degenerate) {
+            const float inv = __frcp_rn(X0), ivd = __frcp_rn(den);
+            const float d1 = X1 * inv, d2 = X2 * inv;
+            const float w1 = Dl * (1.0f + fabsf(d1)) * ivd, w2 = Dl * (1.0f + fabsf(d2)) * ivd;
+            const float T = P.T, ih = P.inv_h;
+            j0 = max(0, (int)ceilf(fmaf(d1 - w1 + T, ih, -0.5f)) - 1);
+            j1 = min(n - 1, (int)floorf(fmaf(d1 + w1 + T, ih, -0.5f)) + 1);
+            m0 = max(0, (int)ceilf(fmaf(d2 - w2 + T, ih, -0.5f)) - 1);
+            m1 = min(n - 1, (int)floorf(fmaf(d2 + w2 + T, ih, -0.5f)) + 1);
         }
     }
+    if (__any_sync(FDX_FULL_MASK, degenerate)) j0 = 0, j1 = n - 1, m0 = 0, m1 = n - 1;
     const int J0 = __reduce_min_sync(FDX_FULL_MASK, j0), J1 = __reduce_max_sync(FDX_FULL_MASK, j1);
     const int M0 = __reduce_min_sync(FDX_FULL_MASK, m0), M1 = __reduce_max_sync(FDX_FULL_MASK, m1);
     if (J0 > J1 || M0 > M1) return false;

@@ -2,18 +2,22 @@
 // times the Lorentz factor of Eq. lorentz).
 //
 // Work decomposition.  A CTA of 4 warps covers a 16 x 16 pixel block; each warp
-// owns an 8 x 8 pixel patch, two pixels per lane, and accumulates its pixels
-// in registers (no atomics).  The warp scans the reflection list 32 at a time
-// with a conservative radial/polar test against its patch's (|S|, psi) bounds
-// and evaluates the surviving (patch, reflection) pairs in list order
-// (deterministic) with eval_pair (fdx_pair.cuh).  Pair sums are weighted by
-// the reflection's pair factor and folded into a float-float pixel sum; the
-// epilogue applies the Lorentz factor in FP64.
+// owns an 8 x 8 pixel patch (the tile), two pixels per lane, and accumulates
+// its pixels in registers (no atomics).  Binning is tile-major: the warp bins
+// the reflections to its tile by the closed-form footprint of each one in
+// (|S|, psi) -- the inverse-Ewald image of a pixel is its (R, Z), and a
+// reflection reaches it only within its (r0 +- rho_B, psi_D +- dpsi) window --
+// and stages the tile's list in shared memory, then evaluates the listed
+// (tile, reflection) pairs in list order (deterministic) with eval_pair
+// (fdx_pair.cuh).  Pair sums are weighted by the reflection's pair factor and
+// folded into a float-float pixel sum; the epilogue applies the Lorentz
+// factor in FP64.
 #include "fdx_pair.cuh"
 
 namespace fdx {
 
-static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp (even); 4 warps x 288 x 40 B keeps static shared memory < 48 KB
+static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp (even): 54 KB per CTA, 4 CTAs per SM
+static constexpr int TILE_SCAN = 512;     // reflections tested per refill of a tile's list
 // Pixels per lane (PPL): 2 (a warp owns 8 x 8 pixels, a CTA 16 x 16) when
 // the patch spans a small fraction of a lattice period, else 1 (8 x 4, 16 x 8);
 // chosen on the host from the pixel pitch and the cell.
@@ -22,7 +26,7 @@ static constexpr int FWD_NODE_BUF = 288;  // staged nodes per warp (even); 4 war
 // reflections, evaluate the surviving pairs, write the pixels.
 template <int LS, int MODE, int PPL>
 __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, int py0, float4 *buf, float4 *bsc,
-                                             float4 *bsc2, float *rec, int lane) {
+                                             float4 *bsc2, float *rec, int *lst, int lane) {
     const PatchPix<PPL> g = load_patch<PPL>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
 
     float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
@@ -39,18 +43,38 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
 #pragma unroll
     for (int p = 0; p < PPL; ++p) acc[p] = ff{0.0f, 0.0f}, cnt[p] = 0;
 
-    for (int base = 0; base < P.n_refl; base += 32) {
-        bool cand = false;
-        const int rr = base + lane;
-        if (rr < P.n_refl) {
-            const float4 q = P.reach[rr];
-            cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - q.w <= pmax) && (q.z + q.w >= pmin);
+    // The tile's reflection list, TILE_SCAN reflections at a time: the
+    // closed-form footprint test (reflection's (|S|, psi) window against the
+    // patch's) on 16 coalesced loads in flight, survivors staged in shared
+    // memory in list order.  The list is then evaluated in order, each
+    // candidate's record loaded into registers while the previous one is
+    // evaluated.
+    for (int base = 0; base < P.n_refl; base += TILE_SCAN) {
+        int n = 0;
+#pragma unroll
+        for (int gq = 0; gq < TILE_SCAN / 32; ++gq) {
+            const int rr = base + 32 * gq + lane;
+            bool cand = false;
+            if (rr < P.n_refl) {
+                const float4 q = P.reach[rr];
+                cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - q.w <= pmax) && (q.z + q.w >= pmin);
+            }
+            const unsigned m = __ballot_sync(FDX_FULL_MASK, cand);
+            if (cand) lst[n + __popc(m & ((1u << lane) - 1u))] = rr;
+            n += __popc(m);
         }
-        unsigned mask = __ballot_sync(FDX_FULL_MASK, cand);
-        while (mask) {
-            const int b = __ffs(mask) - 1;
-            mask &= mask - 1;
-            load_record(P.recs, base + b, rec, lane);
+        __syncwarp();
+        if (n == 0) continue;
+        const float *grec = P.recs + (size_t)lst[0] * REC_SIZE;
+        float nx0 = grec[lane], nx1 = grec[lane + 32];
+        for (int c = 0; c < n; ++c) {
+            __syncwarp();
+            rec[lane] = nx0, rec[lane + 32] = nx1;
+            __syncwarp();
+            if (c + 1 < n) {
+                const float *gn = P.recs + (size_t)lst[c + 1] * REC_SIZE;
+                nx0 = gn[lane], nx1 = gn[lane + 32];
+            }
             PairAcc pa[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) clear(pa[p]);
@@ -63,6 +87,7 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
                     acc[p] = ff_add(acc[p], ff_mul_f(pa[p].s0, rec[REC_FR]));
             }
         }
+        __syncwarp();
     }
 #pragma unroll
     for (int p = 0; p < PPL; ++p) {
@@ -79,19 +104,35 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
     }
 }
 
-#define FDX_PATTERN_SMEM(LS, MODE)                                                                  \
-    __shared__ float4 s_nodes[PAIR_WARPS][FWD_NODE_BUF];                                            \
-    __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1]; \
-    __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF / 2 : 1]; \
-    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+// Shared memory of a pattern CTA (dynamic, so that it may exceed the 48 KB a
+// kernel can declare statically), per warp: the staged nodes, the scaled
+// sin/cos of the Hosemann walk, the reflection record and the tile's
+// reflection list.
+template <int LS, int MODE>
+struct PatternSmem {
+    static constexpr int SC = (LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF : 1;
+    static constexpr int SC2 = (LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? FWD_NODE_BUF / 2 : 1;
+    static constexpr int PER_WARP = FWD_NODE_BUF + SC + SC2 + REC_SIZE / 4 + TILE_SCAN / 4;  // float4 units
+    static constexpr size_t BYTES = sizeof(float4) * PAIR_WARPS * PER_WARP;
+    float4 *nodes, *sc, *sc2;
+    float *rec;
+    int *lst;
+    __device__ __forceinline__ PatternSmem(float4 *base, int warp) {
+        float4 *w = base + (size_t)warp * PER_WARP;
+        nodes = w, sc = nodes + FWD_NODE_BUF, sc2 = sc + SC;
+        rec = reinterpret_cast<float *>(sc2 + SC2);
+        lst = reinterpret_cast<int *>(sc2 + SC2 + REC_SIZE / 4);
+    }
+};
 
 template <int LS, int MODE, int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternParams P) {
-    FDX_PATTERN_SMEM(LS, MODE)
+    extern __shared__ float4 dsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * (8 * PPL) + (warp >> 1) * (4 * PPL);
     if (px0 >= P.nx || py0 >= P.ny) return;  // the whole patch is outside; its first pixel is valid otherwise
-    pattern_warp<LS, MODE, PPL>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    const PatternSmem<LS, MODE> sm(dsm, warp);
+    pattern_warp<LS, MODE, PPL>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
 }
 
 // Model of a flattened item index: the last m with prefix[m] <= item.
@@ -110,9 +151,10 @@ __device__ __forceinline__ int item_model(const long long *prefix, int n_models,
 // order in which items are taken.
 template <int LS>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(BatchFwdParams B) {
-    FDX_PATTERN_SMEM(LS, MODE_FWD)
+    extern __shared__ float4 dsm[];
     __shared__ long long s_item;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const PatternSmem<LS, MODE_FWD> sm(dsm, warp);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1u);
@@ -128,43 +170,54 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(Batch
         const int px0 = bx * 16 + (warp & 1) * 8, py0 = by * (8 * ppl) + (warp >> 1) * (4 * ppl);
         if (px0 >= P.nx || py0 >= P.ny) continue;
         if (ppl == 2)
-            pattern_warp<LS, MODE_FWD, 2>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+            pattern_warp<LS, MODE_FWD, 2>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
         else
-            pattern_warp<LS, MODE_FWD, 1>(P, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+            pattern_warp<LS, MODE_FWD, 1>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
     }
 }
 
+// Opt a kernel into `bytes` of dynamic shared memory (above 48 KB this must be
+// requested; done once per kernel and device).
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s) {
-    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
+    constexpr size_t bytes = PatternSmem<FDX_LINESHAPE_HOSEMANN, MODE_FWD>::BYTES;
+    cudaError_t e = allow_smem(pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN>, bytes);
+    if (e != cudaSuccess) return e;
+    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_ctas, PAIR_WARPS * 32, bytes, s>>>(B);
     return cudaGetLastError();
 }
 
 template <int LS, int PPL>
-static void launch_ls(const PatternParams &p, bool count_mode, cudaStream_t s) {
+static cudaError_t launch_ls(const PatternParams &p, bool count_mode, cudaStream_t s) {
     dim3 grid((p.nx + 15) / 16, (p.ny + 8 * PPL - 1) / (8 * PPL));
     dim3 block(PAIR_WARPS * 32);
-    if (count_mode)
-        pattern_kernel<LS, MODE_CNT, PPL><<<grid, block, 0, s>>>(p);
-    else
-        pattern_kernel<LS, MODE_FWD, PPL><<<grid, block, 0, s>>>(p);
+    if (count_mode) {
+        constexpr size_t bytes = PatternSmem<LS, MODE_CNT>::BYTES;
+        cudaError_t e = allow_smem(pattern_kernel<LS, MODE_CNT, PPL>, bytes);
+        if (e != cudaSuccess) return e;
+        pattern_kernel<LS, MODE_CNT, PPL><<<grid, block, bytes, s>>>(p);
+    } else {
+        constexpr size_t bytes = PatternSmem<LS, MODE_FWD>::BYTES;
+        cudaError_t e = allow_smem(pattern_kernel<LS, MODE_FWD, PPL>, bytes);
+        if (e != cudaSuccess) return e;
+        pattern_kernel<LS, MODE_FWD, PPL><<<grid, block, bytes, s>>>(p);
+    }
+    return cudaGetLastError();
 }
 
 template <int PPL>
-static void launch_ppl(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
-    if (lineshape == FDX_LINESHAPE_HOSEMANN)
-        launch_ls<FDX_LINESHAPE_HOSEMANN, PPL>(p, count_mode, s);
-    else if (lineshape == FDX_LINESHAPE_GAUSS)
-        launch_ls<FDX_LINESHAPE_GAUSS, PPL>(p, count_mode, s);
-    else
-        launch_ls<FDX_LINESHAPE_SINC, PPL>(p, count_mode, s);
+static cudaError_t launch_ppl(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
+    if (lineshape == FDX_LINESHAPE_HOSEMANN) return launch_ls<FDX_LINESHAPE_HOSEMANN, PPL>(p, count_mode, s);
+    if (lineshape == FDX_LINESHAPE_GAUSS) return launch_ls<FDX_LINESHAPE_GAUSS, PPL>(p, count_mode, s);
+    return launch_ls<FDX_LINESHAPE_SINC, PPL>(p, count_mode, s);
 }
 
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s) {
-    if (p.ppl == 2)
-        launch_ppl<2>(p, lineshape, count_mode, s);
-    else
-        launch_ppl<1>(p, lineshape, count_mode, s);
-    return cudaGetLastError();
+    return p.ppl == 2 ? launch_ppl<2>(p, lineshape, count_mode, s) : launch_ppl<1>(p, lineshape, count_mode, s);
 }
 
 }  // namespace fdx

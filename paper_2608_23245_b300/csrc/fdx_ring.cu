@@ -44,7 +44,8 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
         const int rr = base + lane;
         if (rr < P.n_refl) {
             const float4 q = P.reach[rr];
-            cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - q.w <= pmax) && (q.z + q.w >= pmin);
+            const float dw = q.w + RP.dpsi_extra;  // ring points leave the meridional plane
+            cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - dw <= pmax) && (q.z + dw >= pmin);
         }
         unsigned mask = __ballot_sync(FDX_FULL_MASK, cand);
         while (mask) {

@@ -5,7 +5,7 @@
 // every sample is the direct sum of Eq. direct_sum, the sample carries the
 // Lorentz factor of Eq. lorentz, is rotated about the fiber axis into the
 // diffraction condition with the closed form of Eqs. harmonic/solutions, and
-// its two hits are added to the detector pixels they fall in.
+// its two hits are added to the detector as spots of spot x spot pixels.
 //
 // Samples: normalised (x_r, x_1, x_2) in [-1, 1]^3 with quadrature weight q,
 // shared by all reflections; for a reflection with radius r0 and support
@@ -138,8 +138,20 @@ __device__ __forceinline__ void splat_sample(const ScatterParams &p, const ff *s
         const ff ib = ff_mul(ffv(p.dp_f), ff_rcp(kb));
         const float fi = ff_floor(ff_add(ff_mul(ku, ib), ffv(p.hx_f)));
         const float fj = ff_floor(ff_add(ff_mul(kv, ib), ffv(p.hy_f)));
-        if (!(fi >= 0.0f) || !(fj >= 0.0f) || fi >= (float)p.P.nx || fj >= (float)p.P.ny) continue;
-        atomicAdd(&p.img64[(size_t)fj * p.P.nx + (size_t)fi], v);
+        // detector spot: the spot x spot block centred on the hit pixel
+        const int half = (p.spot - 1) >> 1;
+        if (!(fi >= (float)-half) || !(fj >= (float)-half) || fi >= (float)(p.P.nx + half) ||
+            fj >= (float)(p.P.ny + half))
+            continue;
+        const int ci = (int)fi, cj = (int)fj;
+        if (half == 0) {
+            atomicAdd(&p.img64[(size_t)cj * p.P.nx + (size_t)ci], v);
+            continue;
+        }
+        const double share = v / (double)(p.spot * p.spot);
+        for (int qj = max(cj - half, 0); qj <= min(cj + half, p.P.ny - 1); ++qj)
+            for (int qi = max(ci - half, 0); qi <= min(ci + half, p.P.nx - 1); ++qi)
+                atomicAdd(&p.img64[(size_t)qj * p.P.nx + (size_t)qi], share);
     }
 }
 

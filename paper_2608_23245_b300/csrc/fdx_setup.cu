@@ -320,8 +320,17 @@ __global__ void refl_setup_kernel(ReflSetupParams p) {
         for (int q = 0; q < 3; ++q) fr64[q] = Sh[q], fr64[3 + q] = e1[q], fr64[6 + q] = e2[q];
         fr64[9] = r0, fr64[10] = rhoB, fr64[11] = 0.0;
     }
+    // Polar-angle window of the pixels this reflection can reach.  A pixel's
+    // query point p lies in the reflection's meridional plane (spanned by S^
+    // and e2, reading R12); a node s = r0 (S^ + d1 e1 + d2 e2)/sqrt(1 + d^2)
+    // contributes only if |p - s| <= rho_B, and so does its projection onto
+    // that plane, which sits at the in-plane angle atan(d2) from S^ (|d2| <= T)
+    // and at radius >= r0 / sqrt(1 + T^2).  Hence |psi_p - psi_D| <= atan(T)
+    // + asin(rho_B sqrt(1 + T^2) / r0).  (The ring average, whose query points
+    // leave the plane, widens this by atan(T sqrt 2) - atan(T).)
     const double psiD = atan2(RD, ZD);
-    const double dpsi = atan(p.T * sqrt(2.0)) + (rhoB < r0 ? asin(rhoB / r0) : FDX_PI);
+    const double rho_in = rhoB * sqrt(1.0 + p.T * p.T);
+    const double dpsi = atan(p.T) + (rho_in < r0 ? asin(rho_in / r0) : FDX_PI);
     p.reach[r] = make_float4((float)r0, (float)(rhoB * (1.0 + 1e-4) + 1e-6), (float)psiD,
                              (float)(dpsi * (1.0 + 1e-4) + 1e-6));
 }

@@ -130,10 +130,17 @@ __device__ __forceinline__ void sincos_turn2(unsigned u0, unsigned u1, float2 &s
 // Grouping: group starts at run starts (first reflection, or (h, k) differ
 // from the previous reflection, or l is not the previous l + 1) and where
 // l = 0 mod 4.  A group holds the following reflections up to the next start.
+// Meridional reflections (h = k = 0) are groups of their own: there the
+// group's base phase l0 z and the rotation j z are multiples of the same
+// angle, so the rounding and polynomial errors of the two factors are
+// correlated instead of random, and over many atoms they add up to a bias
+// (e.g. 5e-6 of |F| for (0, 0, 2) = (0, 0, 1) rotated by z, 20,000 atoms).
+// Direct evaluation keeps their errors random; there are only ~2 l_max of them.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool group_start(const int32_t *hkl, int r) {
     const int l = hkl[3 * r + 2];
     if (r == 0 || (l & 3) == 0) return true;
+    if (hkl[3 * r] == 0 && hkl[3 * r + 1] == 0) return true;
     return hkl[3 * r] != hkl[3 * r - 3] || hkl[3 * r + 1] != hkl[3 * r - 2] || l != hkl[3 * r - 1] + 1;
 }
 

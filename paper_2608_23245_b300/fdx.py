@@ -89,8 +89,8 @@ def lib():
             L.fdx_ring_evals.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
             L.fdx_scatter_workspace_size.restype = C.c_size_t
             L.fdx_scatter_workspace_size.argtypes = [C.POINTER(Problem), C.c_int32]
-            L.fdx_scatter.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
-                                      C.c_void_p]
+            L.fdx_scatter.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                      C.c_size_t, C.c_void_p]
             L.fdx_scatter_evals.argtypes = [C.POINTER(Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                             C.c_size_t, C.c_void_p]
             _lib = L
@@ -316,13 +316,14 @@ def fdx_scatter_workspace_size(problem, n_samples: int) -> int:
     return int(lib().fdx_scatter_workspace_size(C.byref(problem), int(n_samples)))
 
 
-def fdx_scatter(problem, samples, image, workspace=None, stream=None):
-    """Scatter form: samples [n_s, 4] float32 (device), image [n_y, n_x] float32 (device)."""
+def fdx_scatter(problem, samples, image, workspace=None, stream=None, spot_size=1):
+    """Scatter form: samples [n_s, 4] float32 (device), image [n_y, n_x]
+    float32 (device); each hit rendered as a spot_size x spot_size spot."""
     import torch
     n_s = int(samples.shape[0])
     if workspace is None:
         workspace = torch.empty(fdx_scatter_workspace_size(problem, n_s), dtype=torch.uint8, device=image.device)
-    _check(lib().fdx_scatter(C.byref(problem), n_s, _ptr(samples), _ptr(image), _ptr(workspace),
+    _check(lib().fdx_scatter(C.byref(problem), n_s, _ptr(samples), int(spot_size), _ptr(image), _ptr(workspace),
                              int(workspace.numel()), _stream(stream)), "fdx_scatter")
     return image
 
@@ -392,12 +393,12 @@ class Simulation:
         counts = torch.empty_like(self.image, dtype=torch.int32)
         return fdx_ring_evals(self.prob, counts, workspace, stream)
 
-    def scatter(self, samples, image=None, workspace=None, stream=None):
+    def scatter(self, samples, image=None, workspace=None, stream=None, spot_size=1):
         """Structure factors (for M) must have been computed; scatter-form image."""
         import torch
         if image is None:
             image = torch.empty_like(self.image)
-        return fdx_scatter(self.prob, samples, image, workspace, stream)
+        return fdx_scatter(self.prob, samples, image, workspace, stream, spot_size)
 
     def scatter_evals(self, samples, workspace=None, stream=None):
         import torch

@@ -396,6 +396,50 @@ def scatter_samples(n_r: int, n_1: int, n_2: int, seed: int = SEED_BASE + 50) ->
     return out
 
 
+def scatter_samples_cauchy(n_r: int, n_1: int, n_2: int, scale: float, extent: float,
+                           seed: int = SEED_BASE + 51) -> np.ndarray:
+    """Seeded stratified samples for the scatter form whose angular coordinates
+    are heavy-tailed: the paper samples the shell from a Cauchy distribution
+    when the orientation distribution has a Lorentzian part, so that the slow
+    tails are not cut off at the sampling stage (Sect. "Angular peak shapes").
+
+    x_r is stratified uniform on [-1, 1].  x_1 and x_2 follow a Cauchy density
+    of half-width `scale` (normalised units: tan(gamma) / T) truncated to
+    |x| <= extent, drawn by inverse transform from stratified u:
+    x = scale tan(theta), theta = theta_max (2u - 1), theta_max =
+    atan(extent / scale), with density scale / ((scale^2 + x^2) 2 theta_max).
+    extent > 1 reaches past the node patch by (extent - 1) T.  The weight
+    q = 1 / (n pdf(x_r) pdf(x_1) pdf(x_2)) makes sum q f(x) an unbiased
+    estimate of the integral of f over [-1, 1] x [-extent, extent]^2.  Rows
+    (x_r, x_1, x_2, q) as float32, in 2 x 4 x 4 bricks like scatter_samples."""
+    if n_r % 2 or n_1 % 4 or n_2 % 4:
+        raise ValueError("grid must be a multiple of 2 x 4 x 4")
+    if not (scale > 0 and extent > 0):
+        raise ValueError("scale and extent must be positive")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jit = rng.uniform(0.0, 1.0, size=(n_r, n_1, n_2, 3))
+    th_max = math.atan(extent / scale)
+    n = n_r * n_1 * n_2
+    out = np.empty((n, 4), dtype=np.float32)
+    k = 0
+    for br in range(0, n_r, 2):
+        for b1 in range(0, n_1, 4):
+            for b2 in range(0, n_2, 4):
+                for ir in range(br, br + 2):
+                    for i1 in range(b1, b1 + 4):
+                        for i2 in range(b2, b2 + 4):
+                            j = jit[ir, i1, i2]
+                            xr = -1.0 + 2.0 * (ir + j[0]) / n_r
+                            th1 = th_max * (2.0 * (i1 + j[1]) / n_1 - 1.0)
+                            th2 = th_max * (2.0 * (i2 + j[2]) / n_2 - 1.0)
+                            x1, x2 = scale * math.tan(th1), scale * math.tan(th2)
+                            pdf = (0.5 * scale / ((scale * scale + x1 * x1) * 2.0 * th_max)
+                                   * scale / ((scale * scale + x2 * x2) * 2.0 * th_max))
+                            out[k] = (xr, x1, x2, 1.0 / (n * pdf))
+                            k += 1
+    return out
+
+
 def small_triclinic() -> Problem:
     """A general triclinic cell (alpha, beta, gamma != 90 deg), Voigt
     orientation, anisotropic g and axis B, 18x18 nodes, 64x48 detector;

@@ -131,7 +131,7 @@ def test_ring_and_scatter_argument_checks(fdx):
     for kw, code in (({"n_x": 0}, -1), ({"beam_axis": (0.0, 0.0, 1.0)}, -2)):
         prob = _problem(fdx, **kw)
         assert lib.fdx_ring(C.byref(prob), img, C.c_void_p(256), 1 << 30, None) == code
-        assert lib.fdx_scatter(C.byref(prob), 16, C.c_void_p(16), img, C.c_void_p(256), 1 << 30, None) == code
+        assert lib.fdx_scatter(C.byref(prob), 16, C.c_void_p(16), 1, img, C.c_void_p(256), 1 << 30, None) == code
     prob = _problem(fdx)
     need = lib.fdx_ring_workspace_size(C.byref(prob))
     assert need >= lib.fdx_workspace_size(1, fdx._problem_array([prob]))
@@ -140,10 +140,12 @@ def test_ring_and_scatter_argument_checks(fdx):
     assert lib.fdx_ring(C.byref(prob), img, C.c_void_p(264), need, None) == -3
     need_s = lib.fdx_scatter_workspace_size(C.byref(prob), 64)
     assert need_s > lib.fdx_scatter_workspace_size(C.byref(prob), 32) > 0
-    assert lib.fdx_scatter(C.byref(prob), 0, C.c_void_p(16), img, C.c_void_p(256), need_s, None) == -1
-    assert lib.fdx_scatter(C.byref(prob), 64, None, img, C.c_void_p(256), need_s, None) == -1
-    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(24), img, C.c_void_p(256), need_s, None) == -1
-    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(16), img, C.c_void_p(256), need_s - 1, None) == -3
+    assert lib.fdx_scatter(C.byref(prob), 0, C.c_void_p(16), 1, img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, None, 1, img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(24), 1, img, C.c_void_p(256), need_s, None) == -1
+    assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(16), 1, img, C.c_void_p(256), need_s - 1, None) == -3
+    for spot in (0, 2, -1, 17):     # the detector spot is an odd block of 1..15 pixels
+        assert lib.fdx_scatter(C.byref(prob), 64, C.c_void_p(16), spot, img, C.c_void_p(256), need_s, None) == -1
 
 
 def test_ring_workspace_holds_the_split_partials(fdx):

@@ -242,3 +242,24 @@ def test_adjoint_against_central_differences(orc):
     scale = max(abs(a) for a, _ in checks)
     for a, f in checks:
         assert a == pytest.approx(f, rel=1e-6, abs=1e-9 * scale)
+
+
+def test_edge_term_magnitude_marks_exactly_the_ambiguous_pixels(orc):
+    """The oracle's edge-term magnitude A (terms whose inclusion flips between
+    the support shrunk and grown by eta) is zero exactly where the strict and
+    loose counts agree, positive where they differ, and grows with eta (a
+    wider band holds at least the same terms); I and E are unchanged by asking
+    for it."""
+    p = W.small_helix()
+    hkl = orc.reflections(p.cell, p.d_min)
+    M = orc.intensities_M(p, hkl)
+    I0, E0 = orc.pattern(p, hkl, M)
+    for eta in (1e-3, 1e-2):
+        I, E, A = orc.pattern(p, hkl, M, eta=eta, with_ambiguous=True)
+        assert np.array_equal(I, I0) and np.array_equal(E[:, 0], E0[:, 0])
+        amb = E[:, 2] > E[:, 1]
+        assert amb.any() and np.all(A >= 0)
+        assert np.all((A > 0) == amb)
+    _, _, A1 = orc.pattern(p, hkl, M, eta=1e-3, with_ambiguous=True)
+    _, _, A2 = orc.pattern(p, hkl, M, eta=1e-2, with_ambiguous=True)
+    assert np.all(A2 >= A1) and A2.sum() > A1.sum()
