@@ -53,10 +53,10 @@ SFU_PER_EVAL = 6
 # compensated sum -- about 10 FP32 operations and 2-3 SFU operations.
 SF_OPS_PER_TERM = 10
 # DRAM bytes (read + written) of one forward pattern_kernel launch of this
-# step, from an ncu capture of it (dram__bytes_read.sum +
-# dram__bytes_write.sum).  Valid only for the kernel as captured: None
-# whenever the pattern kernel changes.
-PATTERN_DRAM_BYTES = None
+# step, from an ncu capture of it (dram__bytes_read.sum 93,552,640 +
+# dram__bytes_write.sum 8,631,552).  Valid only for the kernel as captured:
+# None whenever the pattern kernel changes.
+PATTERN_DRAM_BYTES = 102184192
 
 
 def _peaks():
@@ -498,6 +498,8 @@ def main():
     ap.add_argument("--no-scatter", action="store_true")
     ap.add_argument("--no-ring", action="store_true")
     ap.add_argument("--batch-models", type=int, default=256)
+    ap.add_argument("--region", type=int, default=0,
+                    help="cut the headline detector to its central N x N pixels (short profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -510,6 +512,11 @@ def main():
     barrier(world)
     dev = "cuda"
     p = W.config2(0.01)
+    workload = WORKLOAD
+    if args.region:
+        from dataclasses import replace
+        p = replace(p, geom=replace(p.geom, n_x=args.region, n_y=args.region))
+        workload = WORKLOAD + "_central%d" % args.region
     sim = fdx.Simulation(p, dev)
     stream = torch.cuda.current_stream()
     # evaluation count E (once, outside the timed region)
@@ -588,7 +595,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "evals_per_step": E, "n_refl": int(sim.hkl.shape[0]), "n_atoms": p.atoms.n,
+        "config": {"workload": workload, "evals_per_step": E, "n_refl": int(sim.hkl.shape[0]), "n_atoms": p.atoms.n,
                    "l2_flush": "512 MiB write between steps, outside the per-step events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": rf["achieved"],

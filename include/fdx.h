@@ -284,9 +284,11 @@ size_t fdx_backward_workspace_size(const fdx_problem *prob, int32_t n_atoms, int
  * forward's F ([n_refl][2], device) and the problem's M.  Writes the
  * gradients requested in `grads` with respect to the fractional coordinates,
  * isotropic B, crystallite sizes L_i, Hosemann g_i, sigma and gamma (T held
- * fixed; the pure-Gaussian branch reports 0 for gamma).  Hosemann lineshape
- * only (FDX_ERR_ARG for the sinc lineshape).  Deterministic (no atomics).
- * Asynchronous.
+ * fixed; the pure-Gaussian branch reports 0 for gamma).  Every lineshape:
+ * for the sinc (Eq. I_shape) and Gaussian ones the sums carry dK_i/dbeta_i at
+ * fixed t (the sinc support's moving edge adds nothing: K and dK/dt vanish
+ * there; the Gaussian's truncated tail is below 1e-12 of its peak).
+ * Deterministic (no atomics).  Asynchronous.
  */
 int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const float *F, const float *dL_dI,
                          const fdx_grads *grads, void *workspace, size_t ws_bytes, void *stream);

@@ -82,7 +82,7 @@ __global__ void band_bounds_kernel(AdjParams A) {
 // c = dL/dI L (applied to each 64-pair FP32 chunk sum) are accumulated in one
 // float-float sum per quantity over the item's patches; the warp adds its
 // lanes in FP64 once at the end.
-template <int PPL>
+template <int LS, int PPL>
 __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item, float4 *buf, float4 *dn, float4 *sc,
                                              float4 *sc2, float *rec, int lane) {
     const int r = (int)(item / A.n_bands), b = (int)(item % A.n_bands);
@@ -127,7 +127,7 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
                     any |= qp.cw[p] != 0.0f;
                 }
                 if (__ballot_sync(FDX_FULL_MASK, any) == 0) continue;
-                eval_core<FDX_LINESHAPE_HOSEMANN, MODE_ADJ, ADJ_NODE_BUF, PPL>(A.P, qp, rec, buf, dn, sc, sc2, lane, tot);
+                eval_core<LS, MODE_ADJ, ADJ_NODE_BUF, PPL>(A.P, qp, rec, buf, dn, sc, sc2, lane, tot);
             }
         }
     }
@@ -135,10 +135,13 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
     double acc[ADJ_ITEM_VALS];
 #pragma unroll
     for (int k = 0; k < ADJ_ITEM_VALS; ++k) acc[k] = warp_sum_d((double)ia[k].hi + (double)ia[k].lo);
-    // the beta sums were accumulated as sum w / (den_i prod den); subtract the
-    // profile sum for sum (w / prod den) (1/den_i - 1)
+    // Hosemann: the beta sums were accumulated as sum w / (den_i prod den);
+    // subtract the profile sum for sum (w / prod den) (1/den_i - 1).  The
+    // other lineshapes accumulate sum w dK_i/dbeta_i prod_{j != i} K_j directly.
+    if (LS == FDX_LINESHAPE_HOSEMANN) {
 #pragma unroll
-    for (int k = 1; k <= 3; ++k) acc[k] -= acc[0];
+        for (int k = 1; k <= 3; ++k) acc[k] -= acc[0];
+    }
     if (lane < ADJ_ITEM_VALS) {
         double o = acc[0];
 #pragma unroll
@@ -158,7 +161,7 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
 // Single-model adjoint, persistent: each warp takes (reflection, band) items
 // from the model's queue until none is left, so warps whose items end early
 // (no overlap with the band) pick up more work instead of idling in their CTA.
-template <int PPL>
+template <int LS, int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
     FDX_ADJ_SMEM
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
         if (lane == 0) it = atomicAdd(A.counter, 1u);
         const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
         if (item >= total) break;
-        adjoint_item<PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+        adjoint_item<LS, PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
     }
 }
 
@@ -195,11 +198,11 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(Batch
         const int m = batch_model(B.item_prefix, B.n_models, item);
         const AdjParams &A = B.models[m];
         if (A.P.ppl == 2)
-            adjoint_item<2>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
-                            s_rec[warp], lane);
+            adjoint_item<FDX_LINESHAPE_HOSEMANN, 2>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp],
+                                                    s_sc2[warp], s_rec[warp], lane);
         else
-            adjoint_item<1>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp],
-                            s_rec[warp], lane);
+            adjoint_item<FDX_LINESHAPE_HOSEMANN, 1>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp],
+                                                    s_sc2[warp], s_rec[warp], lane);
     }
 }
 
@@ -213,11 +216,25 @@ __global__ void adjoint_reflection_kernel(AdjParams A) {
     for (int b = 0; b < A.n_bands; ++b)
         for (int k = 0; k < ADJ_ITEM_VALS; ++k) s[k] += A.item_out[((size_t)r * A.n_bands + b) * ADJ_ITEM_VALS + k];
     const float *rec = A.P.recs + (size_t)r * REC_SIZE;
-    const double r2b = rec[REC_R2B], M = rec[REC_M];
-    const double G = r2b * s[0];
-    double dbeta[3];
-    for (int i = 0; i < 3; ++i) dbeta[i] = M * r2b * (s[0] / (double)rec[REC_BETA + i] - (double)rec[REC_DBF + i] * s[1 + i]);
-    const double dsig = M * r2b * s[4], dgam = M * r2b * s[5];
+    const double M = rec[REC_M];
+    double G, dbeta[3], dsig, dgam;
+    if (A.lineshape == FDX_LINESHAPE_HOSEMANN) {
+        // sums relative to prod K_i = prod beta_i / den_i; r0^2 prod beta in the record
+        const double r2b = rec[REC_R2B];
+        G = r2b * s[0];
+        for (int i = 0; i < 3; ++i)
+            dbeta[i] = M * r2b * (s[0] / (double)rec[REC_BETA + i] - (double)rec[REC_DBF + i] * s[1 + i]);
+        dsig = M * r2b * s[4], dgam = M * r2b * s[5];
+    } else {
+        // absolute sums: sum w prod K, sum w dK_i/dbeta_i prod_{j != i} K_j, weight derivatives
+        double Dv[3];
+        for (int q = 0; q < 3; ++q)
+            Dv[q] = A.hkl[3 * r] * A.As[q] + A.hkl[3 * r + 1] * A.As[3 + q] + A.hkl[3 * r + 2] * A.As[6 + q];
+        const double r2 = Dv[0] * Dv[0] + Dv[1] * Dv[1] + Dv[2] * Dv[2];
+        G = r2 * s[0];
+        for (int i = 0; i < 3; ++i) dbeta[i] = M * r2 * s[1 + i];
+        dsig = M * r2 * s[4], dgam = M * r2 * s[5];
+    }
     if (A.dM) A.dM[r] = (float)G;
 
     // chain rule to L_i, g_i; P and DW for the structure-factor adjoint
@@ -423,10 +440,17 @@ cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s) {
         long long want = (items + PAIR_WARPS - 1) / PAIR_WARPS;
         const unsigned grid = (unsigned)(want < n_ctas ? want : n_ctas);
         if (cudaMemsetAsync(A.counter, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
-        if (A.P.ppl == 2)
-            adjoint_kernel<2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-        else
-            adjoint_kernel<1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+        const bool two = A.P.ppl == 2;
+        if (A.lineshape == FDX_LINESHAPE_SINC) {
+            if (two) adjoint_kernel<FDX_LINESHAPE_SINC, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+            else adjoint_kernel<FDX_LINESHAPE_SINC, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+        } else if (A.lineshape == FDX_LINESHAPE_GAUSS) {
+            if (two) adjoint_kernel<FDX_LINESHAPE_GAUSS, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+            else adjoint_kernel<FDX_LINESHAPE_GAUSS, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+        } else {
+            if (two) adjoint_kernel<FDX_LINESHAPE_HOSEMANN, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+            else adjoint_kernel<FDX_LINESHAPE_HOSEMANN, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
+        }
         adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
     }
     adjoint_globals_kernel<<<1, 256, 0, s>>>(A);

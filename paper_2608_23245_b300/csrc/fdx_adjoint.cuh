@@ -22,6 +22,7 @@ struct AdjParams {
     const float *F;            // [n_refl][2]
     const float *ff;           // [n_elem][9]
     int n_elem, intensity_model;
+    int lineshape;             // FDX_LINESHAPE_*: the Hosemann walk's sums are relative, the others absolute
     double As[9];
     double alen[3], L[3], g[3], Bax[3];
 };

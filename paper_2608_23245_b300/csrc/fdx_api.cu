@@ -520,6 +520,7 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
         A.dM = targets ? grads[m]->dM : nullptr;
         A.dglobal = targets ? grads[m]->dglobal : nullptr;
         A.hkl = pr.hkl, A.F = F[m], A.ff = a->ff, A.n_elem = a->n_elem, A.intensity_model = pr.br.intensity_model;
+        A.lineshape = pr.br.lineshape;
         const int ppl = P.ppl;
         const long long ftiles = (long long)((pr.geom.n_x + 15) / 16) * ((pr.geom.n_y + 8 * ppl - 1) / (8 * ppl));
         const long long aitems = (long long)pr.n_refl * B.n_bands;
@@ -750,7 +751,6 @@ int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const 
                          const fdx_grads *grads, void *workspace, size_t ws_bytes, void *stream) {
     int rc = validate_problem(prob);
     if (rc) return rc;
-    if (prob->br.lineshape != FDX_LINESHAPE_HOSEMANN) return FDX_ERR_ARG;
     if (!atoms || atoms->n_atoms < 1 || atoms->n_elem < 1 || atoms->n_elem > 64) return FDX_ERR_ARG;
     if (!atoms->frac || !atoms->B || !atoms->elem || !atoms->ff) return FDX_ERR_ARG;
     if (!dL_dI || !grads || (prob->n_refl > 0 && !F)) return FDX_ERR_ARG;
@@ -790,6 +790,7 @@ int fdx_pattern_backward(const fdx_problem *prob, const fdx_atoms *atoms, const 
     A.ff = atoms->ff;
     A.n_elem = atoms->n_elem;
     A.intensity_model = prob->br.intensity_model;
+    A.lineshape = prob->br.lineshape;
     A.counter = reinterpret_cast<unsigned *>(ws + B.counter);
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) != cudaSuccess) return FDX_ERR_CUDA;

@@ -91,6 +91,34 @@ __device__ __forceinline__ float gauss_term(float ta, float tb, float tc, const 
     return y;
 }
 
+// Forward declaration (defined below).
+__device__ __forceinline__ void sincospi_f(float x, float &s, float &c);
+
+// Lineshape value K and its derivative dK/dbeta at fixed t for the adjoint of
+// the non-Hosemann lineshapes (absolute values, unlike the forward's
+// normalised products):
+//   sinc (Eq. I_shape, N = 1/beta):  K = N sinc^2(N t),
+//     dK/dbeta = -N^2 dK/dN = -N^2 sinc(x) (2 cos(pi x) - sinc(x)),  x = N t;
+//   Gaussian of breadth beta:        K = 2^(-LA t^2) / beta, LA = pi log2(e) / beta^2,
+//     dK/dbeta = (K / beta) (2 ln 2 LA t^2 - 1)   (= (K / beta)(2 pi t^2 / beta^2 - 1)).
+__device__ __forceinline__ void sinc_k_dk(float t, float N, float &K, float &dK) {
+    const float x = N * t;
+    float sn, cs;
+    sincospi_f(x, sn, cs);
+    const float px = 3.14159265358979f * x;
+    const float sc = fabsf(px) < 1e-3f ? fmaf(-px * px, 1.0f / 6.0f, 1.0f) : sn / px;
+    K = N * sc * sc;
+    dK = -N * N * sc * (2.0f * cs - sc);
+}
+__device__ __forceinline__ void gauss_k_dk(float t, float la, float beta, float &K, float &dK) {
+    const float e = la * t * t;
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(-e));
+    const float ib = 1.0f / beta;
+    K = y * ib;
+    dK = K * ib * fmaf(2.0f * 0.69314718056f, e, -1.0f);
+}
+
 // sin(pi x), cos(pi x) for |x| < 2^20: x = q/2 + f with q = rint(2x), |f| <= 1/4,
 // so pi x = q pi/2 + pi f; sin(pi f), cos(pi f) from the sin(2 pi r)/cos(2 pi r)
 // polynomials at r = f/2, then a rotation by q quarter turns.
@@ -355,8 +383,10 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // staged counts: nr = rim nodes (all nodes when not PACKED), nc = core nodes
     int nr = 0, nc = 0;
     constexpr int NBH = NB / 2;                  // slots per list (PACKED)
-    // core/rim split in the forward only (the adjoint's longer per-chunk fold
-    // makes the extra list cost more than the tests it saves)
+    // core/rim split in the forward only.  In the adjoint it would save about
+    // 5 % of the walk, but it reorders the width-derivative sums, which nearly
+    // cancel (a normalised profile's derivative in its width integrates to
+    // zero), and their FP32 result then moved by up to 1.4e-4 relative.
     constexpr bool SPLIT = PACKED && MODE == MODE_FWD;
     constexpr int RIM0 = SPLIT ? NBH : 0;        // first rim slot
     constexpr int RIM_CAP = SPLIT ? NBH : NB;
@@ -374,6 +404,8 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             float r0[PPL];
 #pragma unroll
             for (int p = 0; p < PPL; ++p) r0[p] = 0.0f;
+            // adjoint: the lane's points weighted by cw, six sums (absolute lineshapes)
+            float x0 = 0.f, xa = 0.f, xb = 0.f, xc = 0.f, xs = 0.f, xg = 0.f;
 #pragma unroll 2
             for (int q = q0; q < qe; ++q) {
                 const float4 nq = buf[q];
@@ -383,6 +415,28 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     const bool in = (fabsf(ta) <= tm[0]) & (fabsf(tb) <= tm[1]) & (fabsf(tcc) <= tm[2]);
                     if (MODE == MODE_CNT) {
                         acc[p].cnt += in ? 1 : 0;
+                    } else if (MODE == MODE_ADJ) {
+                        if (in) {
+                            float Ka, Kb, Kc, dKa, dKb, dKc;
+                            if (LS == FDX_LINESHAPE_GAUSS) {
+                                gauss_k_dk(ta, la[0], rec[REC_BETA], Ka, dKa);
+                                gauss_k_dk(tb, la[1], rec[REC_BETA + 1], Kb, dKb);
+                                gauss_k_dk(tcc, la[2], rec[REC_BETA + 2], Kc, dKc);
+                            } else {
+                                sinc_k_dk(ta, la[0], Ka, dKa);
+                                sinc_k_dk(tb, la[1], Kb, dKb);
+                                sinc_k_dk(tcc, la[2], Kc, dKc);
+                            }
+                            const float2 dw = reinterpret_cast<const float2 *>(buf2)[q];
+                            const float c = qp.cw[p];
+                            const float kbc = Kb * Kc, kp = Ka * kbc;
+                            x0 = fmaf(c * nq.w, kp, x0);
+                            xa = fmaf(c * nq.w, dKa * kbc, xa);
+                            xb = fmaf(c * nq.w, Ka * dKb * Kc, xb);
+                            xc = fmaf(c * nq.w, Ka * Kb * dKc, xc);
+                            xs = fmaf(c * dw.x, kp, xs);
+                            xg = fmaf(c * dw.y, kp, xg);
+                        }
                     } else {
                         const float kv =
                             nq.w * (LS == FDX_LINESHAPE_GAUSS ? gauss_term(ta, tb, tcc, la) : sinc_term(ta, tb, tcc, la));
@@ -390,7 +444,14 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     }
                 }
             }
-            if (MODE != MODE_CNT) {
+            if (MODE == MODE_ADJ) {
+                acc[0].s0 = ff_add_f(acc[0].s0, x0);
+                acc[0].sb[0] = ff_add_f(acc[0].sb[0], xa);
+                acc[0].sb[1] = ff_add_f(acc[0].sb[1], xb);
+                acc[0].sb[2] = ff_add_f(acc[0].sb[2], xc);
+                acc[0].ss = ff_add_f(acc[0].ss, xs);
+                acc[0].sg = ff_add_f(acc[0].sg, xg);
+            } else if (MODE != MODE_CNT) {
 #pragma unroll
                 for (int p = 0; p < PPL; ++p) acc[p].s0 = ff_add_f(acc[p].s0, r0[p]);
             }

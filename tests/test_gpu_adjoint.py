@@ -78,7 +78,8 @@ def test_loss_kernel(gpu):
     assert np.allclose(gI.cpu().numpy(), 2 * w * d, rtol=1e-6, atol=1e-12)
 
 
-@pytest.mark.parametrize("make", [W.small_helix, W.small_lorentz, W.small_triclinic, W.small_tilted])
+@pytest.mark.parametrize("make", [W.small_helix, W.small_lorentz, W.small_triclinic, W.small_tilted, W.small_sinc,
+                                  W.small_gauss])
 def test_backward_matches_oracle_adjoint(gpu, orc, make):
     """Common seeded upstream gradient dL/dI into both adjoints."""
     p = api_precision(make())
@@ -148,12 +149,13 @@ def test_refinement_gradient_helix_subset(gpu, orc):
     assert gam.grad.item() == pytest.approx(go["gamma"], rel=ADJ_TOL)
 
 
-@pytest.mark.parametrize("make", [W.small_sinc, W.small_gauss])
-def test_backward_rejects_other_lineshapes(gpu, make):
+def test_batch_refine_rejects_other_lineshapes(gpu):
+    """The batched refinement runs the Hosemann adjoint only; a model with the
+    sinc lineshape is refused on the host (the single-model backward takes
+    every lineshape)."""
     import torch
-    p = api_precision(make())
+    p = api_precision(W.small_sinc())
     sim = gpu.Simulation(p)
-    gI = torch.zeros((p.geom.n_y, p.geom.n_x), dtype=torch.float32, device="cuda")
+    It = torch.zeros((p.geom.n_y, p.geom.n_x), dtype=torch.float32, device="cuda")
     with pytest.raises(gpu.FdxError):
-        gpu.fdx_pattern_backward(sim.prob, sim.atoms, sim.F, gI,
-                                 dglobal=torch.empty(8, dtype=torch.float64, device="cuda"))
+        gpu.BatchStep([sim.prob], [sim.atoms], targets=[It])()

@@ -6,7 +6,9 @@ benchmark times.
   end, against the FP64 oracle's at 1,024 seeded pixels over the whole
   detector plus the full meridian column and equator row.  The oracle values
   come from tests/golden/make_config2_samples.py (oracle only), stored with a
-  fingerprint of the inputs.
+  fingerprint of the inputs.  Where a pixel has terms within rounding of the
+  lineshape support's edge (FP32 here, FP64 in the oracle) it has two correct
+  values; those pixels are bounded by the magnitude of their edge terms.
 - Batched refinement: eight real models of the 256-model recipe (the one with
   the most atoms, the one with the largest detector, six seeded others),
   through fdx_batch_refine with a 256-pixel mask, against the oracle's forward
@@ -58,15 +60,26 @@ def test_large_forward_full_size(gpu, g):
     cnt = sim.evals()
     torch.cuda.synchronize()
     img, cnt = img.cpu().numpy(), cnt.cpu().numpy()
-    I, E = data[key + "_I"], data[key + "_E"]
+    I, E, A = data[key + "_I"], data[key + "_E"], data[key + "_A"]
     ii, jj = pix[:, 0], pix[:, 1]
+    got = img[jj, ii].astype(np.float64)
+    # A pixel with terms within rounding of the support's edge (the Hosemann
+    # factor is beta, not zero, at |t| = 1/2, so each such term is a jump) has
+    # two correct values, the kernel deciding in FP32 and the oracle in FP64;
+    # every other pixel has one.  Unambiguous pixels: the gates (max per line
+    # of pixels, L2 over the whole sample).  Ambiguous ones: off by at most the
+    # magnitude of their edge terms.
+    one = A == 0.0
+    err = np.abs(got - I)
     n_rand = len(pix) - p.geom.n_x - p.geom.n_y
     for name, sl in (("random", slice(0, n_rand)), ("meridian", slice(n_rand, n_rand + p.geom.n_y)),
                      ("equator", slice(n_rand + p.geom.n_y, len(pix)))):
-        got = img[jj[sl], ii[sl]]
-        assert I[sl].max() > 0, name
-        mr, l2 = parity(got, I[sl])
-        assert mr <= MAX_REL and l2 <= L2_REL, (name, mr, l2)
+        mx = np.abs(I[sl]).max()
+        assert mx > 0 and one[sl].mean() > 0.5, (name, one[sl].mean())
+        assert err[sl][one[sl]].max() <= MAX_REL * mx, (name, err[sl][one[sl]].max() / mx)
+        assert np.all(err[sl] <= A[sl] + MAX_REL * mx), (name, np.max(err[sl] - A[sl]) / mx)
+    l2 = np.linalg.norm(err[one]) / np.linalg.norm(I[one])
+    assert l2 <= L2_REL, l2
     c = cnt[jj, ii]
     assert np.all(c >= E[:, 1]) and np.all(c <= E[:, 2]), (int(np.sum(c < E[:, 1])), int(np.sum(c > E[:, 2])))
     assert int(E[:, 0].sum()) > 10 ** 8
@@ -142,3 +155,35 @@ def test_batched_real_models(gpu, orc):
                 assert abs(dg[i]) <= 1e-6 * np.max(np.abs(ref_g)), (chosen[k], name)
             else:
                 assert dg[i] == pytest.approx(ref_g[i], rel=ADJ_TOL), (chosen[k], name, dg[i], ref_g[i])
+
+
+def test_large_structure_factors(gpu, orc):
+    """Structure factors of the large workload against the oracle: every
+    meridional reflection (h = k = 0, where consecutive-l groups would
+    multiply factors of the same angle, whose errors would then add up instead
+    of averaging out: 5e-6 of the amplitude scale for (0, 0, 2) before such
+    reflections were evaluated directly) to 1e-6 of the amplitude scale
+    sqrt(sum amp^2), a seeded 8,000-reflection sample to the general
+    structure-factor tolerance, and M consistent with F's error."""
+    import torch
+    from _common import SF_TOL, amp_scale
+    p = api_precision(W.config2(0.01))
+    sim = gpu.Simulation(p)
+    F, M = sim.structure_factors()
+    torch.cuda.synchronize()
+    h = sim.hkl_host
+    mer = np.where((h[:, 0] == 0) & (h[:, 1] == 0))[0]
+    rng = np.random.default_rng(8000)
+    idx = np.unique(np.concatenate([mer, rng.choice(len(h), 8000, replace=False)]))
+    Fo = orc.structure_factors(p.cell, p.atoms, h[idx])
+    Mo = orc.intensities_M(p, h[idx], Fo)
+    Fg = F.cpu().numpy()[idx].astype(np.float64)
+    Mg = M.cpu().numpy()[idx].astype(np.float64)
+    scale = amp_scale(p, h[idx])
+    err = np.abs((Fg[:, 0] + 1j * Fg[:, 1]) - Fo) / scale
+    is_mer = np.isin(idx, mer)
+    assert is_mer.sum() >= 80 and err[is_mer].max() <= 1e-6, (err[is_mer].max(), h[idx][is_mer][np.argmax(err[is_mer])])
+    assert err.max() <= SF_TOL, (err.max(), h[idx][np.argmax(err)])
+    d = SF_TOL * scale
+    pdw = Mo / np.maximum(np.abs(Fo) ** 2, 1e-300)
+    assert np.all(np.abs(Mg - Mo) <= (2.0 * np.abs(Fo) + d) * d * pdw + 1e-6 * Mo)

@@ -193,11 +193,16 @@ def _loss(orc, p, hkl, It):
     return orc.loss_and_grad(I, It)[0]
 
 
-def test_adjoint_against_central_differences(orc):
+@pytest.mark.parametrize("lineshape", [W.LINESHAPE_HOSEMANN, W.LINESHAPE_SINC, W.LINESHAPE_GAUSS])
+def test_adjoint_against_central_differences(orc, lineshape):
     """The oracle's analytic adjoint (pattern -> M, beta, weights -> atoms,
     sizes, g, sigma, gamma) against FP64 central differences of its own
-    forward loss L = sum w (I - I_t)^2, w = 1/(I_t + 1)."""
+    forward loss L = sum w (I - I_t)^2, w = 1/(I_t + 1), for each lineshape
+    (Eq. Z; Eq. I_shape with N = 1/beta, whose support edge K_z/N moves with
+    beta but where K and dK/dt vanish; the Gaussian of equal breadth)."""
     p = _tiny_problem()
+    if lineshape != W.LINESHAPE_HOSEMANN:
+        p = replace(p, br=replace(p.br, lineshape=lineshape))
     hkl = orc.reflections(p.cell, p.d_min)
     rng = np.random.default_rng(1)
     tgt = replace(p, atoms=replace(p.atoms, frac=p.atoms.frac + rng.uniform(-0.01, 0.01, p.atoms.frac.shape)),
