@@ -316,7 +316,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
         const float den = X0 - Dl;
         degenerate = !(den > 0.05f);
         if (!degenerate) {
-            const float inv = __frcp_rn(X0), ivd = __frcp_rn(den);
+            const float inv = rcp_approx(X0), ivd = rcp_approx(den);  // bounds only
             const float d1 = X1 * inv, d2 = X2 * inv;
             const float w1 = Dl * (1.0f + fabsf(d1)) * ivd, w2 = Dl * (1.0f + fabsf(d2)) * ivd;
             const float T = P.T, ih = P.inv_h;
@@ -375,9 +375,15 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     const int nbr = (nrows + BR - 1) / BR, nbc = (ncols + BC - 1) / BC, nblk = nbr * nbc;
     const float hgrid = 1.0f / P.inv_h;
     const float rho_b = hgrid * 3.8079f;  // sqrt(1.5^2 + 3.5^2)
+    // (the block centres are evaluated in plain FP32 with an approximate rsqrt:
+    // an error of a few 1e-7 in u, times the coefficients of sigma, is added)
     float bw[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) bw[i] = th[i] + rec[REC_AR0 + i] * rho_b + 1e-4f;
+    for (int i = 0; i < 3; ++i)
+        bw[i] = th[i] + rec[REC_AR0 + i] * rho_b + 1e-4f + 1e-6f * (fabsf(hh[i]) + fabsf(E1[i]) + fabsf(E2[i]));
+    // block index -> (row, column) without an integer division: blk < 2^13
+    // and the quotient's fractional part is at least 0.5 / nbc from an integer
+    const float inv_nbc = rcp_approx((float)nbc);
     const unsigned lt_mask = (1u << lane) - 1u;
     const int bj_lane = lane / BC, bm_lane = lane % BC;  // this lane's node inside a block
     // staged counts: nr = rim nodes (all nodes when not PACKED), nc = core nodes
@@ -494,10 +500,11 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             }
             __syncwarp();
             if (q < npad) {
-                float sa, ca, sb, cb, sc, cc;
-                sincospi_f(nq.x, sa, ca);
-                sincospi_f(nq.y, sb, cb);
+                float2 sab, cab;
+                float sc, cc;
+                sincospi_f2(make_float2(nq.x, nq.y), sab, cab);  // axes a, b on packed pairs
                 sincospi_f(nq.z, sc, cc);
+                const float sa = sab.x, ca = cab.x, sb = sab.y, cb = cab.y;
                 const int u = (base >> 1) + (q >> 1), o = q & 1;
                 bf[8 * u + o] = -nq.x, bf[8 * u + 2 + o] = -nq.y, bf[8 * u + 4 + o] = -nq.z, bf[8 * u + 6 + o] = nq.w;
                 bs[8 * u + o] = slb[0] * ca, bs[8 * u + 2 + o] = slb[0] * sa;
@@ -653,13 +660,11 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
         {
             const int blk = blk0 + lane;
             if (blk < nblk) {
-                const int bj = blk / nbc, bm = blk - bj * nbc;
+                const int bj = (int)(((float)blk + 0.5f) * inv_nbc), bm = blk - bj * nbc;
                 const float d1 = -P.T + (J0 + bj * BR + 0.5f * (BR - 1) + 0.5f) * hgrid;
                 const float d2 = -P.T + (M0 + bm * BC + 0.5f * (BC - 1) + 0.5f) * hgrid;
-                const float rho2 = fmaf(d1, d1, d2 * d2);
-                const float q = sqrtf(1.0f + rho2);
-                const float c = 1.0f / q;
-                const float u0 = -rho2 / (q * (1.0f + q)) - dP[0].hi;
+                const float c = rsqrtf(1.0f + fmaf(d1, d1, d2 * d2));
+                const float u0 = (c - 1.0f) - dP[0].hi;
                 const float u1 = d1 * c - dP[1].hi, u2 = d2 * c - dP[2].hi;
                 blive = true;
 #pragma unroll
@@ -670,17 +675,40 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             }
         }
         unsigned bmask = __ballot_sync(FDX_FULL_MASK, blive);
-        while (bmask) {
-            const int blk = blk0 + __ffs(bmask) - 1;
+        // The live blocks of this round one after another; the node entries of
+        // the next live block are loaded while the current one is staged.
+        // Every lane loads an entry of the grid (clamped into it); lanes whose
+        // node lies outside the bounding box drop theirs.
+        auto node_of = [&](int blk, int &jj, int &mm) {
+            const int bj = (int)(((float)blk + 0.5f) * inv_nbc), bm = blk - bj * nbc;
+            jj = J0 + bj * BR + bj_lane, mm = M0 + bm * BC + bm_lane;
+        };
+        int jc = 0, mc = 0;
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+        float2 dn = make_float2(0.f, 0.f);
+        bool have = bmask != 0;
+        if (have) {
+            node_of(blk0 + __ffs(bmask) - 1, jc, mc);
             bmask &= bmask - 1;
-            const int bj = blk / nbc, bm = blk - bj * nbc;
-            const int jj = J0 + bj * BR + bj_lane, mm = M0 + bm * BC + bm_lane;
+            const size_t k = (size_t)min(jc, J1) * n + min(mc, M1);
+            na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
+            if (MODE == MODE_ADJ) dn = P.dnodes[k];
+        }
+        while (have) {
+            int jn = 0, mn = 0;
+            float4 na2 = make_float4(0.f, 0.f, 0.f, 0.f), nb2 = na2;
+            float2 dn2 = make_float2(0.f, 0.f);
+            const bool more = bmask != 0;
+            if (more) {
+                node_of(blk0 + __ffs(bmask) - 1, jn, mn);
+                bmask &= bmask - 1;
+                const size_t k = (size_t)min(jn, J1) * n + min(mn, M1);
+                na2 = P.nodes[2 * k], nb2 = P.nodes[2 * k + 1];
+                if (MODE == MODE_ADJ) dn2 = P.dnodes[k];
+            }
             bool live = false;
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-            float2 val2 = make_float2(0.f, 0.f);
-            if (jj <= J1 && mm <= M1) {
-                const size_t k = (size_t)jj * n + mm;
-                const float4 na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
+            if (jc <= J1 && mc <= M1) {
                 // u = s_k/r0 - p_ref/r0 in the local frame = (c - 1, c d1, c d2) - dP
                 const float u0 = (na.x - dP[0].hi) + (na.y - dP[0].lo);
                 const float u1 = (na.z - dP[1].hi) + (na.w - dP[1].lo);
@@ -691,7 +719,6 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                 live = (fabsf(sg[0] - tc[0]) <= th[0]) & (fabsf(sg[1] - tc[1]) <= th[1]) &
                        (fabsf(sg[2] - tc[2]) <= th[2]);
                 val = make_float4(sg[0], sg[1], sg[2], nb.z);
-                if (MODE == MODE_ADJ) val2 = P.dnodes[k];
             }
             bool core = false;
             if (SPLIT)
@@ -702,11 +729,12 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             if (live) {
                 const int pos = core ? nc + __popc(balc & lt_mask) : RIM0 + nr + __popc(bal & lt_mask);
                 buf[pos] = val;
-                if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = val2;
+                if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = dn;
             }
             nr += __popc(bal);
             nc += __popc(balc);
             if (nr > RIM_CAP - 32 || nc > NBH - 32) flush();
+            have = more, jc = jn, mc = mn, na = na2, nb = nb2, dn = dn2;
         }
     }
     if (nr > 0 || nc > 0) flush();
