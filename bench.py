@@ -368,8 +368,7 @@ def batch_measurements(n_models=256, tune_models=8, replays=5, loops=2, rank=0, 
         del s
     probs = [s.prob for s in sims]
     datoms = [s.atoms for s in sims]
-    grid = {"ppl_max": (2, 1), "fwd_ctas_per_sm": (4, 3), "adj_ctas_per_sm": (3, 2), "adj_bands": (64, 32)}
-    best, _ = tune.autotune_batch(probs[:tune_models], datoms[:tune_models], tims[:tune_models], grid=grid)
+    best, _ = tune.autotune_batch(probs[:tune_models], datoms[:tune_models], tims[:tune_models])
     E = 0
     for s in sims:
         s.forward()

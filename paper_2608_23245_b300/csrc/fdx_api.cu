@@ -16,7 +16,7 @@ namespace {
 constexpr size_t kAlign = 256;
 
 std::mutex g_tune_mu;
-fdx_tuning g_tune = {2, 4, 3, 64};
+fdx_tuning g_tune = {2, 4, 3, 64, 0};
 
 fdx_tuning tuning() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -193,6 +193,12 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
         double amax = 0.0;
         for (int q = 0; q < 3; ++q) amax = fmax(amax, rp.alen[q]);
         P.ppl = (pitch * 8.0 * sqrt(2.0) * amax <= 0.5 && tuning().ppl_max >= 2) ? 2 : 1;
+    }
+    // node blocks of the culling: 2^blk_lr rows x 2^blk_lc columns, 32 nodes
+    {
+        static const int lr[4] = {2, 3, 1, 4};
+        const int nb = tuning().node_block;
+        P.blk_lr = lr[nb], P.blk_lc = 5 - lr[nb];
     }
     P.pixgeo = pp.pixgeo;
     P.reach = rp.reach;
@@ -597,10 +603,11 @@ int fdx_status(void *stream, int *device_status) {
 }
 
 int fdx_set_tuning(const fdx_tuning *t) {
-    fdx_tuning v = {2, 4, 3, 64};
+    fdx_tuning v = {2, 4, 3, 64, 0};
     if (t) {
         if (t->ppl_max < 1 || t->ppl_max > 2 || t->fwd_ctas_per_sm < 1 || t->fwd_ctas_per_sm > 8 ||
-            t->adj_ctas_per_sm < 1 || t->adj_ctas_per_sm > 8 || t->adj_bands < 1 || t->adj_bands > 256)
+            t->adj_ctas_per_sm < 1 || t->adj_ctas_per_sm > 8 || t->adj_bands < 1 || t->adj_bands > 256 ||
+            t->node_block < 0 || t->node_block > 3)
             return FDX_ERR_ARG;
         v = *t;
     }

@@ -125,6 +125,7 @@ struct PatternParams {
     int nx, ny, n_refl, n_nodes;
     int ppl;              // pixels per lane of the forward kernel (1 or 2)
     float T, inv_h;       // grid half-extent, 1 / node spacing
+    int blk_lr, blk_lc;   // node blocks of the culling: 2^blk_lr rows x 2^blk_lc columns (blk_lr + blk_lc = 5)
     float AZ[3];          // a_i . n (cell constants)
     double delta_L;
     const float4 *pixgeo; // [ny*nx] (R hi, R lo, Z hi, Z lo)

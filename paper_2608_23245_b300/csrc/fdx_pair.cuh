@@ -5,10 +5,12 @@
 //
 // For the pair the warp
 //   1. bounds the node rows/columns that can be in any lane's support by the
-//      gnomonic projection of each lane's support-box corners (union over lanes);
-//   2. computes, one node per lane, sigma_i(k) = a_i . (s_k - p_ref) relative to
-//      the query point of lane 0's pixel, with float-float differences, keeps
-//      the nodes whose sigma lies within the warp's tau range widened by the
+//      gnomonic projection of the support-box corners around the patch's
+//      reference point, widened by the patch's spread;
+//   2. culls blocks of 32 nodes at their centres, then computes, one node per
+//      lane, sigma_i(k) = a_i . (s_k - p_ref) relative to the reference point
+//      (the patch's central pixel) with float-float differences, keeps the
+//      nodes whose sigma lies within the warp's tau range widened by the
 //      support half-width, and compacts them into the warp's shared buffer;
 //   3. every lane walks the buffer: t_i = tau_i - sigma_i with
 //      tau_i = a_i . (p - p_ref), support test, lineshape product, weight.
@@ -367,14 +369,15 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
         th[i] = 0.5f * (hi - lo) + tm[i] + 1e-5f;
     }
     const int nrows = J1 - J0 + 1, ncols = M1 - M0 + 1;
-    // Block culling: the bounding box is cut into 4 x 8-node blocks; a block is
-    // skipped when, at its centre, sigma_i is farther from the warp's tau
-    // window than |a_i| r0 rho_b, rho_b being the block's half-diagonal in the
-    // gnomonic plane (|d s / d d| <= r0, so sigma_i varies by at most that).
-    constexpr int BR = 4, BC = 8;
-    const int nbr = (nrows + BR - 1) / BR, nbc = (ncols + BC - 1) / BC, nblk = nbr * nbc;
+    // Block culling: the bounding box is cut into BR x BC-node blocks (32
+    // nodes, the shape a tuning knob); a block is skipped when, at its centre,
+    // sigma_i is farther from the warp's tau window than |a_i| r0 rho_b, rho_b
+    // being the block's half-diagonal in the gnomonic plane (|d s / d d| <= r0,
+    // so sigma_i varies by at most that).
+    const int lr = P.blk_lr, lc = P.blk_lc, BR = 1 << lr, BC = 1 << lc;
+    const int nbr = (nrows + BR - 1) >> lr, nbc = (ncols + BC - 1) >> lc, nblk = nbr * nbc;
     const float hgrid = 1.0f / P.inv_h;
-    const float rho_b = hgrid * 3.8079f;  // sqrt(1.5^2 + 3.5^2)
+    const float rho_b = hgrid * sqrtf(0.25f * (float)((BR - 1) * (BR - 1) + (BC - 1) * (BC - 1)));
     // (the block centres are evaluated in plain FP32 with an approximate rsqrt:
     // an error of a few 1e-7 in u, times the coefficients of sigma, is added)
     float bw[3];
@@ -385,7 +388,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // and the quotient's fractional part is at least 0.5 / nbc from an integer
     const float inv_nbc = rcp_approx((float)nbc);
     const unsigned lt_mask = (1u << lane) - 1u;
-    const int bj_lane = lane / BC, bm_lane = lane % BC;  // this lane's node inside a block
+    const int bj_lane = lane >> lc, bm_lane = lane & (BC - 1);  // this lane's node inside a block
     // staged counts: nr = rim nodes (all nodes when not PACKED), nc = core nodes
     int nr = 0, nc = 0;
     constexpr int NBH = NB / 2;                  // slots per list (PACKED)

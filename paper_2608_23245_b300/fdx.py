@@ -576,7 +576,19 @@ class BatchStep:
 
 class Tuning(C.Structure):
     _fields_ = [("ppl_max", C.c_int32), ("fwd_ctas_per_sm", C.c_int32), ("adj_ctas_per_sm", C.c_int32),
-                ("adj_bands", C.c_int32)]
+                ("adj_bands", C.c_int32), ("node_block", C.c_int32)]
+
+    DEFAULTS = {"ppl_max": 2, "fwd_ctas_per_sm": 4, "adj_ctas_per_sm": 3, "adj_bands": 64, "node_block": 0}
+
+    @classmethod
+    def of(cls, **knobs):
+        """A tuning with the library defaults, overridden by `knobs`."""
+        v = dict(cls.DEFAULTS)
+        v.update(knobs)
+        return cls(**v)
+
+    def as_dict(self):
+        return {name: int(getattr(self, name)) for name, _ in self._fields_}
 
 
 def fdx_set_tuning(t=None):

@@ -1,12 +1,17 @@
-"""Autotuner of the batched refinement step's launch shapes.
+"""Autotuner of the batched refinement step's launch and chunk shapes.
 
-Times fdx_batch_refine on the caller's own models for a small grid of
-fdx_tuning settings (pixels per lane, persistent CTAs per SM of the forward
-and adjoint kernels, adjoint bands per reflection), keeps the fastest, sets it
-process-wide, and caches the choice in a JSON file keyed by a signature of
-the workload (model count, detector sizes, reflection and atom counts, node
-grids), so a later run of the same workload starts from the tuned setting.
-All timing is on the device with CUDA events.
+Times fdx_batch_refine on the caller's own models over fdx_tuning settings --
+the detector tile (pixels per lane: 8 x 8 or 8 x 4 pixel patches), the
+quadrature-node block that the kernels cull and stage as one unit (4 x 8,
+8 x 4, 2 x 16 or 16 x 2 nodes), persistent CTAs per SM of the forward and
+adjoint kernels and the adjoint's bands per reflection -- keeps the fastest,
+sets it process-wide, and caches the choice in a JSON file keyed by a
+signature of the workload (model count, detector sizes, reflection and atom
+counts, node grids), so a later run of the same workload starts from the
+tuned setting.  The search is coordinate-wise by default (one knob at a time,
+in the grid's order, the others at their best so far, starting from the
+library defaults; sum of the grid's lengths timings) or over the full product
+of the grid.  All timing is on the device with CUDA events.
 """
 from __future__ import annotations
 
@@ -19,6 +24,7 @@ from . import fdx
 
 DEFAULT_GRID = {
     "ppl_max": (2, 1),
+    "node_block": (0, 1, 2, 3),
     "fwd_ctas_per_sm": (4, 3),
     "adj_ctas_per_sm": (3, 2),
     "adj_bands": (64, 32, 128),
@@ -44,7 +50,33 @@ def _time_step(problems, datoms, targets, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def autotune_batch(problems, datoms, targets, grid=None, reps=1, cache_path=None, verbose=False):
+def _search(grid, measure, method):
+    """Best setting of `grid` under `measure(setting dict) -> ms`; returns
+    (best dict, {json setting: ms}).  Every setting is complete: the library
+    defaults overridden by the grid's knobs."""
+    names = list(grid)
+    timings = {}
+
+    def run(t):
+        key = json.dumps(t, sort_keys=True)
+        if key not in timings:
+            timings[key] = measure(t)
+        return timings[key]
+
+    if method == "grid":
+        best = min((dict(fdx.Tuning.DEFAULTS, **dict(zip(names, combo)))
+                    for combo in itertools.product(*(grid[k] for k in names))), key=run)
+        return best, timings
+    if method != "coordinate":
+        raise ValueError("method must be 'coordinate' or 'grid'")
+    best = dict(fdx.Tuning.DEFAULTS)
+    for name in names:
+        best = min((dict(best, **{name: v}) for v in grid[name]), key=run)
+    return best, timings
+
+
+def autotune_batch(problems, datoms, targets, grid=None, reps=1, cache_path=None, verbose=False,
+                   method="coordinate"):
     """Return (best tuning dict, {setting: ms}) and apply the best setting."""
     grid = grid or DEFAULT_GRID
     sig = signature(problems, datoms)
@@ -54,21 +86,18 @@ def autotune_batch(problems, datoms, targets, grid=None, reps=1, cache_path=None
         except (OSError, ValueError):
             cached = None
         if cached:
-            fdx.fdx_set_tuning(fdx.Tuning(**cached["best"]))
+            fdx.fdx_set_tuning(fdx.Tuning.of(**cached["best"]))
             return cached["best"], cached["timings"]
-    names = list(grid)
-    timings = {}
-    best, best_ms = None, float("inf")
-    for combo in itertools.product(*(grid[k] for k in names)):
-        t = dict(zip(names, combo))
-        fdx.fdx_set_tuning(fdx.Tuning(**t))
+
+    def measure(t):
+        fdx.fdx_set_tuning(fdx.Tuning.of(**t))
         ms = _time_step(problems, datoms, targets, reps)
-        timings[json.dumps(t, sort_keys=True)] = ms
         if verbose:
             print("tune", t, "%.2f ms" % ms, flush=True)
-        if ms < best_ms:
-            best, best_ms = t, ms
-    fdx.fdx_set_tuning(fdx.Tuning(**best))
+        return ms
+
+    best, timings = _search(grid, measure, method)
+    fdx.fdx_set_tuning(fdx.Tuning.of(**best))
     if cache_path:
         data = {}
         if os.path.exists(cache_path):

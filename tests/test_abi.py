@@ -162,15 +162,15 @@ def test_ring_workspace_holds_the_split_partials(fdx):
 
 
 def test_backward_and_loss_argument_checks(fdx):
-    """The adjoint covers the Hosemann lineshape only; missing inputs and short
-    workspaces are rejected on the host."""
+    """An unknown lineshape, missing inputs and short workspaces are rejected
+    on the host (the adjoint covers the three lineshapes)."""
     lib = fdx._bind_refine(fdx.lib())
     prob = _problem(fdx)
     a = fdx.Atoms()
     a.n_atoms, a.n_elem = 10, 4
     a.frac = a.B = a.elem = a.ff = 16
     g = fdx.Grads()
-    prob.br.lineshape = 0  # sinc: forward only
+    prob.br.lineshape = 3  # no such lineshape
     assert lib.fdx_pattern_backward(C.byref(prob), C.byref(a), C.c_void_p(16), C.c_void_p(16), C.byref(g),
                                     C.c_void_p(256), 1 << 30, None) == -1
     prob.br.lineshape = 1
