@@ -53,10 +53,10 @@ SFU_PER_EVAL = 6
 # compensated sum -- about 10 FP32 operations and 2-3 SFU operations.
 SF_OPS_PER_TERM = 10
 # DRAM bytes (read + written) of one forward pattern_kernel launch of this
-# step, from an ncu capture of it (dram__bytes_read.sum 93,552,640 +
-# dram__bytes_write.sum 8,631,552).  Valid only for the kernel as captured:
+# step, from an ncu capture of it (dram__bytes_read.sum 93,140,224 +
+# dram__bytes_write.sum 8,641,536).  Valid only for the kernel as captured:
 # None whenever the pattern kernel changes.
-PATTERN_DRAM_BYTES = 102184192
+PATTERN_DRAM_BYTES = 101781760
 
 
 def _peaks():
@@ -598,7 +598,8 @@ def main():
                    "l2_flush": "512 MiB write between steps, outside the per-step events",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "alu", "kernel": "pattern_kernel<Hosemann>", "achieved": rf["achieved"],
-                     "peak": rf["peak"], "unit": "Tops/s", "frac": rf["frac"], "traffic": PATTERN_DRAM_BYTES,
+                     "peak": rf["peak"], "unit": "Tops/s", "frac": rf["frac"],
+                     "traffic": None if args.region else PATTERN_DRAM_BYTES,
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "basis": "%d FP32 operations per in-support evaluation (the algorithm's count, an FMA is one); "
                               "peak = 148 SMs x 128 FP32 lanes x %.0f MHz, nominal (no measured FP32 peak); "
