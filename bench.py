@@ -456,6 +456,27 @@ def cpu_baseline(problem, hkl, M, t_sf, budget_s=12.0, seed=5):
             "sample_evals": evals, "sample_s": dt}, dt
 
 
+def cpu_one_thread(problem, hkl, M, n_px=8, seed=7):
+    """The same oracle on one host thread, on a fixed sample of n_px seeded
+    pixels over the whole detector (the scope asks for a 1-thread figure
+    beside the all-cores one; ~0.3e6 evals/s, so a few seconds here)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    nx, ny = problem.geom.n_x, problem.geom.n_y
+    pix = np.stack([rng.integers(0, nx, n_px), rng.integers(0, ny, n_px)], 1).astype(np.int32)
+    n_all = oracle.num_threads()
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        _, Ec = oracle.pattern(problem, hkl, M, pix)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(n_all)
+    evals = int(Ec[:, 0].sum())
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "sample_evals": evals, "sample_s": dt,
+            "sample": "%d seeded pixels over the whole %dx%d detector, full reflection list" % (n_px, nx, ny)}
+
+
 def run_reference(args):
     rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
@@ -635,6 +656,7 @@ def main():
     if not args.no_cpu_baseline:
         hkl, M, t_sf = _oracle_M(p)
         cb, _ = cpu_baseline(p, hkl, M, t_sf)
+        cb["one_thread"] = cpu_one_thread(p, hkl, M)
         line["cpu_baseline"] = cb
     print(json.dumps(line))
 
