@@ -82,7 +82,8 @@ def autotune_batch(problems, datoms, targets, grid=None, reps=1, cache_path=None
     sig = signature(problems, datoms)
     if cache_path and os.path.exists(cache_path):
         try:
-            cached = json.load(open(cache_path)).get(sig)
+            with open(cache_path) as f:
+                cached = json.load(f).get(sig)
         except (OSError, ValueError):
             cached = None
         if cached:
@@ -102,10 +103,12 @@ def autotune_batch(problems, datoms, targets, grid=None, reps=1, cache_path=None
         data = {}
         if os.path.exists(cache_path):
             try:
-                data = json.load(open(cache_path))
+                with open(cache_path) as f:
+                    data = json.load(f)
             except (OSError, ValueError):
                 data = {}
         data[sig] = {"best": best, "timings": timings}
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
-        json.dump(data, open(cache_path, "w"), indent=1, sort_keys=True)
+        with open(cache_path, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
     return best, timings
