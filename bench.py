@@ -518,6 +518,8 @@ def main():
     ap.add_argument("--no-scatter", action="store_true")
     ap.add_argument("--no-ring", action="store_true")
     ap.add_argument("--batch-models", type=int, default=256)
+    ap.add_argument("--refine-rois", default="256,512",
+                    help="central regions for the refine leg's FP32 vs plain FP64 comparison ('' for none)")
     ap.add_argument("--region", type=int, default=0,
                     help="cut the headline detector to its central N x N pixels (short profiling captures)")
     args = ap.parse_args()
@@ -646,7 +648,7 @@ def main():
     if not args.no_helix:
         line["helix"] = helix_measurements()
     if not args.no_refine:
-        line["refine"] = refine_measurements()
+        line["refine"] = refine_measurements(rois=tuple(int(x) for x in args.refine_rois.split(",") if x.strip()))
     if not args.no_scatter:
         line["scatter"] = scatter_measurements()
     if not args.no_ring:
