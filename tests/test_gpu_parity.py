@@ -329,3 +329,22 @@ def test_status_after_work(gpu):
     sim = gpu.Simulation(p)
     sim.forward()
     assert gpu.fdx_status() == 0
+
+
+@pytest.mark.parametrize("n_nodes", [1, 2, 7, 33, 130, 257, 512])
+def test_node_grid_sizes(gpu, orc, n_nodes):
+    """Node grids from one node to 512 per axis (ragged 4 x 8 culling blocks,
+    bounding boxes clipped by the grid's edge, many flushes of the staging
+    buffers) on a small ragged detector: whole-image parity and the in-support
+    count bracket."""
+    p = api_precision(W.small_helix())
+    p = replace(p, br=replace(p.br, n_nodes=n_nodes), geom=replace(p.geom, n_x=17, n_y=13))
+    hkl = orc.reflections(p.cell, p.d_min)
+    M = orc.intensities_M(p, hkl).astype(np.float32)
+    I, E = orc.pattern(p, hkl, M.astype(np.float64))
+    img, cnt = _gpu_pattern(gpu, p, hkl, M)
+    assert I.max() > 0
+    mr, l2 = parity(img.reshape(-1), I)
+    assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
+    c = cnt.reshape(-1)
+    assert np.all(c >= E[:, 1]) and np.all(c <= E[:, 2])
