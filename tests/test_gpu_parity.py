@@ -348,3 +348,25 @@ def test_node_grid_sizes(gpu, orc, n_nodes):
     assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
     c = cnt.reshape(-1)
     assert np.all(c >= E[:, 1]) and np.all(c <= E[:, 2])
+
+
+def test_pattern_several_models_one_call(gpu, orc):
+    """fdx_pattern over three different problems in one call (one workspace
+    of the largest model's size, reused in stream order) gives each model's
+    single-call image bit for bit."""
+    import torch
+    probs, imgs, refs, keep = [], [], [], []
+    for make in (W.small_helix, W.small_triclinic, W.small_sinc):
+        p = api_precision(make())
+        hkl = orc.reflections(p.cell, p.d_min)
+        M = orc.intensities_M(p, hkl).astype(np.float32)
+        refs.append(_gpu_pattern(gpu, p, hkl, M)[0])
+        hk = torch.as_tensor(np.ascontiguousarray(hkl, np.int32), device="cuda").reshape(-1, 3)
+        Mt = torch.as_tensor(M, device="cuda")
+        keep += [hk, Mt]
+        probs.append(gpu.make_problem(p.cell, p.br, p.geom, hk, Mt))
+        imgs.append(torch.full((p.geom.n_y, p.geom.n_x), float("nan"), dtype=torch.float32, device="cuda"))
+    gpu.fdx_pattern(probs, imgs)
+    _sync()
+    for img, ref in zip(imgs, refs):
+        assert np.array_equal(img.cpu().numpy(), ref)
