@@ -178,3 +178,48 @@ def test_library_slices_sum_to_unsharded_step():
     assert loss.item() == pytest.approx(loss_ref.item(), rel=1e-5)
     for got, want in zip(sums, ref):
         assert _rel(got.cpu().numpy(), want.cpu().numpy()) <= 1e-5
+
+
+@pytest.mark.gpu
+def test_nccl_all_reduce_path_one_rank():
+    """The sharded step's exchanges through NCCL on CUDA tensors (a one-rank
+    process group on this GPU: every all-reduce is the identity, so the step
+    must equal the same step with no exchange bit for bit).  Runs in a child
+    process so that the process group does not outlive the test."""
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    pr = ctx.Process(target=_nccl_worker, args=(_free_port(), q))
+    pr.start()
+    ok, msg = q.get(timeout=300)
+    pr.join(timeout=60)
+    assert pr.exitcode == 0 and ok, msg
+
+
+def _nccl_worker(port, q):
+    try:
+        import os
+        import torch.distributed as dist
+        os.environ["MASTER_ADDR"], os.environ["MASTER_PORT"] = "127.0.0.1", str(port)
+        os.environ.setdefault("NCCL_NVLS_ENABLE", "0")
+        torch.cuda.set_device(0)
+        dist.init_process_group("nccl", rank=0, world_size=1)
+        from paper_2608_23245_b300 import _build
+        _build.build()
+        p = api_precision(W.small_helix())
+        be = sharded.FdxBackend(p, None)
+        img0 = be.partial_image(0, be.hkl.shape[0]).clone()
+        target = (img0 * 0.8 + 0.01).contiguous()
+        be = sharded.FdxBackend(p, target)
+        n = be.hkl.shape[0]
+        # the backend returns its own buffers: keep copies of the first step's results
+        plain = [x.clone() if torch.is_tensor(x) else x for x in sharded.ShardedRefineStep(be, n, 0, 1)()]
+        viaccl = sharded.ShardedRefineStep(be, n, 0, 1, reduce=sharded._all_reduce_sum)()
+        torch.cuda.synchronize()
+        same = all(torch.equal(a, b) if torch.is_tensor(a) else a == b for a, b in zip(plain, viaccl))
+        dist.destroy_process_group()
+        q.put((bool(same) and float(plain[0].max()) > 0, "nccl step differs" if not same else ""))
+    except Exception as e:  # report to the parent instead of hanging it
+        q.put((False, repr(e)))
