@@ -175,34 +175,22 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
     }
 }
 
-__device__ __forceinline__ int batch_model(const long long *prefix, int n_models, long long item) {
-    int lo = 0, hi = n_models - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Persistent adjoint over many models: each warp takes (model, reflection,
-// band) items from an atomic counter; items are independent, so the order in
-// which they are taken does not change any result.
+// Persistent adjoint over the models of one tile shape: each warp takes
+// (model, reflection, band) items from an atomic counter; items are
+// independent, so the order in which they are taken does not change any
+// result.  Compiled for one PPL, like the per-model kernel.
+template <int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(BatchAdjParams B) {
     FDX_ADJ_SMEM
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (;;) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(B.counter, 1u);
-        const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
-        if (item >= B.total_items) break;
-        const int m = batch_model(B.item_prefix, B.n_models, item);
-        const AdjParams &A = B.models[m];
-        if (A.P.ppl == 2)
-            adjoint_item<FDX_LINESHAPE_HOSEMANN, 2>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp],
-                                                    s_sc2[warp], s_rec[warp], lane);
-        else
-            adjoint_item<FDX_LINESHAPE_HOSEMANN, 1>(A, item - B.item_prefix[m], s_nodes[warp], s_dn[warp], s_sc[warp],
-                                                    s_sc2[warp], s_rec[warp], lane);
+        const long long item = B.item0 + (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
+        if (item >= B.item_end) break;
+        const int j = item_position(B.item_prefix, B.pos0, B.n_pos, item);
+        adjoint_item<FDX_LINESHAPE_HOSEMANN, PPL>(B.models[B.item_model[j]], item - B.item_prefix[j], s_nodes[warp],
+                                                  s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
     }
 }
 
@@ -457,8 +445,11 @@ cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s) {
-    adjoint_batch_kernel<<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int ppl, int n_ctas, cudaStream_t s) {
+    if (ppl == 2)
+        adjoint_batch_kernel<2><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
+    else
+        adjoint_batch_kernel<1><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
     return cudaGetLastError();
 }
 

@@ -27,11 +27,14 @@ struct AdjParams {
     double alen[3], L[3], g[3], Bax[3];
 };
 
+// Adjoint over the models of one tile shape (adjoint_batch_kernel<PPL>), with
+// position tables as for the forward ((reflection, band) items).
 struct BatchAdjParams {
-    const AdjParams *models;       // [n_models] device
-    const long long *item_prefix;  // [n_models] exclusive prefix of (reflection, band) items
-    long long total_items;
-    int n_models;
+    const AdjParams *models;       // [n_models] device, by model index
+    const long long *item_prefix;  // [n_models] by position: the model's first item
+    const int *item_model;         // [n_models] by position: the model index
+    int pos0, n_pos;
+    long long item0, item_end;
     unsigned *counter;             // zeroed before the launch
 };
 
@@ -76,7 +79,7 @@ struct Plain64Params {
 
 cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s);
 cudaError_t launch_bounds_only(AdjParams &A, cudaStream_t s);
-cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s);
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int ppl, int n_ctas, cudaStream_t s);
 cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s);
 cudaError_t launch_globals_only(AdjParams &A, cudaStream_t s);
 cudaError_t launch_plain64_forward(Plain64Params &p, cudaStream_t s);

@@ -132,6 +132,18 @@ void cross3(const double *x, const double *y, double *z) {
     z[2] = x[0] * y[1] - x[1] * y[0];
 }
 
+// Two pixels per lane (8 x 8 warp patches) when the patch spans at most half
+// a lattice period along every cell axis: pitch in S (largest at the beam
+// centre) x 8 sqrt 2 x max |a_i| <= 0.5; otherwise one (8 x 4).
+int pattern_ppl(const fdx_problem *p) {
+    double A[9], As[9];
+    cell_basis(p->cell, A, As);
+    const double pitch = p->geom.pixel / (p->geom.wavelength * p->geom.distance);
+    double amax = 0.0;
+    for (int i = 0; i < 3; ++i) amax = fmax(amax, sqrt(A[3 * i] * A[3 * i] + A[3 * i + 1] * A[3 * i + 1] + A[3 * i + 2] * A[3 * i + 2]));
+    return (pitch * 8.0 * sqrt(2.0) * amax <= 0.5 && tuning().ppl_max >= 2) ? 2 : 1;
+}
+
 // Queue the set-up kernels (pixel geometry, node table, reflection records)
 // for one problem and fill the pattern kernel's parameters.
 int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams &P, bool with_dnodes,
@@ -185,15 +197,7 @@ int setup_pattern(const fdx_problem *p, char *ws, cudaStream_t st, PatternParams
     P.inv_h = (float)(p->br.n_nodes / (2.0 * p->br.T));
     for (int i = 0; i < 3; ++i) P.AZ[i] = (float)(A[3 * i] * nh[0] + A[3 * i + 1] * nh[1] + A[3 * i + 2] * nh[2]);
     P.delta_L = p->geom.delta_L;
-    // Two pixels per lane (8 x 8 warp patches) when the patch spans at most half
-    // a lattice period along every cell axis: pitch in S (largest at the beam
-    // centre) x 8 sqrt 2 x max |a_i| <= 0.5; otherwise one (8 x 4).
-    {
-        const double pitch = p->geom.pixel / (p->geom.wavelength * p->geom.distance);
-        double amax = 0.0;
-        for (int q = 0; q < 3; ++q) amax = fmax(amax, rp.alen[q]);
-        P.ppl = (pitch * 8.0 * sqrt(2.0) * amax <= 0.5 && tuning().ppl_max >= 2) ? 2 : 1;
-    }
+    P.ppl = pattern_ppl(p);
     // node blocks of the culling: 2^blk_lr rows x 2^blk_lc columns, 32 nodes
     {
         static const int lr[4] = {2, 3, 1, 4};
@@ -274,18 +278,23 @@ BackLayout back_layout(const fdx_problem *p, int n_atoms, int n_elem) {
 
 // Writes one model's parameter blocks and item prefixes into the batch tables
 // (a kernel, so that the whole batch step can be captured in a CUDA graph).
+// One model's parameter blocks (at its index) and its entries of the
+// position tables (at its position; models are ordered by tile shape).
 __global__ void batch_write_params(PatternParams *fdst, const PatternParams P, AdjParams *adst, const AdjParams A,
-                                   long long *fpre, long long fp, long long *apre, long long ap) {
+                                   long long *fpre, long long fp, long long *apre, long long ap, int *fmod, int *amod,
+                                   int m) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         *fdst = P;
         *adst = A;
         *fpre = fp;
         *apre = ap;
+        *fmod = m;
+        *amod = m;
     }
 }
 
 struct BatchLayout {
-    size_t fwd_tab, adj_tab, fpre, apre, counters, head;
+    size_t fwd_tab, adj_tab, fpre, apre, fmod, amod, counters, head;
     std::vector<size_t> region, back, sf, gI, loss;
     size_t total;
 };
@@ -297,7 +306,9 @@ BatchLayout batch_layout(int n, const fdx_problem *const *probs, const fdx_atoms
     L.adj_tab = off, off += align_up(sizeof(AdjParams) * n);
     L.fpre = off, off += align_up(sizeof(long long) * n);
     L.apre = off, off += align_up(sizeof(long long) * n);
-    L.counters = off, off += align_up(sizeof(unsigned) * 2);
+    L.fmod = off, off += align_up(sizeof(int) * n);
+    L.amod = off, off += align_up(sizeof(int) * n);
+    L.counters = off, off += align_up(sizeof(unsigned) * 4);
     L.head = off;
     for (int m = 0; m < n; ++m) {
         const fdx_problem *p = probs[m];
@@ -468,10 +479,33 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
     if (cudaGetDevice(&dev) != cudaSuccess) return FDX_ERR_CUDA;
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     unsigned *counters = reinterpret_cast<unsigned *>(ws + L.counters);
-    if (cudaMemsetAsync(counters, 0, 2 * sizeof(unsigned), st) != cudaSuccess) return FDX_ERR_CUDA;
+    if (cudaMemsetAsync(counters, 0, 4 * sizeof(unsigned), st) != cudaSuccess) return FDX_ERR_CUDA;
+
+    // Models ordered by tile shape (two pixels per lane first): each shape's
+    // forward and adjoint run as persistent launches of their own, each
+    // compiled for that shape.  Item counts and offsets per model, on the host.
+    std::vector<int> ppl(n_models), pos(n_models);
+    std::vector<long long> fitems(n_models), aitems(n_models), fstart(n_models), astart(n_models);
+    int n_pos2 = 0;
+    for (int m = 0; m < n_models; ++m) {
+        fdx_problem pr = *probs[m];
+        pr.M = M[m];
+        ppl[m] = pattern_ppl(&pr);
+        fitems[m] = (long long)((pr.geom.n_x + 15) / 16) * ((pr.geom.n_y + 8 * ppl[m] - 1) / (8 * ppl[m]));
+        aitems[m] = (long long)pr.n_refl * back_layout(&pr, atoms[m]->n_atoms, atoms[m]->n_elem).n_bands;
+        n_pos2 += ppl[m] == 2;
+    }
+    long long f_split = 0, a_split = 0, fsum = 0, asum = 0;  // items of the two-pixel models; totals
+    for (int cls = 2, next = 0; cls >= 1; --cls) {
+        if (cls == 1) f_split = fsum, a_split = asum;
+        for (int m = 0; m < n_models; ++m) {
+            if (ppl[m] != cls) continue;
+            pos[m] = next++, fstart[m] = fsum, astart[m] = asum;
+            fsum += fitems[m], asum += aitems[m];
+        }
+    }
 
     std::vector<AdjParams> adj(n_models);
-    long long fsum = 0, asum = 0;
     for (int m = 0; m < n_models; ++m) {
         fdx_problem pr = *probs[m];
         pr.M = M[m];
@@ -527,24 +561,30 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
         A.dglobal = targets ? grads[m]->dglobal : nullptr;
         A.hkl = pr.hkl, A.F = F[m], A.ff = a->ff, A.n_elem = a->n_elem, A.intensity_model = pr.br.intensity_model;
         A.lineshape = pr.br.lineshape;
-        const int ppl = P.ppl;
-        const long long ftiles = (long long)((pr.geom.n_x + 15) / 16) * ((pr.geom.n_y + 8 * ppl - 1) / (8 * ppl));
-        const long long aitems = (long long)pr.n_refl * B.n_bands;
+        if (P.ppl != ppl[m] || B.n_bands * (long long)pr.n_refl != aitems[m]) return FDX_ERR_ARG;  // cannot happen
+        const int j = pos[m];
         batch_write_params<<<1, 32, 0, st>>>(reinterpret_cast<PatternParams *>(ws + L.fwd_tab) + m, P,
                                              reinterpret_cast<AdjParams *>(ws + L.adj_tab) + m, A,
-                                             reinterpret_cast<long long *>(ws + L.fpre) + m, fsum,
-                                             reinterpret_cast<long long *>(ws + L.apre) + m, asum);
+                                             reinterpret_cast<long long *>(ws + L.fpre) + j, fstart[m],
+                                             reinterpret_cast<long long *>(ws + L.apre) + j, astart[m],
+                                             reinterpret_cast<int *>(ws + L.fmod) + j,
+                                             reinterpret_cast<int *>(ws + L.amod) + j, m);
         if (cudaGetLastError() != cudaSuccess) return FDX_ERR_CUDA;
-        fsum += ftiles;
-        asum += aitems;
     }
-    // one persistent forward launch over all models
-    BatchFwdParams BF;
-    BF.models = reinterpret_cast<const PatternParams *>(ws + L.fwd_tab);
-    BF.item_prefix = reinterpret_cast<const long long *>(ws + L.fpre);
-    BF.total_items = fsum, BF.n_models = n_models, BF.counter = counters;
+    // one persistent forward launch per tile shape over its models
     const fdx_tuning tu = tuning();
-    if (launch_pattern_batch(BF, n_sm * tu.fwd_ctas_per_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    for (int cls = 2; cls >= 1; --cls) {
+        BatchFwdParams BF;
+        BF.models = reinterpret_cast<const PatternParams *>(ws + L.fwd_tab);
+        BF.item_prefix = reinterpret_cast<const long long *>(ws + L.fpre);
+        BF.item_model = reinterpret_cast<const int *>(ws + L.fmod);
+        BF.pos0 = cls == 2 ? 0 : n_pos2, BF.n_pos = cls == 2 ? n_pos2 : n_models - n_pos2;
+        BF.item0 = cls == 2 ? 0 : f_split, BF.item_end = cls == 2 ? f_split : fsum;
+        BF.counter = counters + (cls == 2 ? 0 : 1);
+        if (BF.n_pos > 0 && BF.item_end > BF.item0 &&
+            launch_pattern_batch(BF, cls, n_sm * tu.fwd_ctas_per_sm, st) != cudaSuccess)
+            return FDX_ERR_CUDA;
+    }
     if (!targets) return FDX_OK;
 
     for (int m = 0; m < n_models; ++m) {
@@ -557,12 +597,19 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
         if (launch_loss(lp, st) != cudaSuccess) return FDX_ERR_CUDA;
         if (launch_bounds_only(adj[m], st) != cudaSuccess) return FDX_ERR_CUDA;
     }
-    // one persistent adjoint launch over all models
-    BatchAdjParams BA;
-    BA.models = reinterpret_cast<const AdjParams *>(ws + L.adj_tab);
-    BA.item_prefix = reinterpret_cast<const long long *>(ws + L.apre);
-    BA.total_items = asum, BA.n_models = n_models, BA.counter = counters + 1;
-    if (asum > 0 && launch_adjoint_batch(BA, n_sm * tu.adj_ctas_per_sm, st) != cudaSuccess) return FDX_ERR_CUDA;
+    // one persistent adjoint launch per tile shape over its models
+    for (int cls = 2; cls >= 1; --cls) {
+        BatchAdjParams BA;
+        BA.models = reinterpret_cast<const AdjParams *>(ws + L.adj_tab);
+        BA.item_prefix = reinterpret_cast<const long long *>(ws + L.apre);
+        BA.item_model = reinterpret_cast<const int *>(ws + L.amod);
+        BA.pos0 = cls == 2 ? 0 : n_pos2, BA.n_pos = cls == 2 ? n_pos2 : n_models - n_pos2;
+        BA.item0 = cls == 2 ? 0 : a_split, BA.item_end = cls == 2 ? a_split : asum;
+        BA.counter = counters + (cls == 2 ? 2 : 3);
+        if (BA.n_pos > 0 && BA.item_end > BA.item0 &&
+            launch_adjoint_batch(BA, cls, n_sm * tu.adj_ctas_per_sm, st) != cudaSuccess)
+            return FDX_ERR_CUDA;
+    }
     for (int m = 0; m < n_models; ++m) {
         const fdx_problem *pr = probs[m];
         const fdx_atoms *a = atoms[m];

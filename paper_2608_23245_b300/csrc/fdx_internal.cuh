@@ -137,15 +137,30 @@ struct PatternParams {
     int32_t *counts;      // [ny][nx] (count mode)
 };
 
-// Forward over many models (pattern_batch_kernel): per-model parameters in
-// device memory, item prefix (CTA tiles per model), atomic item counter.
+// Forward over the models of one tile shape (pattern_batch_kernel<LS, PPL>):
+// per-model parameters in device memory by model index; the models are
+// ordered by tile shape in the position tables, and those of this launch take
+// positions [pos0, pos0 + n_pos) and items [item0, item_end) (CTA tiles).
 struct BatchFwdParams {
-    const PatternParams *models;  // [n_models] device
-    const long long *item_prefix; // [n_models] exclusive prefix of items
-    long long total_items;
-    int n_models;
+    const PatternParams *models;  // [n_models] device, by model index
+    const long long *item_prefix; // [n_models] by position: the model's first item
+    const int *item_model;        // [n_models] by position: the model index
+    int pos0, n_pos;
+    long long item0, item_end;
     unsigned *counter;            // zeroed before the launch
 };
+
+// First item of position j's model is item_prefix[j]; the position of `item`
+// among [pos0, pos0 + n_pos): the last j with item_prefix[j] <= item (models
+// without items share their successor's prefix and are passed over).
+__device__ __forceinline__ int item_position(const long long *prefix, int pos0, int n_pos, long long item) {
+    int lo = pos0, hi = pos0 + n_pos - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 struct ReflSetupParams {
     double A[9], As[9];   // real basis rows a, b, c and reciprocal rows a*, b*, c*
@@ -208,7 +223,7 @@ cudaError_t launch_pixel_geometry(const PixelParams &p, cudaStream_t s);
 cudaError_t launch_nodes(const NodeParams &p, const WeidemanCoeffs &wc, cudaStream_t s);
 cudaError_t launch_refl_setup(const ReflSetupParams &p, cudaStream_t s);
 cudaError_t launch_pattern(const PatternParams &p, int lineshape, bool count_mode, cudaStream_t s);
-cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s);
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int ppl, int n_ctas, cudaStream_t s);
 
 struct SFParams {
     int n_atoms, n_elem, n_refl, n_split;

@@ -135,21 +135,12 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_kernel(PatternPara
     pattern_warp<LS, MODE, PPL>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
 }
 
-// Model of a flattened item index: the last m with prefix[m] <= item.
-__device__ __forceinline__ int item_model(const long long *prefix, int n_models, long long item) {
-    int lo = 0, hi = n_models - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (prefix[mid] <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Persistent forward over many models: CTAs take (model, tile) items from an
-// atomic counter until the items of all models are done.  Every item is
-// computed by one CTA start to finish, so the result does not depend on the
-// order in which items are taken.
-template <int LS>
+// Persistent forward over the models of one tile shape: CTAs take (model,
+// tile) items from an atomic counter until the items of all of them are done.
+// Every item is computed by one CTA start to finish, so the result does not
+// depend on the order in which items are taken; compiled for one PPL, like
+// the per-model kernel.
+template <int LS, int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(BatchFwdParams B) {
     extern __shared__ float4 dsm[];
     __shared__ long long s_item;
@@ -157,22 +148,18 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(Batch
     const PatternSmem<LS, MODE_FWD> sm(dsm, warp);
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(B.counter, 1u);
+        if (threadIdx.x == 0) s_item = B.item0 + (long long)atomicAdd(B.counter, 1u);
         __syncthreads();
         const long long item = s_item;
-        if (item >= B.total_items) break;
-        const int m = item_model(B.item_prefix, B.n_models, item);
-        const PatternParams &P = B.models[m];
-        const int t = (int)(item - B.item_prefix[m]);
-        const int ppl = P.ppl;
+        if (item >= B.item_end) break;
+        const int j = item_position(B.item_prefix, B.pos0, B.n_pos, item);
+        const PatternParams &P = B.models[B.item_model[j]];
+        const int t = (int)(item - B.item_prefix[j]);
         const int tiles_x = (P.nx + 15) / 16;
         const int bx = t % tiles_x, by = t / tiles_x;
-        const int px0 = bx * 16 + (warp & 1) * 8, py0 = by * (8 * ppl) + (warp >> 1) * (4 * ppl);
+        const int px0 = bx * 16 + (warp & 1) * 8, py0 = by * (8 * PPL) + (warp >> 1) * (4 * PPL);
         if (px0 >= P.nx || py0 >= P.ny) continue;
-        if (ppl == 2)
-            pattern_warp<LS, MODE_FWD, 2>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
-        else
-            pattern_warp<LS, MODE_FWD, 1>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
+        pattern_warp<LS, MODE_FWD, PPL>(P, px0, py0, sm.nodes, sm.sc, sm.sc2, sm.rec, sm.lst, lane);
     }
 }
 
@@ -183,12 +170,17 @@ static cudaError_t allow_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launch_pattern_batch(const BatchFwdParams &B, int n_ctas, cudaStream_t s) {
+template <int PPL>
+static cudaError_t launch_pattern_batch_ppl(const BatchFwdParams &B, int n_ctas, cudaStream_t s) {
     constexpr size_t bytes = PatternSmem<FDX_LINESHAPE_HOSEMANN, MODE_FWD>::BYTES;
-    cudaError_t e = allow_smem(pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN>, bytes);
+    cudaError_t e = allow_smem(pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN, PPL>, bytes);
     if (e != cudaSuccess) return e;
-    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN><<<n_ctas, PAIR_WARPS * 32, bytes, s>>>(B);
+    pattern_batch_kernel<FDX_LINESHAPE_HOSEMANN, PPL><<<n_ctas, PAIR_WARPS * 32, bytes, s>>>(B);
     return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_batch(const BatchFwdParams &B, int ppl, int n_ctas, cudaStream_t s) {
+    return ppl == 2 ? launch_pattern_batch_ppl<2>(B, n_ctas, s) : launch_pattern_batch_ppl<1>(B, n_ctas, s);
 }
 
 template <int LS, int PPL>

@@ -116,3 +116,32 @@ def test_batch_graph_replay(gpu):
     ref = _per_model(gpu, sims[:1], tims[:1])
     assert torch.equal(step.images[0], ref[0]["image"])
     assert torch.equal(step.dfrac[0], ref[0]["dfrac"])
+
+
+def test_batch_mixed_tile_shapes(gpu):
+    """Models of both tile shapes in one batch (the reduced models take one
+    pixel per lane; the helix with 0.2 mm pixels two): one persistent launch
+    per shape and kernel, each model still bitwise equal to its per-model
+    entry points."""
+    import torch
+    from dataclasses import replace
+    h = W.small_helix()
+    fine = replace(h, geom=replace(h.geom, pixel=0.2))
+    models = [api_precision(p) for p in W.small_batch(2)] + [api_precision(fine)] + \
+             [api_precision(W.small_batch(3)[2])]
+    targets = [api_precision(W.config4_target(p, m)) if m != 2 else api_precision(replace(
+        p, br=replace(p.br, g=(0.025, 0.025, 0.0)))) for m, p in enumerate(models)]
+    sims = [gpu.Simulation(p) for p in models]
+    tims = [gpu.Simulation(t).forward().clone() for t in targets]
+    probs = [s.prob for s in sims]
+    ref = _per_model(gpu, sims, tims)
+    step = gpu.BatchStep(probs, [s.atoms for s in sims], targets=tims)
+    step()
+    torch.cuda.synchronize()
+    for m in range(len(models)):
+        assert torch.equal(step.images[m], ref[m]["image"]), m
+        assert step.losses[m].item() == ref[m]["loss"].item(), m
+        assert torch.equal(step.dfrac[m], ref[m]["dfrac"]), m
+        assert torch.equal(step.dB[m], ref[m]["dB"]), m
+        assert torch.equal(step.dglobal[m], ref[m]["dg"]), m
+        assert float(step.images[m].max()) > 0

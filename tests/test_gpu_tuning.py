@@ -47,7 +47,16 @@ def _forward(gpu, p, hkl, M):
     return img.cpu().numpy().reshape(-1), cnt.cpu().numpy().reshape(-1)
 
 
-@pytest.mark.parametrize("make", [W.small_helix, W.small_triclinic, W.small_tilted, W.small_sinc])
+def _fine_helix():
+    """The reduced helix with 0.2 mm pixels: its 8 x 8 patches span less than
+    half a lattice period, so the kernels take two pixels per lane (the other
+    reduced workloads take one)."""
+    from dataclasses import replace
+    p = W.small_helix()
+    return replace(p, geom=replace(p.geom, pixel=0.2))
+
+
+@pytest.mark.parametrize("make", [W.small_helix, W.small_triclinic, W.small_tilted, W.small_sinc, _fine_helix])
 def test_node_block_shapes_forward(gpu, orc, tuned, make):
     p = api_precision(make())
     hkl = orc.reflections(p.cell, p.d_min)
@@ -74,13 +83,14 @@ def _close(got, ref, what):
     assert err <= ADJ_TOL and l2 <= ADJ_TOL, (what, err, l2)
 
 
+@pytest.mark.parametrize("make", [W.small_helix, _fine_helix])
 @pytest.mark.parametrize("nb", [1, 2, 3])
-def test_node_block_shapes_adjoint(gpu, orc, tuned, nb):
+def test_node_block_shapes_adjoint(gpu, orc, tuned, nb, make):
     """The adjoint of the helix model for a seeded upstream gradient (the
     model's own loss gradient against a perturbed target, so the sums are
     not dominated by cancellation) under each non-default block shape."""
     import torch
-    p = api_precision(W.small_helix())
+    p = api_precision(make())
     tuned(node_block=nb)
     sim = gpu.Simulation(p)
     img = sim.forward()
