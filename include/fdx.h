@@ -331,8 +331,9 @@ size_t fdx_batch_workspace_size(int32_t n_models, const fdx_problem *const *prob
  * F[m], M[m]; probs[m]->M is ignored), the pattern (images[m]), and, when
  * targets is not NULL, the loss of fdx_loss (losses[m], masks optional) and
  * the adjoint of fdx_pattern_backward (grads[m]).  The pattern of all models
- * runs in one persistent launch and the adjoint of all models in another;
- * both take (model, tile) or (model, reflection, band) items from an atomic
+ * runs in one persistent launch per tile shape (pixels per lane; at most two)
+ * and the adjoint likewise; they take (model, tile) or (model, reflection,
+ * band) items from an atomic
  * counter in the workspace, and each item is computed by one CTA or warp from
  * start to finish, so results do not depend on the order items are taken.
  * Every operation is a kernel launch or an asynchronous memset on `stream`,
