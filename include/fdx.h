@@ -357,11 +357,11 @@ typedef struct fdx_tuning {
     int32_t adj_bands;       /* detector bands per reflection in the adjoint work items, 1..256 */
     int32_t node_block;      /* 0..3: shape of the quadrature-node blocks that the pattern-family kernels
                                 cull and stage as one unit, rows x columns of the node grid:
-                                0 = 4 x 8, 1 = 8 x 4, 2 = 2 x 16, 3 = 16 x 2.  Changes the order of the
+                                0 = 4 x 8, 1 = 8 x 4 (default), 2 = 2 x 16, 3 = 16 x 2.  Changes the order of the
                                 node sums (results agree to rounding), not the set of terms */
 } fdx_tuning;
 
-/* Set the tuning (NULL restores the defaults 2, 4, 3, 64, 0).  Workspace sizes
+/* Set the tuning (NULL restores the defaults 2, 4, 3, 64, 1).  Workspace sizes
  * depend on adj_bands: query them after setting. */
 int fdx_set_tuning(const fdx_tuning *t);
 int fdx_get_tuning(fdx_tuning *t);

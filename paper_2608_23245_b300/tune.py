@@ -24,7 +24,7 @@ from . import fdx
 
 DEFAULT_GRID = {
     "ppl_max": (2, 1),
-    "node_block": (0, 1, 2, 3),
+    "node_block": (1, 0, 2, 3),
     "fwd_ctas_per_sm": (4, 3),
     "adj_ctas_per_sm": (3, 2),
     "adj_bands": (64, 32, 128),

@@ -333,7 +333,7 @@ def test_status_after_work(gpu):
 
 @pytest.mark.parametrize("n_nodes", [1, 2, 7, 33, 130, 257, 512])
 def test_node_grid_sizes(gpu, orc, n_nodes):
-    """Node grids from one node to 512 per axis (ragged 4 x 8 culling blocks,
+    """Node grids from one node to 512 per axis (ragged culling blocks,
     bounding boxes clipped by the grid's edge, many flushes of the staging
     buffers) on a small ragged detector: whole-image parity and the in-support
     count bracket."""
