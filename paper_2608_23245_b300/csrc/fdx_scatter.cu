@@ -16,7 +16,8 @@
 // Work decomposition: a warp evaluates 32 consecutive samples of one
 // reflection (one sample per lane) with the same pair evaluation as the
 // gather form (eval_core: block culling, live-node staging, packed walk); the
-// query points are the samples, referred to a centre sample of the warp.  The
+// query points are the samples, referred to the warp's sample nearest their
+// centroid.  The
 // per-sample Ewald rotation runs in float-float (one lane per sample) on seven
 // projections of S, with Newton-refined reciprocals; the weights are FP32.
 // The hits are added with FP64 atomics into an FP64 image that a last kernel
@@ -180,7 +181,24 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     const ff u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
     const ff u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
     const ff u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
-    const int rl = min(26, n_valid - 1);  // a central sample of the 2 x 4 x 4 brick
+    // reference: the valid sample nearest the centroid of the warp's samples
+    // (any order of the samples is correct; neighbours in a warp cull best)
+    float cx = valid ? u0.hi : 0.0f, cy = valid ? u1.hi : 0.0f, cz = valid ? u2.hi : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cx += __shfl_xor_sync(FDX_FULL_MASK, cx, o);
+        cy += __shfl_xor_sync(FDX_FULL_MASK, cy, o);
+        cz += __shfl_xor_sync(FDX_FULL_MASK, cz, o);
+    }
+    const float inv_n = 1.0f / (float)n_valid;
+    cx *= inv_n, cy *= inv_n, cz *= inv_n;
+    const float dx = u0.hi - cx, dy = u1.hi - cy, dz = u2.hi - cz;
+    // squared distances are >= 0, so their bit patterns order like the values;
+    // the low 5 bits carry the lane (ties and near-ties go to either lane)
+    unsigned key = valid ? ((__float_as_uint(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) & ~31u) | (unsigned)lane) : 0xffffffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(FDX_FULL_MASK, key, o));
+    const int rl = (int)(key & 31u);
     const ff v0 = {__shfl_sync(FDX_FULL_MASK, u0.hi, rl), __shfl_sync(FDX_FULL_MASK, u0.lo, rl)};
     const ff v1 = {__shfl_sync(FDX_FULL_MASK, u1.hi, rl), __shfl_sync(FDX_FULL_MASK, u1.lo, rl)};
     const ff v2 = {__shfl_sync(FDX_FULL_MASK, u2.hi, rl), __shfl_sync(FDX_FULL_MASK, u2.lo, rl)};

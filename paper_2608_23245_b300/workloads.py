@@ -371,24 +371,33 @@ def small_tilted() -> Problem:
     return tilted(small_helix(), 20.0)
 
 
+def sample_brick(n_r: int, n_1: int, n_2: int):
+    """Brick of 32 grid cells in which the scatter samples are ordered (a warp
+    of the scatter kernel takes one brick): 4 x 4 x 2 (radial x angular x
+    angular), the fastest shape measured, or 2 x 4 x 4 when n_r is not a
+    multiple of 4."""
+    brick = (4, 4, 2) if n_r % 4 == 0 and n_2 % 2 == 0 else (2, 4, 4)
+    if n_r % brick[0] or n_1 % brick[1] or n_2 % brick[2]:
+        raise ValueError("grid must be a multiple of 4 x 4 x 2 or of 2 x 4 x 4")
+    return brick
+
+
 def scatter_samples(n_r: int, n_1: int, n_2: int, seed: int = SEED_BASE + 50) -> np.ndarray:
     """Seeded stratified samples for the scatter form: one jittered point in
     each cell of an n_r x n_1 x n_2 grid on [-1, 1]^3, float32 rows (x_r, x_1,
-    x_2, q) with q = 8 / (n_r n_1 n_2), ordered in bricks of 2 x 4 x 4 cells so
-    that every 32 consecutive samples are neighbours.  n_r even, n_1 and n_2
-    multiples of 4."""
-    if n_r % 2 or n_1 % 4 or n_2 % 4:
-        raise ValueError("grid must be a multiple of 2 x 4 x 4")
+    x_2, q) with q = 8 / (n_r n_1 n_2), ordered in bricks of 32 cells (see
+    `sample_brick`) so that every 32 consecutive samples are neighbours."""
+    b_r, b_1, b_2 = sample_brick(n_r, n_1, n_2)
     rng = np.random.Generator(np.random.PCG64(seed))
     jit = rng.uniform(0.0, 1.0, size=(n_r, n_1, n_2, 3))
     out = np.empty((n_r * n_1 * n_2, 4), dtype=np.float32)
     k = 0
-    for br in range(0, n_r, 2):
-        for b1 in range(0, n_1, 4):
-            for b2 in range(0, n_2, 4):
-                for ir in range(br, br + 2):
-                    for i1 in range(b1, b1 + 4):
-                        for i2 in range(b2, b2 + 4):
+    for br in range(0, n_r, b_r):
+        for b1 in range(0, n_1, b_1):
+            for b2 in range(0, n_2, b_2):
+                for ir in range(br, br + b_r):
+                    for i1 in range(b1, b1 + b_1):
+                        for i2 in range(b2, b2 + b_2):
                             j = jit[ir, i1, i2]
                             out[k] = (-1.0 + 2.0 * (ir + j[0]) / n_r, -1.0 + 2.0 * (i1 + j[1]) / n_1,
                                       -1.0 + 2.0 * (i2 + j[2]) / n_2, 8.0 / (n_r * n_1 * n_2))
@@ -411,9 +420,8 @@ def scatter_samples_cauchy(n_r: int, n_1: int, n_2: int, scale: float, extent: f
     extent > 1 reaches past the node patch by (extent - 1) T.  The weight
     q = 1 / (n pdf(x_r) pdf(x_1) pdf(x_2)) makes sum q f(x) an unbiased
     estimate of the integral of f over [-1, 1] x [-extent, extent]^2.  Rows
-    (x_r, x_1, x_2, q) as float32, in 2 x 4 x 4 bricks like scatter_samples."""
-    if n_r % 2 or n_1 % 4 or n_2 % 4:
-        raise ValueError("grid must be a multiple of 2 x 4 x 4")
+    (x_r, x_1, x_2, q) as float32, in bricks like scatter_samples."""
+    b_r, b_1, b_2 = sample_brick(n_r, n_1, n_2)
     if not (scale > 0 and extent > 0):
         raise ValueError("scale and extent must be positive")
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -422,12 +430,12 @@ def scatter_samples_cauchy(n_r: int, n_1: int, n_2: int, scale: float, extent: f
     n = n_r * n_1 * n_2
     out = np.empty((n, 4), dtype=np.float32)
     k = 0
-    for br in range(0, n_r, 2):
-        for b1 in range(0, n_1, 4):
-            for b2 in range(0, n_2, 4):
-                for ir in range(br, br + 2):
-                    for i1 in range(b1, b1 + 4):
-                        for i2 in range(b2, b2 + 4):
+    for br in range(0, n_r, b_r):
+        for b1 in range(0, n_1, b_1):
+            for b2 in range(0, n_2, b_2):
+                for ir in range(br, br + b_r):
+                    for i1 in range(b1, b1 + b_1):
+                        for i2 in range(b2, b2 + b_2):
                             j = jit[ir, i1, i2]
                             xr = -1.0 + 2.0 * (ir + j[0]) / n_r
                             th1 = th_max * (2.0 * (i1 + j[1]) / n_1 - 1.0)
