@@ -453,3 +453,45 @@ def test_pixel_roundtrip_paper_forward_solver(orc, tilt):
             u, v = r @ u_hat, r @ v_hat
             hits.append((u / p.geom.pixel + p.geom.n_x / 2 - 0.5, v / p.geom.pixel + p.geom.n_y / 2 - 0.5))
         assert any(abs(x - i) < 1e-7 and abs(y - j) < 1e-7 for (x, y) in hits), (i, j, hits)
+
+
+@pytest.mark.parametrize("delta_L", [1e-5, 1e-2, 1e2])
+def test_lorentz_factor(orc, delta_L):
+    """Eq. lorentz through the oracle's own composition: for one reflection,
+    a pixel's value divided by the reciprocal-space intensity at the pixel's
+    query point (oracle.point, which applies no Lorentz factor) is L(R);
+    0 < L <= 1, L -> 1 for R << delta_L and L R / delta_L -> 1 for
+    R >> delta_L."""
+    from dataclasses import replace
+    p = W.small_helix()
+    p = replace(p, geom=replace(p.geom, delta_L=delta_L))
+    hkl_all = orc.reflections(p.cell, p.d_min)
+    n = np.array(p.geom.fiber_axis, float) / np.linalg.norm(p.geom.fiber_axis)
+    _, As = orc.basis(p.cell)
+    As = np.asarray(As)
+    pix = orc.all_pixels(p)
+    checked = 0
+    low = hkl_all[np.argsort(np.linalg.norm(hkl_all @ As, axis=1))][:24]  # the reflections nearest the beam
+    for hkl in low:
+        one = hkl.reshape(1, 3)
+        I, _ = orc.pattern(p, one, np.ones(1), pix)
+        hit = np.nonzero(I > 0)[0][:6]
+        if len(hit) == 0:
+            continue
+        D = one[0] @ As
+        perp = D - (D @ n) * n
+        if np.linalg.norm(perp) < 1e-12:
+            continue  # meridional reflection: e_R is the frame's e1, covered elsewhere
+        eR = perp / np.linalg.norm(perp)
+        for q in hit:
+            _, R, Z = orc.pixel_S(p, int(pix[q, 0]), int(pix[q, 1]))
+            Ip = orc.point(p, one, np.ones(1), (Z * n + R * eR).reshape(1, 3))[0]
+            L = I[q] / Ip
+            assert L == pytest.approx(delta_L / (R + delta_L), rel=1e-10)
+            assert 0.0 < L <= 1.0
+            if R < 1e-3 * delta_L:
+                assert L > 0.999
+            if R > 1e3 * delta_L:
+                assert L * R / delta_L == pytest.approx(1.0, rel=2e-3)
+            checked += 1
+    assert checked >= 20
