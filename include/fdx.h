@@ -380,6 +380,27 @@ int fdx_get_tuning(fdx_tuning *t);
 int fdx_status(void *stream, int *device_status);
 
 /* Human-readable text for a return code (static storage). */
+/*
+ * fdx_debug_status -- bounds checks of a debugging build.  A library compiled
+ * with FDX_DEBUG defined and relocatable device code (the package's build
+ * script writes it as libfdx_debug.so) checks its kernels' main indexing (node table, staging buffers, tile lists,
+ * reflection records, pixel and gradient images, adjoint items,
+ * structure-factor partial rows, batched position tables): an index outside
+ * its buffer sets a bit in a device status word (bit k for check k, see
+ * DebugCheck in the sources), records the index and skips the access.  This
+ * call waits for the device, copies the word into *flags and the last bad
+ * index into *last_index (either may be NULL), clears both, and returns 1.
+ * A normal build has no checks: it sets *flags = 0, *last_index = -1 and
+ * returns 0.  FDX_ERR_CUDA if the device copy fails.
+ */
+int fdx_debug_status(unsigned long long *flags, long long *last_index);
+
+/* fdx_debug_probe -- in a debugging build, queue on `stream` one check that
+ * fails on purpose (check 63, index 7; no memory but the status word is
+ * touched), so that a caller can see fdx_debug_status report it; returns 1.
+ * A normal build does nothing and returns 0. */
+int fdx_debug_probe(void *stream);
+
 const char *fdx_error_string(int code);
 
 /* Library version as major*10000 + minor*100 + patch. */

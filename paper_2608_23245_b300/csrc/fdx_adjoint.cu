@@ -101,8 +101,11 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
             bool cand = false;
             if (idx < np) {
                 const int pj = pj0 + PPL * (idx / A.npx), pi = idx % A.npx;
-                float4 bb = A.patch_bounds[(size_t)pj * A.npx + pi];
-                if (PPL == 2 && pj + 1 < A.npy) {
+                float4 bb = make_float4(3.0e38f, -3.0e38f, 3.0e38f, -3.0e38f);  // empty: no overlap
+                if (FDX_IN_BOUNDS((size_t)pj * A.npx + pi, (long long)A.npx * A.npy, DBG_PATCH))
+                    bb = A.patch_bounds[(size_t)pj * A.npx + pi];
+                if (PPL == 2 && pj + 1 < A.npy &&
+                    FDX_IN_BOUNDS((size_t)(pj + 1) * A.npx + pi, (long long)A.npx * A.npy, DBG_PATCH)) {
                     const float4 b2 = A.patch_bounds[(size_t)(pj + 1) * A.npx + pi];
                     bb = make_float4(fminf(bb.x, b2.x), fmaxf(bb.y, b2.y), fminf(bb.z, b2.z), fmaxf(bb.w, b2.w));
                 }
@@ -122,7 +125,9 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
                     qp.cw[p] = 0.0f;
                     if (g.valid[p]) {
                         const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
-                        qp.cw[p] = A.gI[(size_t)py * A.P.nx + px] * (dl / ((g.Rh[p] + g.Rl[p]) + dl));
+                        const size_t q = (size_t)py * A.P.nx + px;
+                        if (FDX_IN_BOUNDS(q, (long long)A.P.nx * A.P.ny, DBG_GRAD_IN))
+                            qp.cw[p] = A.gI[q] * (dl / ((g.Rh[p] + g.Rl[p]) + dl));
                     }
                     any |= qp.cw[p] != 0.0f;
                 }
@@ -147,7 +152,8 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
 #pragma unroll
         for (int k = 1; k < ADJ_ITEM_VALS; ++k)
             if (lane == k) o = acc[k];
-        A.item_out[item * ADJ_ITEM_VALS + lane] = o;
+        if (FDX_IN_BOUNDS(item * ADJ_ITEM_VALS + lane, (long long)A.P.n_refl * A.n_bands * ADJ_ITEM_VALS, DBG_ITEM))
+            A.item_out[item * ADJ_ITEM_VALS + lane] = o;
     }
 }
 
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(Batch
         const long long item = B.item0 + (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
         if (item >= B.item_end) break;
         const int j = item_position(B.item_prefix, B.pos0, B.n_pos, item);
+        if (!FDX_IN_BOUNDS(j - B.pos0, B.n_pos, DBG_BATCH)) continue;
         adjoint_item<FDX_LINESHAPE_HOSEMANN, PPL>(B.models[B.item_model[j]], item - B.item_prefix[j], s_nodes[warp],
                                                   s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
     }

@@ -643,6 +643,42 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
 
 int fdx_version(void) { return 100; }
 
+#ifdef FDX_DEBUG
+__device__ unsigned long long fdx_debug_word[2];
+
+// One check that fails on purpose (index 7 of a 3-entry range, check 63):
+// nothing is accessed, only the status word is written.
+__global__ void debug_probe_kernel() {
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)FDX_IN_BOUNDS(7, 3, 63);
+}
+#endif
+
+int fdx_debug_probe(void *stream) {
+#ifdef FDX_DEBUG
+    debug_probe_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>();
+    return cudaGetLastError() == cudaSuccess ? 1 : FDX_ERR_CUDA;
+#else
+    (void)stream;
+    return 0;
+#endif
+}
+
+int fdx_debug_status(unsigned long long *flags, long long *last_index) {
+#ifdef FDX_DEBUG
+    unsigned long long w[2] = {0ull, 0ull};
+    const unsigned long long z[2] = {0ull, 0ull};
+    if (cudaMemcpyFromSymbol(w, fdx_debug_word, sizeof w) != cudaSuccess) return FDX_ERR_CUDA;
+    if (cudaMemcpyToSymbol(fdx_debug_word, z, sizeof z) != cudaSuccess) return FDX_ERR_CUDA;
+    if (flags) *flags = w[0];
+    if (last_index) *last_index = (long long)w[1];
+    return 1;
+#else
+    if (flags) *flags = 0ull;
+    if (last_index) *last_index = -1;
+    return 0;
+#endif
+}
+
 int fdx_status(void *stream, int *device_status) {
     const cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     if (device_status) *device_status = (int)e;

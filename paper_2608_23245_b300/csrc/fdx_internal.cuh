@@ -10,7 +10,45 @@
 #define FDX_FULL_MASK 0xffffffffu
 #define FDX_PI 3.14159265358979323846
 
+// ---------------------------------------------------------------------------
+// Bounds checks of a debugging build (compiled with FDX_DEBUG and relocatable
+// device code): an index outside its buffer sets the check's bit in a device
+// status word, records the index and skips the access (no trap, no assert:
+// the context stays usable); fdx_debug_status reads and clears the word.  In
+// a normal build FDX_IN_BOUNDS is the constant true and changes no code.
+// ---------------------------------------------------------------------------
+#ifdef FDX_DEBUG
+extern __device__ unsigned long long fdx_debug_word[2];  // [0]: bits of failed checks, [1]: last bad index
+__device__ __forceinline__ bool fdx_in_bounds(long long i, long long n, int check) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&fdx_debug_word[0], 1ull << check);
+    atomicExch(&fdx_debug_word[1], (unsigned long long)i);
+    return false;
+}
+#define FDX_IN_BOUNDS(i, n, check) fdx_in_bounds((long long)(i), (long long)(n), (check))
+#else
+#define FDX_IN_BOUNDS(i, n, check) true
+#endif
+
 namespace fdx {
+
+// The checks of a debugging build, one bit each in the status word.
+enum DebugCheck {
+    DBG_NODES = 0,    // node-table entry of a staged block
+    DBG_STAGE = 1,    // slot of the warp's node buffer written by staging
+    DBG_PACK = 2,     // node pair written by packing
+    DBG_WALK = 3,     // node pair read by the walk
+    DBG_LIST = 4,     // slot of a tile's reflection list
+    DBG_RECORD = 5,   // reflection index of a list entry
+    DBG_IMAGE = 6,    // pixel written by a pattern-family kernel
+    DBG_PIXGEO = 7,   // pixel-geometry entry read
+    DBG_PATCH = 8,    // adjoint patch bounds
+    DBG_GRAD_IN = 9,  // dL/dI entry read by the adjoint
+    DBG_ITEM = 10,    // adjoint item output
+    DBG_SF_PART = 11, // structure-factor partial-sum row
+    DBG_SPLAT = 12,   // scatter-form image entry
+    DBG_BATCH = 13    // position-table entry of a batched launch
+};
 
 // ---------------------------------------------------------------------------
 // Float-float ("double-float") arithmetic: a value is hi + lo with |lo| <=

@@ -196,7 +196,8 @@ __device__ __forceinline__ PatchPix<PPL> load_patch(const float4 *pixgeo, int nx
         const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
         g.valid[p] = (px < nx) && (py < ny);
         const size_t pidx = g.valid[p] ? (size_t)py * nx + px : (size_t)py0 * nx + px0;
-        const float4 v = pixgeo[pidx];
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (FDX_IN_BOUNDS(pidx, (long long)nx * ny, DBG_PIXGEO)) v = pixgeo[pidx];
         g.Rh[p] = v.x, g.Rl[p] = v.y, g.Zh[p] = v.z, g.Zl[p] = v.w;
     }
     // central pixel: row 2 PPL = lane-row (2 PPL) % 4 of pixel set (2 PPL) / 4
@@ -497,12 +498,12 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             const int q = q0 + lane;
             float4 nq = rim ? make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float2 dw = make_float2(0.0f, 0.0f);
-            if (q < n) {
+            if (q < n && FDX_IN_BOUNDS(base + q, NB, DBG_PACK)) {
                 nq = buf[base + q];
                 if (MODE == MODE_ADJ) dw = reinterpret_cast<const float2 *>(buf2)[base + q];
             }
             __syncwarp();
-            if (q < npad) {
+            if (q < npad && FDX_IN_BOUNDS((base >> 1) + (q >> 1), NB / 2, DBG_PACK)) {
                 float2 sab, cab;
                 float sc, cc;
                 sincospi_f2(make_float2(nq.x, nq.y), sab, cab);  // axes a, b on packed pairs
@@ -526,6 +527,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     auto pack_pair = [&](int base, int n, bool rim) {
         const int npair = (n + 1) >> 1;
         for (int k = lane; k < npair; k += 32) {
+            if (!FDX_IN_BOUNDS((base >> 1) + k, NB / 2, DBG_PACK)) continue;
             const float4 pad = rim ? make_float4(-3.0e4f, -3.0e4f, -3.0e4f, 0.0f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             const float4 n0 = buf[base + 2 * k];
             const float4 n1 = 2 * k + 1 < n ? buf[base + 2 * k + 1] : pad;
@@ -570,6 +572,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             for (int p = 0; p < PPL; ++p) r0[p] = rb0[p] = rb1[p] = rb2[p] = rss[p] = rsg[p] = f2(0.0f);
 #pragma unroll 2
             for (int u = ub + u0; u < ue; ++u) {
+                if (!FDX_IN_BOUNDS(u, NB / 2, DBG_WALK)) continue;
                 const float4 A4 = buf[2 * u], B4 = buf[2 * u + 1];
                 const float4 C4 = bsc[2 * u], D4 = bsc[2 * u + 1], E4 = bsc2[u];
                 float4 W4;
@@ -694,8 +697,10 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             node_of(blk0 + __ffs(bmask) - 1, jc, mc);
             bmask &= bmask - 1;
             const size_t k = (size_t)min(jc, J1) * n + min(mc, M1);
-            na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
-            if (MODE == MODE_ADJ) dn = P.dnodes[k];
+            if (FDX_IN_BOUNDS(k, (long long)n * n, DBG_NODES)) {
+                na = P.nodes[2 * k], nb = P.nodes[2 * k + 1];
+                if (MODE == MODE_ADJ) dn = P.dnodes[k];
+            }
         }
         while (have) {
             int jn = 0, mn = 0;
@@ -706,8 +711,10 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                 node_of(blk0 + __ffs(bmask) - 1, jn, mn);
                 bmask &= bmask - 1;
                 const size_t k = (size_t)min(jn, J1) * n + min(mn, M1);
-                na2 = P.nodes[2 * k], nb2 = P.nodes[2 * k + 1];
-                if (MODE == MODE_ADJ) dn2 = P.dnodes[k];
+                if (FDX_IN_BOUNDS(k, (long long)n * n, DBG_NODES)) {
+                    na2 = P.nodes[2 * k], nb2 = P.nodes[2 * k + 1];
+                    if (MODE == MODE_ADJ) dn2 = P.dnodes[k];
+                }
             }
             bool live = false;
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -731,8 +738,10 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
             const unsigned balc = SPLIT ? __ballot_sync(FDX_FULL_MASK, core) : 0u;
             if (live) {
                 const int pos = core ? nc + __popc(balc & lt_mask) : RIM0 + nr + __popc(bal & lt_mask);
-                buf[pos] = val;
-                if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = dn;
+                if (FDX_IN_BOUNDS(pos, NB, DBG_STAGE)) {
+                    buf[pos] = val;
+                    if (MODE == MODE_ADJ) reinterpret_cast<float2 *>(buf2)[pos] = dn;
+                }
             }
             nr += __popc(bal);
             nc += __popc(balc);

@@ -60,18 +60,22 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
                 cand = (q.x - q.y <= rmax) && (q.x + q.y >= rmin) && (q.z - q.w <= pmax) && (q.z + q.w >= pmin);
             }
             const unsigned m = __ballot_sync(FDX_FULL_MASK, cand);
-            if (cand) lst[n + __popc(m & ((1u << lane) - 1u))] = rr;
+            const int slot = n + __popc(m & ((1u << lane) - 1u));
+            if (cand && FDX_IN_BOUNDS(slot, TILE_SCAN, DBG_LIST)) lst[slot] = rr;
             n += __popc(m);
         }
         __syncwarp();
         if (n == 0) continue;
-        const float *grec = P.recs + (size_t)lst[0] * REC_SIZE;
-        float nx0 = grec[lane], nx1 = grec[lane + 32];
+        float nx0 = 0.0f, nx1 = 0.0f;
+        if (FDX_IN_BOUNDS(lst[0], P.n_refl, DBG_RECORD)) {
+            const float *grec = P.recs + (size_t)lst[0] * REC_SIZE;
+            nx0 = grec[lane], nx1 = grec[lane + 32];
+        }
         for (int c = 0; c < n; ++c) {
             __syncwarp();
             rec[lane] = nx0, rec[lane + 32] = nx1;
             __syncwarp();
-            if (c + 1 < n) {
+            if (c + 1 < n && FDX_IN_BOUNDS(lst[c + 1], P.n_refl, DBG_RECORD)) {
                 const float *gn = P.recs + (size_t)lst[c + 1] * REC_SIZE;
                 nx0 = gn[lane], nx1 = gn[lane + 32];
             }
@@ -94,6 +98,7 @@ __device__ __forceinline__ void pattern_warp(const PatternParams &P, int px0, in
         if (!g.valid[p]) continue;
         const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
         const size_t out = (size_t)py * P.nx + px;
+        if (!FDX_IN_BOUNDS(out, (long long)P.nx * P.ny, DBG_IMAGE)) continue;
         if (MODE == MODE_CNT) {
             P.counts[out] = cnt[p];
         } else {
@@ -153,6 +158,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) pattern_batch_kernel(Batch
         const long long item = s_item;
         if (item >= B.item_end) break;
         const int j = item_position(B.item_prefix, B.pos0, B.n_pos, item);
+        if (!FDX_IN_BOUNDS(j - B.pos0, B.n_pos, DBG_BATCH)) continue;
         const PatternParams &P = B.models[B.item_model[j]];
         const int t = (int)(item - B.item_prefix[j]);
         const int tiles_x = (P.nx + 15) / 16;

@@ -126,6 +126,7 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
     if (!g.valid[0]) return;
     const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
     const size_t out = (size_t)py * P.nx + px;
+    if (!FDX_IN_BOUNDS(out, (long long)P.nx * P.ny, DBG_IMAGE)) return;
     if (RP.partial) {
         const size_t slot = (size_t)blockIdx.z * P.nx * P.ny + out;
         if (MODE == MODE_CNT)

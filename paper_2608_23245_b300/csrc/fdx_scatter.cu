@@ -146,13 +146,15 @@ __device__ __forceinline__ void splat_sample(const ScatterParams &p, const ff *s
             continue;
         const int ci = (int)fi, cj = (int)fj;
         if (half == 0) {
-            atomicAdd(&p.img64[(size_t)cj * p.P.nx + (size_t)ci], v);
+            if (FDX_IN_BOUNDS((size_t)cj * p.P.nx + (size_t)ci, (long long)p.P.nx * p.P.ny, DBG_SPLAT))
+                atomicAdd(&p.img64[(size_t)cj * p.P.nx + (size_t)ci], v);
             continue;
         }
         const double share = v / (double)(p.spot * p.spot);
         for (int qj = max(cj - half, 0); qj <= min(cj + half, p.P.ny - 1); ++qj)
             for (int qi = max(ci - half, 0); qi <= min(ci + half, p.P.nx - 1); ++qi)
-                atomicAdd(&p.img64[(size_t)qj * p.P.nx + (size_t)qi], share);
+                if (FDX_IN_BOUNDS((size_t)qj * p.P.nx + (size_t)qi, (long long)p.P.nx * p.P.ny, DBG_SPLAT))
+                    atomicAdd(&p.img64[(size_t)qj * p.P.nx + (size_t)qi], share);
     }
 }
 

@@ -479,7 +479,8 @@ __global__ void __launch_bounds__(SF_THREADS) sf_main_kernel(SFParams p) {
         for (int t = 0; t < SF_GPT; ++t)
 #pragma unroll
             for (int j = 0; j < SF_GROUP; ++j)
-                if (j < cnt[t]) p.partial[row + r0[t] + j] = make_float4(reF[t][j].hi, reF[t][j].lo, imF[t][j].hi, imF[t][j].lo);
+                if (j < cnt[t] && FDX_IN_BOUNDS(row + r0[t] + j, (long long)p.n_rows * p.n_refl, DBG_SF_PART))
+                    p.partial[row + r0[t] + j] = make_float4(reF[t][j].hi, reF[t][j].lo, imF[t][j].hi, imF[t][j].lo);
     }
 }
 
@@ -614,6 +615,7 @@ cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s) {
     const int passes = sf_passes(p.n_elem);
     // items: at most (n_refl groups) / SF_GPB blocks x n_split; CTAs loop over items
     const long long items_ub = (long long)((p.n_refl + SF_GPB - 1) / SF_GPB) * p.n_split;
+    p.n_rows = passes * p.n_split;
     for (int pass = 0; pass < passes; ++pass) {
         p.e_lo = pass * SF_FE_MAX;
         p.n_fe = min(SF_FE_MAX, p.n_elem - p.e_lo);
@@ -623,7 +625,6 @@ cudaError_t launch_structure_factors(SFParams &p, cudaStream_t s) {
         const size_t shm = sizeof(float4) * 2 * SF_THREADS * (size_t)p.n_fe;
         sf_main_kernel<<<grid, SF_THREADS, shm, s>>>(p);
     }
-    p.n_rows = passes * p.n_split;
     sf_reduce_kernel<<<(p.n_refl + 127) / 128, 128, 0, s>>>(p);
     return cudaGetLastError();
 }

@@ -199,6 +199,30 @@ def fdx_status(stream=None) -> int:
     return code.value
 
 
+def fdx_debug_status():
+    """Bounds checks of a debugging build (libfdx_debug.so): returns
+    (checks_compiled_in, failed_check_bits, last_bad_index) and clears the
+    record; a normal build returns (False, 0, -1)."""
+    L = lib()
+    L.fdx_debug_status.argtypes = [C.POINTER(C.c_ulonglong), C.POINTER(C.c_longlong)]
+    flags, idx = C.c_ulonglong(0), C.c_longlong(0)
+    rc = L.fdx_debug_status(C.byref(flags), C.byref(idx))
+    if rc < 0:
+        raise FdxError(rc, "fdx_debug_status")
+    return bool(rc == 1), int(flags.value), int(idx.value)
+
+
+def fdx_debug_probe(stream=None) -> bool:
+    """Queue one deliberately failing bounds check in a debugging build
+    (True); a normal build does nothing (False)."""
+    L = lib()
+    L.fdx_debug_probe.argtypes = [C.c_void_p]
+    rc = L.fdx_debug_probe(_stream(stream) if stream is not None else None)
+    if rc < 0:
+        raise FdxError(rc, "fdx_debug_probe")
+    return rc == 1
+
+
 def fdx_reflections(cell, d_min, d_max=0.0) -> np.ndarray:
     """Reflection list as a host int32 [n, 3] array (count, then fill)."""
     c = make_cell(cell)

@@ -255,3 +255,10 @@ def test_status_reports_cuda_failure_without_device(fdx):
     assert lib.fdx_status(None, C.byref(code)) == -4
     assert code.value != 0
     assert lib.fdx_status(None, None) == -4
+
+
+def test_debug_status_of_a_normal_build(fdx):
+    """The product library has no bounds checks compiled in: fdx_debug_status
+    reports so without touching the device."""
+    assert fdx.fdx_debug_status() == (False, 0, -1)
+    assert fdx.fdx_debug_probe() is False
