@@ -361,7 +361,7 @@ typedef struct fdx_tuning {
                                 node sums (results agree to rounding), not the set of terms */
 } fdx_tuning;
 
-/* Set the tuning (NULL restores the defaults 2, 4, 3, 64, 1).  Workspace sizes
+/* Set the tuning (NULL restores the defaults 2, 4, 3, 128, 1).  Workspace sizes
  * depend on adj_bands: query them after setting. */
 int fdx_set_tuning(const fdx_tuning *t);
 int fdx_get_tuning(fdx_tuning *t);

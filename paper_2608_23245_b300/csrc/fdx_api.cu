@@ -16,7 +16,7 @@ namespace {
 constexpr size_t kAlign = 256;
 
 std::mutex g_tune_mu;
-fdx_tuning g_tune = {2, 4, 3, 64, 1};
+fdx_tuning g_tune = {2, 4, 3, 128, 1};
 
 fdx_tuning tuning() {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -686,7 +686,7 @@ int fdx_status(void *stream, int *device_status) {
 }
 
 int fdx_set_tuning(const fdx_tuning *t) {
-    fdx_tuning v = {2, 4, 3, 64, 1};
+    fdx_tuning v = {2, 4, 3, 128, 1};
     if (t) {
         if (t->ppl_max < 1 || t->ppl_max > 2 || t->fwd_ctas_per_sm < 1 || t->fwd_ctas_per_sm > 8 ||
             t->adj_ctas_per_sm < 1 || t->adj_ctas_per_sm > 8 || t->adj_bands < 1 || t->adj_bands > 256 ||

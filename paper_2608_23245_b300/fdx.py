@@ -602,7 +602,7 @@ class Tuning(C.Structure):
     _fields_ = [("ppl_max", C.c_int32), ("fwd_ctas_per_sm", C.c_int32), ("adj_ctas_per_sm", C.c_int32),
                 ("adj_bands", C.c_int32), ("node_block", C.c_int32)]
 
-    DEFAULTS = {"ppl_max": 2, "fwd_ctas_per_sm": 4, "adj_ctas_per_sm": 3, "adj_bands": 64, "node_block": 1}
+    DEFAULTS = {"ppl_max": 2, "fwd_ctas_per_sm": 4, "adj_ctas_per_sm": 3, "adj_bands": 128, "node_block": 1}
 
     @classmethod
     def of(cls, **knobs):

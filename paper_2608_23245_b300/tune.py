@@ -27,7 +27,7 @@ DEFAULT_GRID = {
     "node_block": (1, 0, 2, 3),
     "fwd_ctas_per_sm": (4, 3),
     "adj_ctas_per_sm": (3, 2),
-    "adj_bands": (64, 32, 128),
+    "adj_bands": (128, 64, 32),
 }
 
 

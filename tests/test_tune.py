@@ -101,5 +101,5 @@ def test_cache_round_trip(monkeypatch, tmp_path):
 def test_tuning_struct_defaults():
     t = fdx.Tuning.of(node_block=1)
     d = t.as_dict()
-    assert d["node_block"] == 1 and d["ppl_max"] == 2 and d["adj_bands"] == 64
+    assert d["node_block"] == 1 and d["ppl_max"] == 2 and d["adj_bands"] == 128
     assert set(d) == set(fdx.Tuning.DEFAULTS)
