@@ -29,7 +29,12 @@
 namespace fdx {
 
 static constexpr int ADJ_ITEM_VALS = 6;
-static constexpr int ADJ_NODE_BUF = 224;  // keeps the CTA's static shared memory under 48 KB
+// Staged nodes per warp: 384 (dynamic shared memory, 74.8 KB per CTA, 3 CTAs
+// per SM at the kernels' register count); 224, the most that static shared
+// memory allows, flushed twice as often and was 1.4 % slower.
+static constexpr int ADJ_NODE_BUF = 384;
+static constexpr int ADJ_PER_WARP = ADJ_NODE_BUF * 3 + REC_SIZE / 4;  // float4: nodes, dw (NB/2), sc, sc2 (NB/2), record
+static constexpr size_t ADJ_SMEM_BYTES = sizeof(float4) * PAIR_WARPS * ADJ_PER_WARP;
 
 __device__ __forceinline__ bool reach_overlap(float4 q, float4 b) {
     // q = (r0, rho_B, psi_D, dpsi); b = (rmin, rmax, psimin, psimax)
@@ -157,12 +162,13 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
     }
 }
 
-#define FDX_ADJ_SMEM                                        \
-    __shared__ float4 s_nodes[PAIR_WARPS][ADJ_NODE_BUF];    \
-    __shared__ float4 s_dn[PAIR_WARPS][ADJ_NODE_BUF / 2];   \
-    __shared__ float4 s_sc[PAIR_WARPS][ADJ_NODE_BUF];       \
-    __shared__ float4 s_sc2[PAIR_WARPS][ADJ_NODE_BUF / 2];  \
-    __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
+// This warp's slice of the adjoint kernels' dynamic shared memory.
+#define FDX_ADJ_SMEM                                                                           \
+    extern __shared__ float4 adsm[];                                                           \
+    float4 *const s_nodes = adsm + (size_t)(threadIdx.x >> 5) * ADJ_PER_WARP;                  \
+    float4 *const s_dn = s_nodes + ADJ_NODE_BUF, *const s_sc = s_dn + ADJ_NODE_BUF / 2;        \
+    float4 *const s_sc2 = s_sc + ADJ_NODE_BUF;                                                 \
+    float *const s_rec = reinterpret_cast<float *>(s_sc2 + ADJ_NODE_BUF / 2);
 
 // Single-model adjoint, persistent: each warp takes (reflection, band) items
 // from the model's queue until none is left, so warps whose items end early
@@ -170,14 +176,14 @@ __device__ __forceinline__ void adjoint_item(const AdjParams &A, long long item,
 template <int LS, int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A) {
     FDX_ADJ_SMEM
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     const long long total = (long long)A.P.n_refl * A.n_bands;
     for (;;) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(A.counter, 1u);
         const long long item = (long long)__shfl_sync(FDX_FULL_MASK, it, 0);
         if (item >= total) break;
-        adjoint_item<LS, PPL>(A, item, s_nodes[warp], s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+        adjoint_item<LS, PPL>(A, item, s_nodes, s_dn, s_sc, s_sc2, s_rec, lane);
     }
 }
 
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_kernel(AdjParams A
 template <int PPL>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(BatchAdjParams B) {
     FDX_ADJ_SMEM
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned it = 0;
         if (lane == 0) it = atomicAdd(B.counter, 1u);
@@ -196,8 +202,8 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 3) adjoint_batch_kernel(Batch
         if (item >= B.item_end) break;
         const int j = item_position(B.item_prefix, B.pos0, B.n_pos, item);
         if (!FDX_IN_BOUNDS(j - B.pos0, B.n_pos, DBG_BATCH)) continue;
-        adjoint_item<FDX_LINESHAPE_HOSEMANN, PPL>(B.models[B.item_model[j]], item - B.item_prefix[j], s_nodes[warp],
-                                                  s_dn[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+        adjoint_item<FDX_LINESHAPE_HOSEMANN, PPL>(B.models[B.item_model[j]], item - B.item_prefix[j], s_nodes, s_dn,
+                                                  s_sc, s_sc2, s_rec, lane);
     }
 }
 
@@ -426,6 +432,17 @@ __global__ void loss_final_kernel(LossParams p, int nblocks) {
 }
 
 // ---------------------------------------------------------------------------
+// The single-model adjoint kernel with its dynamic shared memory (above the
+// 48 KB a launch gets without asking).
+template <int LS, int PPL>
+static cudaError_t launch_adj(const AdjParams &A, unsigned grid, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<LS, PPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ADJ_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    adjoint_kernel<LS, PPL><<<grid, PAIR_WARPS * 32, ADJ_SMEM_BYTES, s>>>(A);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s) {
     const int n_patch = A.npx * A.npy;
     patch_bounds_kernel<<<(n_patch * 32 + 127) / 128, 128, 0, s>>>(A);
@@ -436,28 +453,31 @@ cudaError_t launch_adjoint(AdjParams &A, int n_ctas, cudaStream_t s) {
         const unsigned grid = (unsigned)(want < n_ctas ? want : n_ctas);
         if (cudaMemsetAsync(A.counter, 0, sizeof(unsigned), s) != cudaSuccess) return cudaGetLastError();
         const bool two = A.P.ppl == 2;
-        if (A.lineshape == FDX_LINESHAPE_SINC) {
-            if (two) adjoint_kernel<FDX_LINESHAPE_SINC, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-            else adjoint_kernel<FDX_LINESHAPE_SINC, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-        } else if (A.lineshape == FDX_LINESHAPE_GAUSS) {
-            if (two) adjoint_kernel<FDX_LINESHAPE_GAUSS, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-            else adjoint_kernel<FDX_LINESHAPE_GAUSS, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-        } else {
-            if (two) adjoint_kernel<FDX_LINESHAPE_HOSEMANN, 2><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-            else adjoint_kernel<FDX_LINESHAPE_HOSEMANN, 1><<<grid, PAIR_WARPS * 32, 0, s>>>(A);
-        }
+        cudaError_t e;
+        if (A.lineshape == FDX_LINESHAPE_SINC)
+            e = two ? launch_adj<FDX_LINESHAPE_SINC, 2>(A, grid, s) : launch_adj<FDX_LINESHAPE_SINC, 1>(A, grid, s);
+        else if (A.lineshape == FDX_LINESHAPE_GAUSS)
+            e = two ? launch_adj<FDX_LINESHAPE_GAUSS, 2>(A, grid, s) : launch_adj<FDX_LINESHAPE_GAUSS, 1>(A, grid, s);
+        else
+            e = two ? launch_adj<FDX_LINESHAPE_HOSEMANN, 2>(A, grid, s) : launch_adj<FDX_LINESHAPE_HOSEMANN, 1>(A, grid, s);
+        if (e != cudaSuccess) return e;
         adjoint_reflection_kernel<<<(A.P.n_refl + 127) / 128, 128, 0, s>>>(A);
     }
     adjoint_globals_kernel<<<1, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int ppl, int n_ctas, cudaStream_t s) {
-    if (ppl == 2)
-        adjoint_batch_kernel<2><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
-    else
-        adjoint_batch_kernel<1><<<n_ctas, PAIR_WARPS * 32, 0, s>>>(B);
+template <int PPL>
+static cudaError_t launch_adj_batch(const BatchAdjParams &B, int n_ctas, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(adjoint_batch_kernel<PPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ADJ_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    adjoint_batch_kernel<PPL><<<n_ctas, PAIR_WARPS * 32, ADJ_SMEM_BYTES, s>>>(B);
     return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_batch(const BatchAdjParams &B, int ppl, int n_ctas, cudaStream_t s) {
+    return ppl == 2 ? launch_adj_batch<2>(B, n_ctas, s) : launch_adj_batch<1>(B, n_ctas, s);
 }
 
 cudaError_t launch_adjoint_post(AdjParams &A, cudaStream_t s) {
