@@ -472,8 +472,9 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
 
     // Hosemann walk on node pairs.  Per pixel and pair: t = tau - sigma (support
     // test), scaled sin(pi t) = sin(pi tau) C - cos(pi tau) S, den_i = beta_i^2 +
-    // (scaled sin)^2, 1/prod den by one SFU reciprocal; a node outside the
-    // pixel's support gets the reciprocal of +inf, i.e. weight 0.
+    // (scaled sin)^2, 1/prod den by one SFU reciprocal (the adjoint takes two:
+    // 1/den_a and 1/(den_b den_c)); a node outside the pixel's support gets the
+    // reciprocal of +inf, i.e. weight 0.
     float2 tau2[PPL][3], st2[PPL][3], ctn2[PPL][3], la2[3];
     if (PACKED) {
 #pragma unroll
@@ -590,6 +591,34 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     const float2 da = __ffma2_rn(xa, xa, la2[0]);
                     const float2 db = __ffma2_rn(xb, xb, la2[1]);
                     const float2 dc = __ffma2_rn(xc, xc, la2[2]);
+                    if constexpr (MODE == MODE_ADJ) {
+                        // two reciprocals per node, ra = 1/den_a and rbc = 1/(den_b den_c):
+                        // 1/prod den = ra rbc, and the three kv/den_i are kv ra,
+                        // (kv rbc) den_c and (kv rbc) den_b -- two packed products fewer
+                        // than dividing by the full product, for one more SFU operation
+                        const float2 dbc = __fmul2_rn(db, dc);
+                        float2 ra;
+                        if constexpr (TEST) {
+                            const float2 ta = __fadd2_rn(tau2[p][0], nsa);
+                            const float2 tb = __fadd2_rn(tau2[p][1], nsb);
+                            const float2 tc2 = __fadd2_rn(tau2[p][2], nsc);
+                            ra = make_float2(rcp_approx(support_sel(ta.x, tb.x, tc2.x, tm[0], tm[1], tm[2], da.x, inf)),
+                                             rcp_approx(support_sel(ta.y, tb.y, tc2.y, tm[0], tm[1], tm[2], da.y, inf)));
+                        } else {
+                            ra = make_float2(rcp_approx(da.x), rcp_approx(da.y));
+                        }
+                        const float2 rbc = make_float2(rcp_approx(dbc.x), rcp_approx(dbc.y));
+                        const float2 rp = __fmul2_rn(ra, rbc);
+                        const float2 kv = __fmul2_rn(w, rp);
+                        r0[p] = __fadd2_rn(r0[p], kv);
+                        rb0[p] = __ffma2_rn(kv, ra, rb0[p]);
+                        const float2 q = __fmul2_rn(kv, rbc);
+                        rb1[p] = __ffma2_rn(q, dc, rb1[p]);
+                        rb2[p] = __ffma2_rn(q, db, rb2[p]);
+                        rss[p] = __ffma2_rn(make_float2(W4.x, W4.y), rp, rss[p]);
+                        rsg[p] = __ffma2_rn(make_float2(W4.z, W4.w), rp, rsg[p]);
+                        continue;
+                    }
                     const float2 dab = __fmul2_rn(da, db);
                     const float2 d = __fmul2_rn(dab, dc);
                     float2 rp;
@@ -602,20 +631,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
                     } else {
                         rp = make_float2(rcp_approx(d.x), rcp_approx(d.y));
                     }
-                    if (MODE == MODE_FWD) {
-                        r0[p] = __ffma2_rn(w, rp, r0[p]);
-                    } else {
-                        const float2 kv = __fmul2_rn(w, rp);
-                        r0[p] = __fadd2_rn(r0[p], kv);
-                        // kv / den_i = (kv rp) (product of the other two)
-                        const float2 q = __fmul2_rn(kv, rp);
-                        const float2 dbc = __fmul2_rn(db, dc), dac = __fmul2_rn(da, dc);
-                        rb0[p] = __ffma2_rn(q, dbc, rb0[p]);
-                        rb1[p] = __ffma2_rn(q, dac, rb1[p]);
-                        rb2[p] = __ffma2_rn(q, dab, rb2[p]);
-                        rss[p] = __ffma2_rn(make_float2(W4.x, W4.y), rp, rss[p]);
-                        rsg[p] = __ffma2_rn(make_float2(W4.z, W4.w), rp, rsg[p]);
-                    }
+                    r0[p] = __ffma2_rn(w, rp, r0[p]);
                 }
             }
             if (MODE == MODE_ADJ) {
