@@ -238,10 +238,12 @@ __device__ __forceinline__ void clear(PairAcc &a) {
 //   bsc[2u]  = (C_a, C_a', S_a, S_a'),  bsc[2u+1] = (C_b, C_b', S_b, S_b'),  bsc2[u] = (C_c, C_c', S_c, S_c'),
 //   buf2[u]  = (dw_s, dw_s', dw_g, dw_g')   (primes: the odd node of the pair),
 // with C_i = sqrt(1 - beta_i^2) cos(pi sigma_i), S_i likewise with sin.
-// In the Hosemann forward, nodes are staged in two lists: "core" nodes (slots
-// [0, NB/2)) lie inside the support of every valid pixel of the warp, by a
-// margin far above FP32 rounding, so their walk needs no support test; the
-// others ("rim", slots [NB/2, NB)) are tested per pixel.  Returns false when no node can be
+// In the Hosemann walks (forward and adjoint), nodes are staged in two lists:
+// "core" nodes (slots [0, NB/2)) lie inside the support of every valid pixel
+// of the warp, by a margin far above FP32 rounding, so their walk needs no
+// support test (an invalid point's terms there are finite and weighted by 0 in
+// the adjoint, never written in the forward); the others ("rim", slots
+// [NB/2, NB)) are tested per pixel.  Returns false when no node can be
 // in any pixel's support.
 //
 // Hosemann denominators by angle addition: with t = tau - sigma,
@@ -393,11 +395,12 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // staged counts: nr = rim nodes (all nodes when not PACKED), nc = core nodes
     int nr = 0, nc = 0;
     constexpr int NBH = NB / 2;                  // slots per list (PACKED)
-    // core/rim split in the forward only.  In the adjoint it would save about
-    // 5 % of the walk, but it reorders the width-derivative sums, which nearly
-    // cancel (a normalised profile's derivative in its width integrates to
-    // zero), and their FP32 result then moved by up to 1.4e-4 relative.
-    constexpr bool SPLIT = PACKED && MODE == MODE_FWD;
+    // core/rim split in both the forward and the adjoint (Hosemann).  The
+    // adjoint's global gradients are differences of nearly equal sums over
+    // reflections, so their FP32 rounding depends on the walk order; with the
+    // split and 128-pair chunks the largest relative error against the FP64
+    // adjoint on the seeded test models is 4e-5 (2.9e-5 without the split).
+    constexpr bool SPLIT = PACKED;
     constexpr int RIM0 = SPLIT ? NBH : 0;        // first rim slot
     constexpr int RIM_CAP = SPLIT ? NBH : NB;
     static_assert(NB % 4 == 0, "node buffer must hold an even number of pairs per list");
@@ -565,7 +568,7 @@ __device__ __forceinline__ bool eval_core(const PatternParams &P, const QueryPts
     // walk npair pairs from pair slot ub; TEST: per-pixel support test (rim list)
     auto walk = [&](int ub, int npair, auto test_tag) {
         constexpr bool TEST = decltype(test_tag)::value;
-        constexpr int CH = MODE == MODE_ADJ ? 64 : 32;  // node pairs per FP32 chunk sum (the adjoint folds six)
+        constexpr int CH = MODE == MODE_ADJ ? 128 : 32;  // node pairs per FP32 chunk sum (the adjoint folds six)
         for (int u0 = 0; u0 < npair; u0 += CH) {
             const int ue = ub + min(u0 + CH, npair);
             float2 r0[PPL], rb0[PPL], rb1[PPL], rb2[PPL], rss[PPL], rsg[PPL];
