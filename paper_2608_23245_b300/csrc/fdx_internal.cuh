@@ -227,6 +227,8 @@ enum RingField {
     RING_RT = 13,   // rho_tot = rho_B + sqrt(2) r0 T
     RING_REC = 16
 };
+// Pixels per lane of the ring average: a warp's patch is 8 x 4 RING_PPL pixels.
+static constexpr int RING_PPL = 2;
 
 struct NodeParams {
     int n;

@@ -7,8 +7,9 @@
 // per-reflection midpoint rule over [-Phi_r, Phi_r] (N_r points; window and
 // step from the reflection set-up kernel, reading R21).
 //
-// Work decomposition: as the gather form, a warp owns an 8 x 4 pixel patch
-// and scans the reflections with the reach test (the ring points of a pixel
+// Work decomposition: as the gather form, a warp owns an 8 x 8 pixel patch
+// (two pixels per lane, rows 0-3 and 4-7, so that the packed walk has two
+// query points per node pair) and scans the reflections with the reach test (the ring points of a pixel
 // have its |S| and polar angle, so the test is exact for every azimuth); for
 // each azimuth point of a surviving reflection the patch's query points are
 // the pixels' ring points p(phi_j), evaluated by eval_core (block culling,
@@ -25,19 +26,23 @@ namespace fdx {
 
 static constexpr int RING_NODE_BUF = 288;
 
-template <int LS, int MODE>
+template <int LS, int MODE, int PPL>
 __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0, float4 *buf, float4 *bsc,
                                           float4 *bsc2, float *rec, int lane) {
     const PatternParams &P = RP.P;
-    const PatchPix<1> g = load_patch<1>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
+    const PatchPix<PPL> g = load_patch<PPL>(P.pixgeo, P.nx, P.ny, px0, py0, lane);
     float rmin = 3.0e38f, rmax = -3.0e38f, pmin = 3.0e38f, pmax = -3.0e38f;
-    if (g.valid[0]) {
-        const float rlen = sqrtf(g.Rh[0] * g.Rh[0] + g.Zh[0] * g.Zh[0]), psi = atan2f(g.Rh[0], g.Zh[0]);
-        rmin = rmax = rlen, pmin = pmax = psi;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        if (!g.valid[p]) continue;
+        const float rlen = sqrtf(g.Rh[p] * g.Rh[p] + g.Zh[p] * g.Zh[p]), psi = atan2f(g.Rh[p], g.Zh[p]);
+        rmin = fminf(rmin, rlen), rmax = fmaxf(rmax, rlen), pmin = fminf(pmin, psi), pmax = fmaxf(pmax, psi);
     }
     rmin = warp_min(rmin), rmax = warp_max(rmax), pmin = warp_min(pmin), pmax = warp_max(pmax);
-    ff acc = {0.0f, 0.0f};
-    int32_t cnt = 0;
+    ff acc[PPL];
+    int32_t cnt[PPL];
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) acc[p] = ff{0.0f, 0.0f}, cnt[p] = 0;
 
     for (int base = 0; base < P.n_refl; base += 32) {
         bool cand = false;
@@ -61,15 +66,21 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
             float AT[3], tfrh[3], tfrl[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) AT[k] = gr[RING_AT + k], tfrh[k] = gr[RING_TFR + k], tfrl[k] = gr[RING_TFR + 3 + k];
-            // this lane's pixel relative to D (float, bounds and reach of the arc)
-            const float dZ = (g.Zh[0] - rec[REC_ZD]) + (g.Zl[0] - rec[REC_ZD + 1]);
-            const float dR = (g.Rh[0] - rec[REC_RD]) + (g.Rl[0] - rec[REC_RD + 1]);
-            const float RDf = rec[REC_RD], Rf = g.Rh[0];
+            // this lane's pixels relative to D (float, bounds and reach of the arc)
+            float dZ[PPL], dR[PPL];
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) {
+                dZ[p] = (g.Zh[p] - rec[REC_ZD]) + (g.Zl[p] - rec[REC_ZD + 1]);
+                dR[p] = (g.Rh[p] - rec[REC_RD]) + (g.Rl[p] - rec[REC_RD + 1]);
+            }
+            const float RDf = rec[REC_RD];
             const float rt2 = rt * rt * (1.0f + 1e-4f) + 1e-12f;
             const ff dZr = ff_add(two_sum(g.Zrh, -rec[REC_ZD]), ff{g.Zrl, -rec[REC_ZD + 1]});
             const ff dRr = ff_add(two_sum(g.Rrh, -rec[REC_RD]), ff{g.Rrl, -rec[REC_RD + 1]});
             const ff RD = {rec[REC_RD], rec[REC_RD + 1]}, Rr = {g.Rrh, g.Rrl};
-            ff pair = {0.0f, 0.0f};
+            ff pair[PPL];
+#pragma unroll
+            for (int p = 0; p < PPL; ++p) pair[p] = ff{0.0f, 0.0f};
             // this warp's share of the points: j = z + S m, m = 0, 1, ...
             const int S = RP.n_split, z = blockIdx.z;
             const int nz = N > z ? (N - z + S - 1) / S : 0;
@@ -88,20 +99,27 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
                     const ff om = {__shfl_sync(FDX_FULL_MASK, oh, jj), __shfl_sync(FDX_FULL_MASK, ol, jj)};
                     const float cp = 1.0f - om.hi;
                     // |p(phi) - D|^2 = dZ^2 + dR^2 + 2 R R_D (1 - cos phi): skip arcs out of reach
-                    const bool nearp = g.valid[0] && fmaf(dZ, dZ, fmaf(dR, dR, 2.0f * Rf * RDf * om.hi)) <= rt2;
+                    bool nearp = false;
+#pragma unroll
+                    for (int p = 0; p < PPL; ++p)
+                        nearp |= g.valid[p] &&
+                                 fmaf(dZ[p], dZ[p], fmaf(dR[p], dR[p], 2.0f * g.Rh[p] * RDf * om.hi)) <= rt2;
                     if (!__any_sync(FDX_FULL_MASK, nearp)) continue;
-                    QueryPts<1> q;
-                    q.valid[0] = g.valid[0];
-                    // p - D = dZ n + (dR cos phi - R_D (1 - cos phi)) e_R + R sin phi e_P
-                    const float er = fmaf(dR, cp, -RDf * om.hi), et = Rf * sp.hi;
+                    QueryPts<PPL> q;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k)
-                        q.P[0][k] = fmaf(dZ, rec[REC_NFR + k], fmaf(er, rec[REC_EFR + k], et * tfrh[k]));
+                    for (int p = 0; p < PPL; ++p) {
+                        q.valid[p] = g.valid[p];
+                        // p - D = dZ n + (dR cos phi - R_D (1 - cos phi)) e_R + R sin phi e_P
+                        const float er = fmaf(dR[p], cp, -RDf * om.hi), et = g.Rh[p] * sp.hi;
 #pragma unroll
-                    for (int i = 0; i < 3; ++i)
-                        q.tau[0][i] = g.valid[0]
-                                          ? fmaf(g.dZl[0], P.AZ[i], g.dRl[0] * fmaf(cp, rec[REC_AR + i], sp.hi * AT[i]))
-                                          : 1.0e4f;
+                        for (int k = 0; k < 3; ++k)
+                            q.P[p][k] = fmaf(dZ[p], rec[REC_NFR + k], fmaf(er, rec[REC_EFR + k], et * tfrh[k]));
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+                            q.tau[p][i] = g.valid[p] ? fmaf(g.dZl[p], P.AZ[i],
+                                                            g.dRl[p] * fmaf(cp, rec[REC_AR + i], sp.hi * AT[i]))
+                                                     : 1.0e4f;
+                    }
                     // reference (p_ref - D)/r0 in the reflection frame, float-float
                     const ff cpf = ff_add(ff{1.0f, 0.0f}, ff{-om.hi, -om.lo});
                     const ff erf_ = ff_sub(ff_mul(dRr, cpf), ff_mul(RD, om));
@@ -111,32 +129,42 @@ __device__ __forceinline__ void ring_warp(const RingParams &RP, int px0, int py0
                         q.dP[k] = ff_add(ff_add(ff_mul(dZr, ff{rec[REC_NFR + k], rec[REC_NFR + 3 + k]}),
                                                 ff_mul(erf_, ff{rec[REC_EFR + k], rec[REC_EFR + 3 + k]})),
                                          ff_mul(etf, ff{tfrh[k], tfrl[k]}));
-                    PairAcc pa[1];
-                    clear(pa[0]);
-                    if (!eval_core<LS, MODE, RING_NODE_BUF, 1>(P, q, rec, buf, nullptr, bsc, bsc2, lane, pa)) continue;
-                    if (MODE == MODE_CNT)
-                        cnt += pa[0].cnt;
-                    else
-                        pair = ff_add(pair, pa[0].s0);
+                    PairAcc pa[PPL];
+#pragma unroll
+                    for (int p = 0; p < PPL; ++p) clear(pa[p]);
+                    if (!eval_core<LS, MODE, RING_NODE_BUF, PPL>(P, q, rec, buf, nullptr, bsc, bsc2, lane, pa)) continue;
+#pragma unroll
+                    for (int p = 0; p < PPL; ++p) {
+                        if (MODE == MODE_CNT)
+                            cnt[p] += pa[p].cnt;
+                        else
+                            pair[p] = ff_add(pair[p], pa[p].s0);
+                    }
                 }
             }
-            if (MODE != MODE_CNT) acc = ff_add(acc, ff_mul_f(pair, rec[REC_FR] * hw));
+            if (MODE != MODE_CNT) {
+#pragma unroll
+                for (int p = 0; p < PPL; ++p) acc[p] = ff_add(acc[p], ff_mul_f(pair[p], rec[REC_FR] * hw));
+            }
         }
     }
-    if (!g.valid[0]) return;
-    const int px = px0 + (lane & 7), py = py0 + (lane >> 3);
-    const size_t out = (size_t)py * P.nx + px;
-    if (!FDX_IN_BOUNDS(out, (long long)P.nx * P.ny, DBG_IMAGE)) return;
-    if (RP.partial) {
-        const size_t slot = (size_t)blockIdx.z * P.nx * P.ny + out;
-        if (MODE == MODE_CNT)
-            reinterpret_cast<int32_t *>(RP.partial)[slot] = cnt;
-        else
-            RP.partial[slot] = make_float2(acc.hi, acc.lo);
-    } else if (MODE == MODE_CNT) {
-        P.counts[out] = cnt;
-    } else {
-        P.image[out] = acc.hi + acc.lo;
+#pragma unroll
+    for (int p = 0; p < PPL; ++p) {
+        if (!g.valid[p]) continue;
+        const int px = px0 + (lane & 7), py = py0 + (lane >> 3) + 4 * p;
+        const size_t out = (size_t)py * P.nx + px;
+        if (!FDX_IN_BOUNDS(out, (long long)P.nx * P.ny, DBG_IMAGE)) continue;
+        if (RP.partial) {
+            const size_t slot = (size_t)blockIdx.z * P.nx * P.ny + out;
+            if (MODE == MODE_CNT)
+                reinterpret_cast<int32_t *>(RP.partial)[slot] = cnt[p];
+            else
+                RP.partial[slot] = make_float2(acc[p].hi, acc[p].lo);
+        } else if (MODE == MODE_CNT) {
+            P.counts[out] = cnt[p];
+        } else {
+            P.image[out] = acc[p].hi + acc[p].lo;
+        }
     }
 }
 
@@ -166,14 +194,14 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) ring_kernel(RingParams RP)
     __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? RING_NODE_BUF / 2 : 1];
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * 8 + (warp >> 1) * 4;
+    const int px0 = blockIdx.x * 16 + (warp & 1) * 8, py0 = blockIdx.y * (8 * RING_PPL) + (warp >> 1) * (4 * RING_PPL);
     if (px0 >= RP.P.nx || py0 >= RP.P.ny) return;
-    ring_warp<LS, MODE>(RP, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
+    ring_warp<LS, MODE, RING_PPL>(RP, px0, py0, s_nodes[warp], s_sc[warp], s_sc2[warp], s_rec[warp], lane);
 }
 
 template <int LS>
 static void launch_ring_ls(const RingParams &p, bool count_mode, cudaStream_t s) {
-    dim3 grid((p.P.nx + 15) / 16, (p.P.ny + 7) / 8, p.n_split);
+    dim3 grid((p.P.nx + 15) / 16, (p.P.ny + 8 * RING_PPL - 1) / (8 * RING_PPL), p.n_split);
     if (count_mode)
         ring_kernel<LS, MODE_CNT><<<grid, PAIR_WARPS * 32, 0, s>>>(p);
     else
