@@ -399,9 +399,11 @@ int run_scatter(const fdx_problem *prob, int32_t n_s, const float *samples, int3
 }
 
 // Warps per 8 x 4 RING_PPL patch of the ring average: about 32768 warps in all
-// (some fourteen waves of 16 resident warps on each of 148 SMs), at most 128.
+// (some fourteen waves of 16 resident warps on each of 148 SMs), at most 128;
+// one per patch once the patches alone give 16384 warps (seven waves).
 int ring_split(const fdx_problem *p) {
     const long long patches = (long long)((p->geom.n_x + 7) / 8) * ((p->geom.n_y + 4 * RING_PPL - 1) / (4 * RING_PPL));
+    if (patches >= 16384) return 1;
     const long long s = (32768 + patches - 1) / (patches > 0 ? patches : 1);
     return (int)(s < 1 ? 1 : (s > 128 ? 128 : s));
 }
