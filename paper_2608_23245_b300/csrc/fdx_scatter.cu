@@ -13,11 +13,10 @@
 // d_i = x_i T, c = (1 + d^2)^(-1/2), volume element dV = q h_r T^2
 // (r0 + x_r h_r)^2 c^3.  The pixel value is sum over hits of dV L I.
 //
-// Work decomposition: a warp evaluates 32 consecutive samples of one
-// reflection (one sample per lane) with the same pair evaluation as the
-// gather form (eval_core: block culling, live-node staging, packed walk); the
-// query points are the samples, referred to the warp's sample nearest their
-// centroid.  The
+// Work decomposition: a warp evaluates 64 consecutive samples of one
+// reflection (two per lane) with the same pair evaluation as the gather form
+// (eval_core: block culling, live-node staging, packed walk); the query points
+// are the samples, referred to the warp's sample nearest their centroid.  The
 // per-sample Ewald rotation runs in float-float (one lane per sample) on seven
 // projections of S, with Newton-refined reciprocals; the weights are FP32.
 // The hits are added with FP64 atomics into an FP64 image that a last kernel
@@ -27,6 +26,8 @@
 namespace fdx {
 
 static constexpr int SCAT_NODE_BUF = 288;
+// Query points (samples) per lane of the scatter kernel.
+static constexpr int SCAT_PPL = 2;
 
 // Per-sample table from the normalised samples (FP64, once per call):
 // (c - 1, c d1) and (c d2) as float-float, c, q T^2 c^3, x_r.
@@ -158,34 +159,52 @@ __device__ __forceinline__ void splat_sample(const ScatterParams &p, const ff *s
     }
 }
 
+// (S - D)/r0 of sample m in the reflection frame: (1 + rho) (c, c d1, c d2) - (1, 0, 0),
+// rho = x_r h_r / r0, float-float.
+__device__ __forceinline__ void sample_offset(const ScatterParams &p, int m, float rho_r, ff &u0, ff &u1, ff &u2) {
+    const float4 ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
+    const float rho = tc.x * rho_r;
+    u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
+    u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
+    u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
+}
+
+// A warp evaluates 32 SCAT_PPL consecutive samples of one reflection: sample
+// chunk * 32 SCAT_PPL + 32 p + lane is the lane's query point p, so that the
+// packed walk has SCAT_PPL query points per node pair (with bricks of 32
+// samples, a warp's points are SCAT_PPL adjacent bricks).
 template <int LS, int MODE>
 __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterParams p) {
+    constexpr int PPL = SCAT_PPL, NW = 32 * PPL;
     __shared__ float4 s_nodes[PAIR_WARPS][SCAT_NODE_BUF];
     __shared__ float4 s_sc[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? SCAT_NODE_BUF : 1];
     __shared__ float4 s_sc2[PAIR_WARPS][(LS == FDX_LINESHAPE_HOSEMANN && MODE == MODE_FWD) ? SCAT_NODE_BUF / 2 : 1];
     __shared__ float s_rec[PAIR_WARPS][REC_SIZE];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n_chunks = (p.n_s + 31) / 32;
+    const int n_chunks = (p.n_s + NW - 1) / NW;
     const long long item = (long long)blockIdx.x * PAIR_WARPS + warp;
     if (item >= (long long)p.P.n_refl * n_chunks) return;
     const int r = (int)(item / n_chunks), chunk = (int)(item % n_chunks);
     float *rec = s_rec[warp];
     load_record(p.P.recs, r, rec, lane);
     const float2 *pr = p.proj + (size_t)r * SCAT_PROJ;
+    const float rho_r = pr[23].x;
 
-    const int m = chunk * 32 + lane;
-    const int n_valid = min(32, p.n_s - chunk * 32);
-    const bool valid = lane < n_valid;
-    float4 ta = make_float4(0.f, 0.f, 0.f, 0.f), tb = ta, tc = ta;
-    if (valid) ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
-    // (S - D)/r0 in the reflection frame: (1 + rho) (c, c d1, c d2) - (1, 0, 0), rho = x_r h_r / r0
-    const float rho = tc.x * pr[23].x;
-    const ff u0 = ff_add_f(ff{ta.x, ta.y}, rho * tb.z);
-    const ff u1 = ff_add_f(ff{ta.z, ta.w}, rho * ta.z);
-    const ff u2 = ff_add_f(ff{tb.x, tb.y}, rho * tb.x);
+    const int n_valid = min(NW, p.n_s - chunk * NW);
+    bool valid[PPL];
+    ff u0[PPL], u1[PPL], u2[PPL];
+    float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        valid[q] = 32 * q + lane < n_valid;
+        u0[q] = u1[q] = u2[q] = ff{0.0f, 0.0f};
+        if (valid[q] && FDX_IN_BOUNDS(chunk * NW + 32 * q + lane, p.n_s, DBG_SPLAT)) {
+            sample_offset(p, chunk * NW + 32 * q + lane, rho_r, u0[q], u1[q], u2[q]);
+            cx += u0[q].hi, cy += u1[q].hi, cz += u2[q].hi;
+        }
+    }
     // reference: the valid sample nearest the centroid of the warp's samples
     // (any order of the samples is correct; neighbours in a warp cull best)
-    float cx = valid ? u0.hi : 0.0f, cy = valid ? u1.hi : 0.0f, cz = valid ? u2.hi : 0.0f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         cx += __shfl_xor_sync(FDX_FULL_MASK, cx, o);
@@ -194,55 +213,87 @@ __global__ void __launch_bounds__(PAIR_WARPS * 32, 4) scatter_kernel(ScatterPara
     }
     const float inv_n = 1.0f / (float)n_valid;
     cx *= inv_n, cy *= inv_n, cz *= inv_n;
-    const float dx = u0.hi - cx, dy = u1.hi - cy, dz = u2.hi - cz;
     // squared distances are >= 0, so their bit patterns order like the values;
-    // the low 5 bits carry the lane (ties and near-ties go to either lane)
-    unsigned key = valid ? ((__float_as_uint(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) & ~31u) | (unsigned)lane) : 0xffffffffu;
+    // the low 6 bits carry the point's index in the warp (ties and near-ties go
+    // to either point)
+    unsigned key = 0xffffffffu;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        const float dx = u0[q].hi - cx, dy = u1[q].hi - cy, dz = u2[q].hi - cz;
+        if (valid[q])
+            key = min(key, (__float_as_uint(fmaf(dx, dx, fmaf(dy, dy, dz * dz))) & ~63u) | (unsigned)(32 * q + lane));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(FDX_FULL_MASK, key, o));
-    const int rl = (int)(key & 31u);
-    const ff v0 = {__shfl_sync(FDX_FULL_MASK, u0.hi, rl), __shfl_sync(FDX_FULL_MASK, u0.lo, rl)};
-    const ff v1 = {__shfl_sync(FDX_FULL_MASK, u1.hi, rl), __shfl_sync(FDX_FULL_MASK, u1.lo, rl)};
-    const ff v2 = {__shfl_sync(FDX_FULL_MASK, u2.hi, rl), __shfl_sync(FDX_FULL_MASK, u2.lo, rl)};
-    QueryPts<1> q;
-    q.valid[0] = valid;
-    q.P[0][0] = u0.hi, q.P[0][1] = u1.hi, q.P[0][2] = u2.hi;
-    const float w0 = (u0.hi - v0.hi) + (u0.lo - v0.lo);
-    const float w1 = (u1.hi - v1.hi) + (u1.lo - v1.lo);
-    const float w2 = (u2.hi - v2.hi) + (u2.lo - v2.lo);
+    const int rl = (int)(key & 31u), rq = (int)((key & 63u) >> 5);
+    ff c0 = u0[0], c1 = u1[0], c2 = u2[0];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
-        q.tau[0][i] = valid ? fmaf(rec[REC_H + i], w0, fmaf(rec[REC_E1 + i], w1, rec[REC_E2 + i] * w2)) : 1.0e4f;
-    q.dP[0] = v0, q.dP[1] = v1, q.dP[2] = v2;
+    for (int q = 1; q < PPL; ++q)
+        if (rq == q) c0 = u0[q], c1 = u1[q], c2 = u2[q];
+    const ff v0 = {__shfl_sync(FDX_FULL_MASK, c0.hi, rl), __shfl_sync(FDX_FULL_MASK, c0.lo, rl)};
+    const ff v1 = {__shfl_sync(FDX_FULL_MASK, c1.hi, rl), __shfl_sync(FDX_FULL_MASK, c1.lo, rl)};
+    const ff v2 = {__shfl_sync(FDX_FULL_MASK, c2.hi, rl), __shfl_sync(FDX_FULL_MASK, c2.lo, rl)};
+    QueryPts<PPL> qp;
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) {
+        qp.valid[q] = valid[q];
+        qp.P[q][0] = u0[q].hi, qp.P[q][1] = u1[q].hi, qp.P[q][2] = u2[q].hi;
+        const float w0 = (u0[q].hi - v0.hi) + (u0[q].lo - v0.lo);
+        const float w1 = (u1[q].hi - v1.hi) + (u1[q].lo - v1.lo);
+        const float w2 = (u2[q].hi - v2.hi) + (u2[q].lo - v2.lo);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            qp.tau[q][i] =
+                valid[q] ? fmaf(rec[REC_H + i], w0, fmaf(rec[REC_E1 + i], w1, rec[REC_E2 + i] * w2)) : 1.0e4f;
+    }
+    qp.dP[0] = v0, qp.dP[1] = v1, qp.dP[2] = v2;
 
-    PairAcc pa[1];
-    clear(pa[0]);
-    const bool any = eval_core<LS, MODE, SCAT_NODE_BUF, 1>(p.P, q, rec, s_nodes[warp], nullptr, s_sc[warp],
-                                                           s_sc2[warp], lane, pa);
+    PairAcc pa[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) clear(pa[q]);
+    const bool any = eval_core<LS, MODE, SCAT_NODE_BUF, PPL>(p.P, qp, rec, s_nodes[warp], nullptr, s_sc[warp],
+                                                             s_sc2[warp], lane, pa);
     if (MODE == MODE_CNT) {
-        unsigned long long c = any ? (unsigned long long)pa[0].cnt : 0ull;
+        unsigned long long c = 0ull;
+        if (any) {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) c += (unsigned long long)pa[q].cnt;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FDX_FULL_MASK, c, o);
         if (lane == 0 && c) atomicAdd(p.count, c);
         return;
     }
-    if (!valid || !any) return;
-    const float I = rec[REC_FR] * (pa[0].s0.hi + pa[0].s0.lo);
-    if (!(I != 0.0f)) return;
-    // projections of S = (r0 + x_r h_r) (c, c d1, c d2) in the reflection frame
-    // from the frame projections and the sample table, all float-float (the
-    // hit position of a sample near the edge of the Ewald condition is
-    // sensitive to S), and the volume element (a weight: FP32)
-    const ff rr = ff_add(ffv(pr[21]), ff_mul_f(ffv(pr[22]), tc.x));
-    const ff U0 = ff_add_f(ff{ta.x, ta.y}, 1.0f), U1 = {ta.z, ta.w}, U2 = {tb.x, tb.y};
-    ff sp[7];
+    if (!any) return;
+    float Iq[PPL];
 #pragma unroll
-    for (int j = 0; j < 7; ++j)
-        sp[j] = ff_mul(rr, ff_add(ff_add(ff_mul(U0, ffv(pr[3 * j])), ff_mul(U1, ffv(pr[3 * j + 1]))),
-                                  ff_mul(U2, ffv(pr[3 * j + 2]))));
-    const float rrf = rr.hi + rr.lo;
-    const float dV = tb.w * pr[22].x * rrf * rrf;
-    splat_sample(p, sp, rr, dV * I);
+    for (int q = 0; q < PPL; ++q) Iq[q] = valid[q] ? rec[REC_FR] * (pa[q].s0.hi + pa[q].s0.lo) : 0.0f;
+    const ff rr0 = ffv(pr[21]), rr1 = ffv(pr[22]);
+#pragma unroll 1
+    for (int q = 0; q < PPL; ++q) {
+        float I = 0.0f;
+#pragma unroll
+        for (int k = 0; k < PPL; ++k)
+            if (k == q) I = Iq[k];
+        if (!(I != 0.0f)) continue;
+        const int m = chunk * NW + 32 * q + lane;
+        if (!FDX_IN_BOUNDS(m, p.n_s, DBG_SPLAT)) continue;
+        // projections of S = (r0 + x_r h_r) (c, c d1, c d2) in the reflection frame
+        // from the frame projections and the sample table, all float-float (the
+        // hit position of a sample near the edge of the Ewald condition is
+        // sensitive to S), and the volume element (a weight: FP32)
+        const float4 ta = p.stab[3 * m], tb = p.stab[3 * m + 1], tc = p.stab[3 * m + 2];
+        const ff rr = ff_add(rr0, ff_mul_f(rr1, tc.x));
+        const ff U0 = ff_add_f(ff{ta.x, ta.y}, 1.0f), U1 = {ta.z, ta.w}, U2 = {tb.x, tb.y};
+        ff sp[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j)
+            sp[j] = ff_mul(rr, ff_add(ff_add(ff_mul(U0, ffv(pr[3 * j])), ff_mul(U1, ffv(pr[3 * j + 1]))),
+                                      ff_mul(U2, ffv(pr[3 * j + 2]))));
+        const float rrf = rr.hi + rr.lo;
+        const float dV = tb.w * pr[22].x * rrf * rrf;
+        splat_sample(p, sp, rr, dV * I);
+    }
 }
 
 __global__ void scatter_finish_kernel(const double *img64, float *image, long long n) {
@@ -252,7 +303,7 @@ __global__ void scatter_finish_kernel(const double *img64, float *image, long lo
 
 template <int LS>
 static void launch_scatter_ls(const ScatterParams &p, bool count_mode, cudaStream_t s) {
-    const long long items = (long long)p.P.n_refl * ((p.n_s + 31) / 32);
+    const long long items = (long long)p.P.n_refl * ((p.n_s + 32 * SCAT_PPL - 1) / (32 * SCAT_PPL));
     const unsigned grid = (unsigned)((items + PAIR_WARPS - 1) / PAIR_WARPS);
     if (grid == 0) return;
     if (count_mode)

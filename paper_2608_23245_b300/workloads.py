@@ -373,9 +373,10 @@ def small_tilted() -> Problem:
 
 def sample_brick(n_r: int, n_1: int, n_2: int):
     """Brick of 32 grid cells in which the scatter samples are ordered (a warp
-    of the scatter kernel takes one brick): 4 x 4 x 2 (radial x angular x
-    angular), the fastest shape measured, or 2 x 4 x 4 when n_r is not a
-    multiple of 4."""
+    of the scatter kernel takes two consecutive bricks, one per query point of
+    its lanes; consecutive bricks are neighbours along the last axis):
+    4 x 4 x 2 (radial x angular x angular), the fastest shape measured, or
+    2 x 4 x 4 when n_r is not a multiple of 4."""
     brick = (4, 4, 2) if n_r % 4 == 0 and n_2 % 2 == 0 else (2, 4, 4)
     if n_r % brick[0] or n_1 % brick[1] or n_2 % brick[2]:
         raise ValueError("grid must be a multiple of 4 x 4 x 2 or of 2 x 4 x 4")
