@@ -122,9 +122,11 @@ def test_scatter_matches_oracle(gpu, orc, make, kind, spot):
     assert abs(E - E_ref) <= 1e-4 * E_ref, (E, E_ref)
 
 
-@pytest.mark.parametrize("n", [1, 31, 77])
+@pytest.mark.parametrize("n", [1, 31, 50, 77, 100])
 def test_scatter_ragged_sample_counts(gpu, orc, n):
-    """Sample counts that leave the last warp of samples partly empty."""
+    """Sample counts that leave the last warp of samples partly empty (a warp
+    takes 64, two per lane: 31 leaves every lane's second sample out, 50 and
+    100 part of them)."""
     import torch
     p = api_precision(W.small_helix())
     xs = W.scatter_samples(4, 8, 8)[:n]
