@@ -445,6 +445,18 @@ int run_ring(const fdx_problem *prob, float *image, int32_t *counts, void *works
 
 }  // namespace
 
+// The debugging build's status word (declared in fdx_internal.cuh, C++
+// linkage) and its probe kernel.
+#ifdef FDX_DEBUG
+__device__ unsigned long long fdx_debug_word[2];
+
+// One check that fails on purpose (index 7 of a 3-entry range, check 63):
+// nothing is accessed, only the status word is written.
+__global__ void debug_probe_kernel() {
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)FDX_IN_BOUNDS(7, 3, 63);
+}
+#endif
+
 extern "C" {
 
 size_t fdx_batch_workspace_size(int32_t n_models, const fdx_problem *const *probs, const fdx_atoms *const *atoms) {
@@ -644,16 +656,6 @@ int fdx_batch_refine(int32_t n_models, const fdx_problem *const *probs, const fd
 }
 
 int fdx_version(void) { return 100; }
-
-#ifdef FDX_DEBUG
-__device__ unsigned long long fdx_debug_word[2];
-
-// One check that fails on purpose (index 7 of a 3-entry range, check 63):
-// nothing is accessed, only the status word is written.
-__global__ void debug_probe_kernel() {
-    if (threadIdx.x == 0 && blockIdx.x == 0) (void)FDX_IN_BOUNDS(7, 3, 63);
-}
-#endif
 
 int fdx_debug_probe(void *stream) {
 #ifdef FDX_DEBUG
