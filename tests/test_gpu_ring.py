@@ -56,7 +56,7 @@ def test_ring_mirror_symmetry_gpu(gpu):
 
 
 def test_ring_unsplit_large_detector(gpu, orc):
-    """A detector of 1024 x 1024 pixels has enough 8 x 4 patches to fill the
+    """A detector of 1024 x 1024 pixels has enough 8 x 8 patches to fill the
     GPU with one warp each, so every reflection's azimuth points stay in one
     warp (the reduced detectors above deal them to several): sampled pixels
     against the oracle, and the in-support count of those pixels."""
@@ -103,3 +103,35 @@ def test_ring_edge_cases(gpu, orc):
         I, _ = orc.ring(q, hkl[:n], M[:n].astype(np.float32).astype(np.float64))
         mr, l2 = parity(img, I)
         assert mr <= MAX_REL and l2 <= L2_REL, (nx, ny, mr, l2)
+
+
+def test_ring_helix_central_region(gpu, orc):
+    """The ring average as the benchmark runs it: the helix model's central
+    128 x 128 pixels (0.1 mm), all 5,062 reflections, 64^2 nodes, so that
+    each reflection's azimuth points are dealt to 128 warps per patch and
+    summed by the reduce kernel; seeded pixels against the oracle (both sides
+    fed the oracle's reflections and intensities), and their in-support
+    counts."""
+    import torch
+    p = W.config1()
+    p = api_precision(replace(p, geom=replace(p.geom, n_x=128, n_y=128)))
+    hkl = orc.reflections(p.cell, p.d_min)
+    M = orc.intensities_M(p, hkl).astype(np.float32)
+    hk = torch.as_tensor(np.ascontiguousarray(hkl, np.int32), device="cuda").reshape(-1, 3)
+    Mt = torch.as_tensor(M, device="cuda")
+    prob = gpu.make_problem(p.cell, p.br, p.geom, hk, Mt)
+    img = torch.full((128, 128), float("nan"), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros((128, 128), dtype=torch.int32, device="cuda")
+    gpu.fdx_ring(prob, img)
+    gpu.fdx_ring_evals(prob, cnt)
+    torch.cuda.synchronize()
+    img, cnt = img.cpu().numpy(), cnt.cpu().numpy()
+    rng = np.random.default_rng(11)
+    pix = np.stack([rng.integers(0, 128, 12), rng.integers(0, 128, 12)], 1)
+    I, E = orc.ring(p, hkl, M.astype(np.float64), pix=pix)
+    got = img[pix[:, 1], pix[:, 0]].astype(np.float64)
+    assert I.max() > 0
+    mr, l2 = parity(got, I)
+    assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
+    n = int(cnt[pix[:, 1], pix[:, 0]].astype(np.int64).sum())
+    assert abs(n - int(E.sum())) <= 1e-4 * E.sum()

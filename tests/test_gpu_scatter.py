@@ -190,3 +190,40 @@ def test_scatter_spot_box_filter_gpu(gpu, spot):
     box /= spot * spot
     assert imgs.max() > 0
     assert np.max(np.abs(imgs[h:ny - h, h:nx - h] - box)) <= 1e-6 * imgs.max()
+
+
+def test_scatter_helix_full_geometry(gpu, orc):
+    """The scatter form in the benchmark's geometry: the helix model's 1024 x
+    1024 detector, 64^2 nodes and 16^3 stratified samples per reflection
+    (bricks, two samples per lane), on 12 seeded reflections of the oracle's
+    list with the oracle's intensities (the oracle's cost grows with samples
+    x nodes per reflection): element-wise parity outside the excluded pixels,
+    the excluded pixels bounded by their ambiguous hits, equal totals and
+    term counts."""
+    import torch
+    p = api_precision(W.config1())
+    hkl_all = orc.reflections(p.cell, p.d_min)
+    pick = np.sort(np.random.default_rng(13).choice(len(hkl_all), 12, replace=False))
+    hkl = np.ascontiguousarray(hkl_all[pick], np.int32)
+    M = orc.intensities_M(p, hkl).astype(np.float32)
+    hk = torch.as_tensor(hkl, device="cuda").reshape(-1, 3)
+    Mt = torch.as_tensor(M, device="cuda")
+    prob = gpu.make_problem(p.cell, p.br, p.geom, hk, Mt)
+    xs = W.scatter_samples(16, 16, 16)
+    smp = torch.as_tensor(xs, device="cuda")
+    img = torch.zeros((p.geom.n_y, p.geom.n_x), dtype=torch.float32, device="cuda")
+    gpu.fdx_scatter(prob, smp, img)
+    count = torch.zeros((), dtype=torch.int64, device="cuda")
+    gpu.fdx_scatter_evals(prob, smp, count)
+    torch.cuda.synchronize()
+    img = img.cpu().numpy().astype(np.float64)
+    E = int(count.item())
+    ref, E_ref, samp = orc.scatter(p, hkl, M.astype(np.float64), xs.astype(np.float64), with_samples=True)
+    assert ref.max() > 0
+    bad = _edge_mask(p, samp)
+    mr, l2 = parity(np.where(bad, 0.0, img).reshape(-1), np.where(bad, 0.0, ref).reshape(-1))
+    assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
+    diff_bad = float(np.sum(np.abs(img - ref)[bad]))
+    assert diff_bad <= _ambiguous_value(samp) + MAX_REL * ref.max() * bad.sum(), (diff_bad, _ambiguous_value(samp))
+    assert img.sum() == pytest.approx(ref.sum(), rel=1e-5)
+    assert abs(E - E_ref) <= 1e-4 * E_ref, (E, E_ref)
