@@ -50,3 +50,14 @@ def amp_scale(p, hkl):
 
 
 SF_TOL = 2e-6   # |F_gpu - F_ref| <= SF_TOL * amp_scale per reflection
+
+
+def oracle_hkl(orc, problem, lib_hkl):
+    """The oracle's own reflection list for `problem`, after checking that the
+    library's list (the order the GPU results are in) is the same, entry for
+    entry (integer work: bit-exact).  Oracle calls take this list, never the
+    library's."""
+    h = np.asarray(orc.reflections(problem.cell, problem.d_min, problem.d_max), dtype=np.int32).reshape(-1, 3)
+    lib = np.asarray(lib_hkl, dtype=np.int32).reshape(-1, 3)
+    assert h.shape == lib.shape and np.array_equal(h, lib), "library and oracle reflection lists differ"
+    return h

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import api_precision
+from _common import api_precision, oracle_hkl
 
 pytestmark = pytest.mark.gpu
 
@@ -86,7 +86,7 @@ def test_backward_matches_oracle_adjoint(gpu, orc, make):
     rng = np.random.default_rng(17)
     gI = rng.uniform(-1.0, 1.0, p.geom.n_x * p.geom.n_y).astype(np.float32)
     sim, g = _gpu_grads(gpu, p, gI)
-    o = _oracle_grads(orc, p, sim.hkl_host, gI.astype(np.float64))
+    o = _oracle_grads(orc, p, oracle_hkl(orc, p, sim.hkl_host), gI.astype(np.float64))
     _close(g["dM"], o["dM"], what="dM")
     _close(g["dfrac"], o["dfrac"], what="dfrac")
     _close(g["dB"], o["dB"], what="dB")
@@ -136,7 +136,7 @@ def test_refinement_gradient_helix_subset(gpu, orc):
     loss.backward()
     torch.cuda.synchronize()
     # oracle
-    hkl = rm.hkl_host
+    hkl = oracle_hkl(orc, model, rm.hkl_host)
     Mt = orc.intensities_M(target, hkl)
     It_o, _ = orc.pattern(target, hkl, Mt, pix)
     loss_o, go, _ = orc.full_gradient(model, hkl, It_o, pix)

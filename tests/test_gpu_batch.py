@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, api_precision, parity
+from _common import L2_REL, MAX_REL, api_precision, oracle_hkl, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -76,7 +76,7 @@ def test_batch_forward_against_oracle(gpu, orc):
     step()
     torch.cuda.synchronize()
     for m, p in enumerate(models):
-        hkl = sims[m].hkl_host
+        hkl = oracle_hkl(orc, p, sims[m].hkl_host)
         I, _ = orc.pattern(p, hkl, orc.intensities_M(p, hkl))
         mr, l2 = parity(step.images[m].cpu().numpy().reshape(-1), I)
         assert mr <= MAX_REL and l2 <= L2_REL, (m, mr, l2)

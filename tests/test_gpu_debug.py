@@ -95,8 +95,9 @@ def test_debug_build_records_no_out_of_bounds_index(orc):
     assert out["enabled"]
     assert out["flags"] == 0, "failed checks 0x%x, last index %d" % (out["flags"], out["index"])
     from paper_2608_23245_b300 import workloads as W
-    from _common import L2_REL, MAX_REL, api_precision, parity
+    from _common import L2_REL, MAX_REL, api_precision, oracle_hkl, parity
     p = api_precision(W.small_helix())
-    I, _ = orc.pattern(p, out["helix_hkl"], orc.intensities_M(p, out["helix_hkl"]))
+    hkl = oracle_hkl(orc, p, out["helix_hkl"])
+    I, _ = orc.pattern(p, hkl, orc.intensities_M(p, hkl))
     mr, l2 = parity(out["helix_image"].reshape(-1), I)
     assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)

@@ -23,7 +23,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, api_precision, parity
+from _common import L2_REL, MAX_REL, api_precision, oracle_hkl, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -108,8 +108,9 @@ def test_batched_real_models(gpu, orc):
         n = p.geom.n_x
         flat = rng.choice(n * p.geom.n_y, 256, replace=False)       # distinct pixels
         pix = np.stack([flat % n, flat // n], 1).astype(np.int32)
-        M = orc.intensities_M(p, s.hkl_host)
-        I, E = orc.pattern(p, s.hkl_host, M, pix)
+        hkl = oracle_hkl(orc, p, s.hkl_host)
+        M = orc.intensities_M(p, hkl)
+        I, E = orc.pattern(p, hkl, M, pix)
         # targets off the model by up to 0.3 max I everywhere, so every residual
         # is large against the image gate (1e-5 max I)
         It = np.maximum(I + 0.3 * I.max() * rng.uniform(-1.0, 1.0, len(I)), 0.0)
@@ -133,7 +134,7 @@ def test_batched_real_models(gpu, orc):
         torch.cuda.synchronize()
         c = cnt.cpu().numpy()[pix[:, 1], pix[:, 0]]
         assert np.all(c >= Eo[k][:, 1]) and np.all(c <= Eo[k][:, 2]), chosen[k]
-        loss_o, go, _ = orc.full_gradient(p, s.hkl_host, Its[k], pix)
+        loss_o, go, _ = orc.full_gradient(p, oracle_hkl(orc, p, s.hkl_host), Its[k], pix)
         # the loss bound that follows from the image gate: |I - I_o| <= d =
         # MAX_REL max I_o per pixel gives |dL| <= sum w (2 |I_o - I_t| d + d^2)
         d = MAX_REL * Io[k].max()
@@ -171,7 +172,7 @@ def test_large_structure_factors(gpu, orc):
     sim = gpu.Simulation(p)
     F, M = sim.structure_factors()
     torch.cuda.synchronize()
-    h = sim.hkl_host
+    h = oracle_hkl(orc, p, sim.hkl_host)
     mer = np.where((h[:, 0] == 0) & (h[:, 1] == 0))[0]
     rng = np.random.default_rng(8000)
     idx = np.unique(np.concatenate([mer, rng.choice(len(h), 8000, replace=False)]))

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, SF_TOL, amp_scale as _amp_scale, api_precision, parity
+from _common import L2_REL, MAX_REL, SF_TOL, amp_scale as _amp_scale, api_precision, oracle_hkl, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -59,13 +59,14 @@ def test_structure_factors(gpu, orc, make):
     _sync()
     F = F.cpu().numpy().astype(np.float64)
     Fg = F[:, 0] + 1j * F[:, 1]
-    Fo = orc.structure_factors(p.cell, p.atoms, sim.hkl_host)
-    Mo = orc.intensities_M(p, sim.hkl_host, Fo)
-    scale = _amp_scale(p, sim.hkl_host)
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
+    Fo = orc.structure_factors(p.cell, p.atoms, hkl)
+    Mo = orc.intensities_M(p, hkl, Fo)
+    scale = _amp_scale(p, hkl)
     err = np.abs(Fg - Fo) / scale
     assert err.max() <= SF_TOL, err.max()
     Mg = M.cpu().numpy().astype(np.float64)
-    _, P, DW = orc.refl_scalars(p, sim.hkl_host)
+    _, P, DW = orc.refl_scalars(p, hkl)
     merr = np.abs(Mg - Mo) / ((2 * np.abs(Fo) + scale) * scale * P * DW)
     assert merr.max() <= 4e-6, merr.max()
 
@@ -208,8 +209,9 @@ def test_end_to_end(gpu, orc, make):
     img = sim.forward()
     _sync()
     img = img.cpu().numpy()
-    Mo = orc.intensities_M(p, sim.hkl_host)
-    I, _ = orc.pattern(p, sim.hkl_host, Mo)
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
+    Mo = orc.intensities_M(p, hkl)
+    I, _ = orc.pattern(p, hkl, Mo)
     mr, l2 = parity(img.reshape(-1), I)
     assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)
 
@@ -229,8 +231,9 @@ def test_helix_full_size_sampled(gpu, orc):
     ii = np.concatenate([rng.integers(0, n, 48), rng.integers(n // 4, 3 * n // 4, 48)])
     jj = np.concatenate([rng.integers(0, n, 48), rng.integers(n // 4, 3 * n // 4, 48)])
     pix = np.stack([ii, jj], axis=1).astype(np.int32)
-    Mo = orc.intensities_M(p, sim.hkl_host)
-    I, E = orc.pattern(p, sim.hkl_host, Mo, pix)
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
+    Mo = orc.intensities_M(p, hkl)
+    I, E = orc.pattern(p, hkl, Mo, pix)
     got = img[jj, ii]
     mr, l2 = parity(got, I)
     assert mr <= MAX_REL and l2 <= L2_REL, (mr, l2)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import api_precision
+from _common import api_precision, oracle_hkl
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,7 @@ def test_plain64_forward_and_gradient(gpu, orc, make):
     dglob = torch.empty(8, dtype=torch.float64, device="cuda")
     gpu.fdx_plain64_refine(sim.prob, sim.atoms, img, torch.as_tensor(It, device="cuda"), None, loss, dfrac, dB, dglob)
     torch.cuda.synchronize()
-    hkl = sim.hkl_host
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
     Mo = orc.intensities_M(p, hkl)
     I, _ = orc.pattern(p, hkl, Mo)
     assert _rel(img.cpu().numpy(), I) <= TOL64

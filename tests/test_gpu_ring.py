@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, api_precision, parity
+from _common import L2_REL, MAX_REL, api_precision, oracle_hkl, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,7 @@ def test_ring_matches_oracle(gpu, orc, make):
     img = sim.ring().cpu().numpy().reshape(-1)
     cnt = sim.ring_evals().cpu().numpy().reshape(-1)
     torch.cuda.synchronize()
-    hkl = sim.hkl_host
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
     I, E = orc.ring(p, hkl, orc.intensities_M(p, hkl))
     assert I.max() > 0
     mr, l2 = parity(img, I)
@@ -72,7 +72,7 @@ def test_ring_unsplit_large_detector(gpu, orc):
     torch.cuda.synchronize()
     rng = np.random.default_rng(7)
     pix = np.stack([rng.integers(0, 1024, 32), rng.integers(0, 1024, 32)], 1)
-    hkl = sim.hkl_host
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
     I, E = orc.ring(p, hkl, orc.intensities_M(p, hkl), pix=pix)
     got = img[pix[:, 1], pix[:, 0]].astype(np.float64)
     assert I.max() > 0

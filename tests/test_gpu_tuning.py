@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2608_23245_b300 import workloads as W
-from _common import L2_REL, MAX_REL, api_precision, parity
+from _common import L2_REL, MAX_REL, api_precision, oracle_hkl, parity
 
 pytestmark = pytest.mark.gpu
 
@@ -106,7 +106,7 @@ def test_node_block_shapes_adjoint(gpu, orc, tuned, nb, make):
     dM = torch.empty(n, dtype=torch.float32, device="cuda")
     gpu.fdx_pattern_backward(sim.prob, sim.atoms, sim.F, gI, dfrac, dB, dg, dM)
     torch.cuda.synchronize()
-    hkl = sim.hkl_host
+    hkl = oracle_hkl(orc, p, sim.hkl_host)
     gIo = gI.cpu().numpy().astype(np.float64).reshape(-1)
     F = orc.structure_factors(p.cell, p.atoms, hkl)
     _, P, DW = orc.refl_scalars(p, hkl)
